@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark of the sampled-frame hot path on the synthetic 1080p workload.
+
+Workload: one synthetic 1920x1080 NV12 video, 7200 frames (22.4 GB in HBM),
+60 shots, generated on the device by libscn's generator.  One step is one pass
+of the hot path over the three sampling modes:
+  * stride-1 (7200 frames), stride-24 (300 frames), gather of 1000 seeded frames:
+    fused BT.601 convert + 3x16 histogram + shot scores (scn_hist_scores);
+  * the stride-24 and gathered frames also resized to 224x224 and normalised,
+    once to FP32 and once to BF16 (scn_resize_norm).
+value = sampled frames (8500) per step / step time.  Every input is larger than
+L2 (126 MB), so no flush is needed between steps.
+
+--impl reference times the CPU oracle (oracle/, plain C) on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p sampled frames/s + HBM GB/s (hist+shot score); proposal speedup @99% recall"
+FRAME_BYTES = 1920 * 1080 * 3 // 2
+ALG_BYTES_PER_FRAME = FRAME_BYTES + 48 * 4 + 4 + 1  # NV12 read + hist, score, flag written
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- reference arm (CPU oracle)
+class OracleSample:
+    """A bounded sample of the workload for the CPU oracle: nframes 1080p frames of
+    the workload video, generated by the oracle's own generator (not timed)."""
+
+    def __init__(self, nframes: int, nthreads: int):
+        import numpy as np
+        import oracle
+        from paper_1805_07339_b300.workloads import HD, MASTER_SEED
+        self.oracle, self.W, self.H = oracle, HD["width"], HD["height"]
+        self.nframes, self.nthreads = nframes, nthreads
+        vid = oracle.Video(MASTER_SEED, 0, self.W, self.H, HD["num_frames"], HD["num_shots"])
+        idx = np.arange(nframes, dtype=np.int64) * (HD["num_frames"] // nframes)
+        self.frames = vid.frames(idx, nthreads=nthreads)
+
+    def step(self) -> float:
+        t0 = time.perf_counter()
+        h = self.oracle.hist_batch(self.frames, self.W, self.H, nthreads=self.nthreads)
+        self.oracle.scores(h, self.W * self.H)
+        return time.perf_counter() - t0
+
+    def rate(self, budget_s: float):
+        reps, tot = 0, 0.0
+        while tot < budget_s or reps == 0:
+            tot += self.step()
+            reps += 1
+        return self.nframes * reps / tot, reps, tot
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    ncores = os.cpu_count() or 1
+    nframes = 32
+    smp = OracleSample(nframes, ncores)
+    for _ in range(args.warmup):
+        smp.step()
+    times = [smp.step() for _ in range(args.steps)]
+    ms = 1000 * statistics.mean(times)
+    value = nframes / (ms / 1000)
+    sample = f"hist+score of {nframes} 1080p frames of the workload per step (frame generation excluded)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "1080p NV12 video, 7200 frames, 60 shots; hist+score (CPU oracle sample)",
+                   "frames_per_step": nframes},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": ncores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- native arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1805_07339_b300 import scn
+    from paper_1805_07339_b300.workloads import HD, HD_STRIDE, MASTER_SEED, hd_gather
+
+    W, H, T, S = HD["width"], HD["height"], HD["num_frames"], HD["num_shots"]
+    fb = FRAME_BYTES
+    stream = torch.cuda.current_stream()
+    # ---- setup (not timed): generate the video on the device
+    video = scn.scn_video_create(MASTER_SEED, 0, W, H, T, S)
+    buf = torch.empty(T * fb, dtype=torch.uint8, device="cuda")
+    scn.scn_generate(video, buf, 0, T, fb)
+    table = scn.scn_table_create(buf, W, H, T)
+    gather = hd_gather()
+    modes = [("stride1", dict(kind=scn.SCN_STRIDE, start=0, stop=T, step=1)),
+             ("stride24", dict(kind=scn.SCN_STRIDE, start=0, stop=T, step=HD_STRIDE)),
+             ("gather1000", dict(kind=scn.SCN_GATHER, indices=gather.tolist()))]
+    seqs, outs = {}, {}
+    for name, spec in modes:
+        kind = spec.pop("kind")
+        seqs[name] = scn.scn_sample(table, kind, **spec)
+        n = scn.scn_seq_length(seqs[name])
+        outs[name] = (torch.empty((n, 48), dtype=torch.int32, device="cuda"),
+                      torch.empty(n, dtype=torch.int32, device="cuda"),
+                      torch.empty(n, dtype=torch.uint8, device="cuda"))
+    resize_modes = ["stride24", "gather1000"]
+    mean, std = (0.485, 0.456, 0.406), (0.229, 0.224, 0.225)
+    rs_out = {m: (torch.empty((scn.scn_seq_length(seqs[m]), 3, 224, 224), dtype=torch.float32, device="cuda"),
+                  torch.empty((scn.scn_seq_length(seqs[m]), 3, 224, 224), dtype=torch.bfloat16, device="cuda"))
+              for m in resize_modes}
+    frames_per_step = sum(scn.scn_seq_length(seqs[m]) for m, _ in modes)
+    launches_per_step = len(modes) + 2 * len(resize_modes)
+    ev = {m: [] for m, _ in modes}
+
+    def step(record: bool):
+        for m, _ in modes:
+            h, s, f = outs[m]
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            scn.scn_hist_scores(seqs[m], h, s, f, stream)
+            if record:
+                e1.record(stream)
+                ev[m].append((e0, e1))
+        for m in resize_modes:
+            o32, o16 = rs_out[m]
+            scn.scn_resize_norm(seqs[m], 224, 224, mean, std, scn.SCN_F32, o32, stream)
+            scn.scn_resize_norm(seqs[m], 224, 224, mean, std, scn.SCN_BF16, o16, stream)
+
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    for m, _ in modes:
+        if scn.scn_seq_sync_status(seqs[m]) != scn.SCN_OK:
+            raise RuntimeError("device status error in warm-up")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = frames_per_step * world / (ms_step / 1000)
+
+    # dominant kernel: the fused hist+score launch over the 7200-frame stride-1 sequence
+    kern = {}
+    for m, _ in modes:
+        d = [a.elapsed_time(b) for a, b in ev[m]]
+        n = scn.scn_seq_length(seqs[m])
+        avg = statistics.mean(d)
+        kern[m] = {"frames": n, "ms": avg, "frames_per_s": n / (avg / 1000),
+                   "GB_per_s": n * ALG_BYTES_PER_FRAME / (avg / 1000) / 1e9}
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_kind = "measured" if peak else "fallback"
+    if not peak:
+        peak = 6400.0
+    dom = kern["stride1"]
+    roofline = {"bound": "hbm", "achieved": dom["GB_per_s"], "peak": peak, "unit": "GB/s",
+                "frac": dom["GB_per_s"] / peak, "traffic": None, "peak_source": peak_kind,
+                "kernel": "hist_kernel (scn_hist_scores, stride-1, 7200 frames)",
+                "alg_bytes_per_launch": dom["frames"] * ALG_BYTES_PER_FRAME}
+
+    # ---- end-to-end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, scn, torch, buf, video, seqs, modes, W, H, T, fb, gather, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ncores = os.cpu_count() or 1
+        fps, reps, secs = OracleSample(32, ncores).rate(budget_s=10.0)
+        cpu = {"value": fps, "unit": "frames/s", "cores": ncores, "kind": "oracle",
+               "sample": f"hist+score of 32 1080p frames of the workload, {reps} passes, {secs:.1f} s"}
+
+    for m, _ in modes:
+        if scn.scn_seq_sync_status(seqs[m]) != scn.SCN_OK:
+            raise RuntimeError("device status error")
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "1080p NV12 video, 7200 frames (22.4 GB), 60 shots; per step: hist+score of "
+                                   "stride-1 (7200), stride-24 (300), gather (1000) + 224x224 FP32 and BF16 "
+                                   "resize of the stride-24 and gathered frames",
+                       "frames_per_step": frames_per_step, "l2": "inputs larger than L2, no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "hbm_GB_per_s": frames_per_step * ALG_BYTES_PER_FRAME / (ms_step / 1000) / 1e9,
+            "kernels": kern, "roofline": roofline, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+            "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, scn, torch, dev_buf, video, seqs, modes, W, H, T, fb, gather, stream):
+    """Same step through the C ABI with the frames in pinned HOST memory: every
+    step copies the sampled frames host->device (only the sampled rows, as a
+    strided table) and reads the histograms, scores and flags back."""
+    import numpy as np
+    rows = {"stride1": np.arange(T), "stride24": np.arange(0, T, 24), "gather1000": gather}
+    host, dbuf, tables, eseqs, outs, houts = {}, {}, {}, {}, {}, {}
+    for m, _ in modes:
+        r = rows[m]
+        n = len(r)
+        host[m] = torch.empty(n * fb, dtype=torch.uint8, pin_memory=True)
+        # the host copy is made once from the device-generated video (setup)
+        for i0 in range(0, n, 256):
+            ri = torch.from_numpy(np.ascontiguousarray(r[i0:i0 + 256])).cuda()
+            src = dev_buf.view(T, fb).index_select(0, ri)
+            host[m][i0 * fb:(i0 + len(ri)) * fb].copy_(src.view(-1))
+        dbuf[m] = torch.empty(n * fb, dtype=torch.uint8, device="cuda")
+        tables[m] = scn.scn_table_create(dbuf[m], W, H, T, rows=r.tolist())
+        eseqs[m] = scn.scn_sample(tables[m], scn.SCN_GATHER, indices=r.tolist())
+        outs[m] = (torch.empty((n, 48), dtype=torch.int32, device="cuda"),
+                   torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.uint8, device="cuda"))
+        houts[m] = (torch.empty((n, 48), dtype=torch.int32, pin_memory=True),
+                    torch.empty(n, dtype=torch.int32, pin_memory=True), torch.empty(n, dtype=torch.uint8, pin_memory=True))
+    h2d = sum(host[m].numel() for m, _ in modes)
+    d2h = sum(sum(t.numel() * t.element_size() for t in houts[m]) for m, _ in modes)
+
+    mean, std = (0.485, 0.456, 0.406), (0.229, 0.224, 0.225)
+    rs = {m: (torch.empty((len(rows[m]), 3, 224, 224), dtype=torch.float32, device="cuda"),
+              torch.empty((len(rows[m]), 3, 224, 224), dtype=torch.bfloat16, device="cuda"))
+          for m in ("stride24", "gather1000")}
+
+    def step():
+        for m, _ in modes:
+            dbuf[m].copy_(host[m], non_blocking=True)
+            h, s, f = outs[m]
+            scn.scn_hist_scores(eseqs[m], h, s, f, stream)
+            if m in rs:
+                scn.scn_resize_norm(eseqs[m], 224, 224, mean, std, scn.SCN_F32, rs[m][0], stream)
+                scn.scn_resize_norm(eseqs[m], 224, 224, mean, std, scn.SCN_BF16, rs[m][1], stream)
+            for d, hh in zip(outs[m], houts[m]):
+                hh.copy_(d, non_blocking=True)
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    torch.cuda.synchronize()
+    k = max(2, min(args.steps, 5))
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(k):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / k
+    n_frames = sum(len(rows[m]) for m, _ in modes)
+    for m, _ in modes:
+        scn.scn_seq_destroy(eseqs[m])
+        scn.scn_table_destroy(tables[m])
+    return {"value": n_frames / (ms / 1000), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": k,
+            "note": "same step as the device-resident one; the sampled frames are copied from pinned host "
+                    "memory every step and histograms, scores and flags read back"}
+
+
+if __name__ == "__main__":
+    main()

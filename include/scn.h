@@ -1,0 +1,205 @@
+/*
+ * scn.h - C ABI of the B300 sampled-frame video-analysis library (libscn.so).
+ *
+ * The calls follow the paper's model (Scanner, Poms et al., ACM TOG 37(4) 2018):
+ * a video is a table with one row per frame (Sec. 3, "Videos as logical
+ * tables"); a sampling op selects rows by stride, range or index list
+ * (Sec. 3.2, "Sampling/spacing operations", and the access patterns of
+ * Sec. 5.1.1); map ops run per element (Sec. 3.2, "Maps"); the shot score is a
+ * stencil over two consecutive elements (Sec. 3.2, "Stencil operations") of a
+ * per-frame colour histogram (Sec. 5.1.2, HIST; Sec. 5.2 shot detection from
+ * histogram differences).
+ *
+ * Conventions
+ *  - Every call returns scn_status.  Argument errors are detected on the host,
+ *    before any launch, and nothing is written.  scn_status_str() gives text;
+ *    scn_last_cuda_error() gives the CUDA error code behind SCN_ECUDA.
+ *  - "d_" pointers are device memory owned by the caller (e.g. torch tensors),
+ *    "h_" pointers are host memory.  Opaque handles (scn_video, scn_table,
+ *    scn_seq) are owned by the library and freed by their *_destroy call.
+ *  - A table BORROWS the caller's NV12 device buffer: it must outlive the table
+ *    and every sequence sampled from it.
+ *  - Compute calls are asynchronous on the given stream (a cudaStream_t passed
+ *    as void*, NULL = legacy default stream).  Device-side faults that the
+ *    kernels detect themselves (a bounded wait that ran out) are recorded in the
+ *    sequence's status word, read by scn_seq_sync_status().
+ *  - A sequence carries device scratch (completion counters and per-slice
+ *    partial histograms); two calls on the same sequence must not overlap on
+ *    the GPU (use one stream per sequence).
+ *  - Layouts: NV12 frame = W*H luma bytes then H/2 rows of W interleaved U,V
+ *    bytes; histogram = uint32 [n][3][16] (R, G, B; bin = value >> 4);
+ *    score = uint32 [n]; flag = uint8 [n]; resize output = [n][3][oh][ow].
+ */
+#ifndef SCN_H
+#define SCN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SCN_OK = 0,
+    SCN_EINVAL = 1,        /* bad argument: null pointer, bad size, misalignment */
+    SCN_ERANGE = 2,        /* an index or size outside the table / a buffer */
+    SCN_ENOMEM = 3,        /* host or device allocation failed */
+    SCN_ECUDA = 4,         /* a CUDA runtime call failed (see scn_last_cuda_error) */
+    SCN_ETIMEOUT = 5,      /* a bounded device wait ran out (see scn_seq_sync_status) */
+    SCN_EUNSUPPORTED = 6   /* no usable sm_103 device, or an unsupported request */
+} scn_status;
+
+/* Text for a status code; never NULL. */
+const char* scn_status_str(scn_status s);
+/* The cudaError_t value of the last failing CUDA call made by this thread. */
+int scn_last_cuda_error(void);
+/* Library version string. */
+const char* scn_version(void);
+/* Number of SMs of the current device, or -1 without a device. */
+int scn_device_sm_count(void);
+
+/* ------------------------------------------------------------------------ */
+/* Synthetic video generator (stands in for decoded frames; the paper's     */
+/* compressed-video decode, Sec. 4.3, is out of scope).  SplitMix64 counter */
+/* stream; shots with a base colour, a linear ramp drifting 1 px/frame and  */
+/* Irwin-Hall noise of sigma 8.  The CPU oracle implements the same         */
+/* definition separately; the bytes are checked equal.                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t master_seed;
+    uint64_t video_id;
+    int32_t width, height;   /* even; width % 16 == 0 */
+    int64_t num_frames;      /* >= 1 */
+    int32_t num_shots;       /* shot_mode 0: shots S, 1 <= S <= num_frames */
+    int32_t shot_mode;       /* 0: S-1 uniform boundaries; 1: geometric lengths (p = 1/64, 2..300) */
+} scn_gen_params;
+
+typedef struct {
+    int64_t start;           /* first frame of the shot */
+    int32_t base[3];         /* Y, U, V base levels */
+    int32_t gx[3], gy[3];    /* ramp amplitudes per plane, in [-32, 32] */
+} scn_shot;
+
+typedef struct scn_video scn_video;
+
+/* Host only: the shot table the generator uses for params (no device call).
+ * Writes min(cap, n) shots to h_out and the full count to *n.  Errors:
+ * SCN_EINVAL for bad params. */
+scn_status scn_gen_shots(const scn_gen_params* params, scn_shot* h_out, int64_t cap, int64_t* n);
+
+/* Build the shot table on the host and upload it.  Errors: SCN_EINVAL (bad
+ * params), SCN_ECUDA. */
+scn_status scn_video_create(const scn_gen_params* params, scn_video** out);
+scn_status scn_video_destroy(scn_video* v);
+/* Number of shots; copy of the first min(cap, n) shots into h_out. */
+scn_status scn_video_shots(const scn_video* v, scn_shot* h_out, int64_t cap, int64_t* n);
+/* Default keyframe list: every 104th frame (the paper's average keyframe
+ * distance, Sec. 5.1.1) plus every shot start, ascending.  Writes
+ * min(cap, n) entries into h_out and the full count into *n. */
+scn_status scn_video_keyframes(const scn_video* v, int64_t* h_out, int64_t cap, int64_t* n);
+/* Generate frames first_frame .. first_frame+count-1 into d_out, frame k at
+ * d_out + k*frame_stride (frame_stride >= W*H*3/2, % 16 == 0; d_out 16-byte
+ * aligned).  Asynchronous on stream. */
+scn_status scn_generate(const scn_video* v, uint8_t* d_out, int64_t first_frame, int64_t count,
+                        int64_t frame_stride, void* stream);
+/* Sparse materialisation: generate frame d_frames[k] (device int64 array of n
+ * frame numbers) into d_out + k*frame_stride. */
+scn_status scn_generate_frames(const scn_video* v, const int64_t* d_frames, int64_t n, uint8_t* d_out,
+                               int64_t frame_stride, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Tables and sampling                                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t width, height;        /* even, width % 16 == 0 */
+    int64_t num_frames;           /* logical rows (frames) of the video */
+    int64_t frame_stride;         /* bytes between stored frames, >= W*H*3/2, % 16 == 0 */
+    const uint8_t* d_nv12;        /* device, borrowed, 16-byte aligned */
+    const int64_t* h_rows;        /* optional (NULL = dense): ascending logical frame number of
+                                     each stored frame; only these rows are materialised */
+    int64_t num_rows;             /* entries of h_rows (ignored when h_rows is NULL) */
+    const int64_t* h_keyframes;   /* optional keyframe list (copied, sorted, deduplicated) */
+    int64_t num_keyframes;
+} scn_table_desc;
+
+typedef struct scn_table scn_table;
+typedef struct scn_seq scn_seq;
+
+/* Record a table over the caller's NV12 buffer (host only, no device call).
+ * Errors: SCN_EINVAL for odd sizes, width % 16, stride, alignment, unsorted
+ * h_rows or keyframes outside [0, num_frames). */
+scn_status scn_table_create(const scn_table_desc* desc, scn_table** out);
+scn_status scn_table_destroy(scn_table* t);
+
+typedef enum {
+    SCN_STRIDE = 0,     /* start, start+step, ... < stop */
+    SCN_RANGE = 1,      /* [start, stop) */
+    SCN_GATHER = 2,     /* h_indices[0..n), in the given order, duplicates kept */
+    SCN_KEYFRAME = 3    /* the table's keyframe list */
+} scn_sample_kind;
+
+typedef struct {
+    int32_t kind;                 /* scn_sample_kind */
+    int64_t start, stop, step;    /* STRIDE / RANGE */
+    const int64_t* h_indices;     /* GATHER (host) */
+    int64_t n;                    /* GATHER length */
+} scn_sample_spec;
+
+/* Host-only: the logical frame numbers the spec selects (Sec. 3.2 sampling).
+ * Writes min(cap, n) entries and sets *n.  Errors: SCN_EINVAL (bad kind, step
+ * < 1), SCN_ERANGE (a row outside [0, num_frames) or not materialised). */
+scn_status scn_sample_indices(const scn_table* t, const scn_sample_spec* spec, int64_t* h_out,
+                              int64_t cap, int64_t* n);
+/* Create a sequence: the selected rows' storage slots uploaded to the device
+ * plus the sequence's scratch (allocated here with cudaMalloc, freed by
+ * scn_seq_destroy).  Synchronous. */
+scn_status scn_sample(const scn_table* t, const scn_sample_spec* spec, scn_seq** out);
+scn_status scn_seq_length(const scn_seq* s, int64_t* n);
+scn_status scn_seq_destroy(scn_seq* s);
+/* Synchronise stream, read and clear the sequence's device status word.
+ * Returns SCN_OK or SCN_ETIMEOUT. */
+scn_status scn_seq_sync_status(scn_seq* s, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Launch shape of the fused kernel (chosen by the autotuner when not set). */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t slices;        /* row slices per frame (work items per frame), 1..16 */
+    int32_t chunk_rows;    /* luma rows per staged chunk (even), 0 = largest that fits */
+    int32_t grid;          /* CTAs, 0 = one per SM */
+} scn_tune;
+
+scn_status scn_seq_set_tune(scn_seq* s, const scn_tune* tune);
+scn_status scn_seq_get_tune(const scn_seq* s, scn_tune* tune);
+
+/* ------------------------------------------------------------------------ */
+/* Per-frame ops                                                             */
+/* ------------------------------------------------------------------------ */
+/* d_hist[k] = 3x16-bin histogram of the BT.601 fixed-point RGB of sampled
+ * frame k (R = clamp((298(Y-16) + 409(V-128) + 128) >> 8), G with -100, -208,
+ * B with 516; chroma nearest; bin = v >> 4).  n = 0 writes nothing. */
+scn_status scn_hist(scn_seq* s, uint32_t* d_hist, void* stream);
+/* Shot scores from histograms: d_score[0] = 0, d_score[k] = L1 distance of
+ * hist[k] and hist[k-1]; d_flag[k] = (2*score > pixel_count). */
+scn_status scn_shot_scores(const uint32_t* d_hist, int64_t n, int64_t pixel_count, uint32_t* d_score,
+                           uint8_t* d_flag, void* stream);
+/* Fused: histograms and shot scores of the sequence in one launch. */
+scn_status scn_hist_scores(scn_seq* s, uint32_t* d_hist, uint32_t* d_score, uint8_t* d_flag,
+                           void* stream);
+
+typedef enum { SCN_F32 = 0, SCN_BF16 = 1 } scn_dtype;
+/* Bilinear resize (half-pixel centres, no antialias, stretch) of the RGB
+ * frame to oh x ow, then (v/255 - mean[c]) / std[c]; output [n][3][oh][ow]
+ * in dtype.  mean/std are host arrays of 3. */
+scn_status scn_resize_norm(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean, const float* h_std,
+                           int32_t dtype, void* d_out, void* stream);
+/* Luma thumbnails: d_thumb[k][r][c] = Y[s*r][s*c], s = W/64 = H/36
+ * (requires W == 64*s and H == 36*s); output uint8 [n][36][64]. */
+scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCN_H */

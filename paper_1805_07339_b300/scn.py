@@ -1,0 +1,279 @@
+"""ctypes binding of libscn.so (include/scn.h).  Argument marshalling only.
+
+The functions keep the C names.  Device buffers are torch CUDA tensors passed
+by pointer; streams default to torch's current stream.  Every compute step runs
+in libscn's CUDA kernels; there is no CPU path here: if the library cannot be
+built or loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_i32, c_i64, c_u64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
+
+SCN_OK, SCN_EINVAL, SCN_ERANGE, SCN_ENOMEM, SCN_ECUDA, SCN_ETIMEOUT, SCN_EUNSUPPORTED = range(7)
+SCN_STRIDE, SCN_RANGE, SCN_GATHER, SCN_KEYFRAME = range(4)
+SCN_F32, SCN_BF16 = 0, 1
+
+
+class ScnError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.scn_status_str(status).decode()
+        if status == SCN_ECUDA:
+            msg += f" (cudaError {_lib.scn_last_cuda_error()})"
+        super().__init__(f"{where}: {msg} [{status}]")
+
+
+class scn_gen_params(ctypes.Structure):
+    _fields_ = [("master_seed", c_u64), ("video_id", c_u64), ("width", c_i32), ("height", c_i32),
+                ("num_frames", c_i64), ("num_shots", c_i32), ("shot_mode", c_i32)]
+
+
+class scn_shot(ctypes.Structure):
+    _fields_ = [("start", c_i64), ("base", c_i32 * 3), ("gx", c_i32 * 3), ("gy", c_i32 * 3)]
+
+
+class scn_table_desc(ctypes.Structure):
+    _fields_ = [("width", c_i32), ("height", c_i32), ("num_frames", c_i64), ("frame_stride", c_i64),
+                ("d_nv12", c_vp), ("h_rows", ctypes.POINTER(c_i64)), ("num_rows", c_i64),
+                ("h_keyframes", ctypes.POINTER(c_i64)), ("num_keyframes", c_i64)]
+
+
+class scn_sample_spec(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("start", c_i64), ("stop", c_i64), ("step", c_i64),
+                ("h_indices", ctypes.POINTER(c_i64)), ("n", c_i64)]
+
+
+class scn_tune(ctypes.Structure):
+    _fields_ = [("slices", c_i32), ("chunk_rows", c_i32), ("grid", c_i32)]
+
+
+# (name, restype, argtypes) of every exported symbol declared in include/scn.h
+_P = ctypes.POINTER
+SIGNATURES = [
+    ("scn_status_str", ctypes.c_char_p, [c_i32]),
+    ("scn_last_cuda_error", c_i32, []),
+    ("scn_version", ctypes.c_char_p, []),
+    ("scn_device_sm_count", c_i32, []),
+    ("scn_gen_shots", c_i32, [_P(scn_gen_params), _P(scn_shot), c_i64, _P(c_i64)]),
+    ("scn_video_create", c_i32, [_P(scn_gen_params), _P(c_vp)]),
+    ("scn_video_destroy", c_i32, [c_vp]),
+    ("scn_video_shots", c_i32, [c_vp, _P(scn_shot), c_i64, _P(c_i64)]),
+    ("scn_video_keyframes", c_i32, [c_vp, _P(c_i64), c_i64, _P(c_i64)]),
+    ("scn_generate", c_i32, [c_vp, c_vp, c_i64, c_i64, c_i64, c_vp]),
+    ("scn_generate_frames", c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, c_vp]),
+    ("scn_table_create", c_i32, [_P(scn_table_desc), _P(c_vp)]),
+    ("scn_table_destroy", c_i32, [c_vp]),
+    ("scn_sample_indices", c_i32, [c_vp, _P(scn_sample_spec), _P(c_i64), c_i64, _P(c_i64)]),
+    ("scn_sample", c_i32, [c_vp, _P(scn_sample_spec), _P(c_vp)]),
+    ("scn_seq_length", c_i32, [c_vp, _P(c_i64)]),
+    ("scn_seq_destroy", c_i32, [c_vp]),
+    ("scn_seq_sync_status", c_i32, [c_vp, c_vp]),
+    ("scn_seq_set_tune", c_i32, [c_vp, _P(scn_tune)]),
+    ("scn_seq_get_tune", c_i32, [c_vp, _P(scn_tune)]),
+    ("scn_hist", c_i32, [c_vp, c_vp, c_vp]),
+    ("scn_shot_scores", c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
+    ("scn_hist_scores", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    ("scn_resize_norm", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_i32, c_vp, c_vp]),
+    ("scn_thumbs", c_i32, [c_vp, c_vp, c_vp]),
+]
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != SCN_OK:
+        raise ScnError(status, where)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _i64_array(values):
+    vals = [int(v) for v in values]
+    arr = (c_i64 * max(len(vals), 1))(*vals)
+    return arr, len(vals)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+# --------------------------------------------------------------------------- thin wrappers
+def scn_version() -> str:
+    return _lib.scn_version().decode()
+
+
+def scn_device_sm_count() -> int:
+    return int(_lib.scn_device_sm_count())
+
+
+def _shots_list(arr, n):
+    return [dict(start=s.start, base=list(s.base), gx=list(s.gx), gy=list(s.gy)) for s in arr[:n]]
+
+
+def scn_gen_shots(master_seed: int, video_id: int, width: int, height: int, num_frames: int,
+                  num_shots: int = 1, shot_mode: int = 0) -> list[dict]:
+    p = scn_gen_params(master_seed, video_id, width, height, num_frames, num_shots, shot_mode)
+    n = c_i64()
+    _check(_lib.scn_gen_shots(ctypes.byref(p), None, 0, ctypes.byref(n)), "scn_gen_shots")
+    arr = (scn_shot * max(n.value, 1))()
+    _check(_lib.scn_gen_shots(ctypes.byref(p), arr, n.value, ctypes.byref(n)), "scn_gen_shots")
+    return _shots_list(arr, n.value)
+
+
+def scn_video_create(master_seed: int, video_id: int, width: int, height: int, num_frames: int,
+                     num_shots: int = 1, shot_mode: int = 0) -> int:
+    p = scn_gen_params(master_seed, video_id, width, height, num_frames, num_shots, shot_mode)
+    h = c_vp()
+    _check(_lib.scn_video_create(ctypes.byref(p), ctypes.byref(h)), "scn_video_create")
+    return h.value
+
+
+def scn_video_destroy(v: int) -> None:
+    _check(_lib.scn_video_destroy(v), "scn_video_destroy")
+
+
+def scn_video_shots(v: int) -> list[dict]:
+    n = c_i64()
+    _check(_lib.scn_video_shots(v, None, 0, ctypes.byref(n)), "scn_video_shots")
+    arr = (scn_shot * max(n.value, 1))()
+    _check(_lib.scn_video_shots(v, arr, n.value, ctypes.byref(n)), "scn_video_shots")
+    return _shots_list(arr, n.value)
+
+
+def scn_video_keyframes(v: int) -> list[int]:
+    n = c_i64()
+    _check(_lib.scn_video_keyframes(v, None, 0, ctypes.byref(n)), "scn_video_keyframes")
+    arr = (c_i64 * max(n.value, 1))()
+    _check(_lib.scn_video_keyframes(v, arr, n.value, ctypes.byref(n)), "scn_video_keyframes")
+    return list(arr[: n.value])
+
+
+def scn_generate(v: int, out, first_frame: int, count: int, frame_stride: int, stream=None) -> None:
+    _check(_lib.scn_generate(v, _ptr(out), first_frame, count, frame_stride, _stream(stream)), "scn_generate")
+
+
+def scn_generate_frames(v: int, frames, out, frame_stride: int, stream=None) -> None:
+    _check(_lib.scn_generate_frames(v, _ptr(frames), frames.numel(), _ptr(out), frame_stride, _stream(stream)),
+           "scn_generate_frames")
+
+
+def scn_table_create(nv12, width: int, height: int, num_frames: int, frame_stride: int | None = None,
+                     rows=None, keyframes=None, d_nv12: int | None = None) -> int:
+    """nv12: a CUDA uint8 tensor (or pass d_nv12 as a raw device address)."""
+    if frame_stride is None:
+        frame_stride = width * height * 3 // 2
+    rows_arr, nrows = _i64_array(rows) if rows is not None else (None, 0)
+    kf_arr, nkf = _i64_array(keyframes) if keyframes is not None else (None, 0)
+    d = scn_table_desc(width, height, num_frames, frame_stride, d_nv12 if d_nv12 is not None else _ptr(nv12),
+                       rows_arr, nrows, kf_arr, nkf)
+    h = c_vp()
+    _check(_lib.scn_table_create(ctypes.byref(d), ctypes.byref(h)), "scn_table_create")
+    return h.value
+
+
+def scn_table_destroy(t: int) -> None:
+    _check(_lib.scn_table_destroy(t), "scn_table_destroy")
+
+
+def _spec(kind: int, start: int = 0, stop: int = 0, step: int = 1, indices=None):
+    if indices is not None:
+        arr, n = _i64_array(indices)
+    else:
+        arr, n = None, 0
+    return scn_sample_spec(kind, start, stop, step, arr, n), arr
+
+
+def scn_sample_indices(t: int, kind: int, start: int = 0, stop: int = 0, step: int = 1, indices=None) -> list[int]:
+    sp, keep = _spec(kind, start, stop, step, indices)
+    n = c_i64()
+    _check(_lib.scn_sample_indices(t, ctypes.byref(sp), None, 0, ctypes.byref(n)), "scn_sample_indices")
+    out = (c_i64 * max(n.value, 1))()
+    _check(_lib.scn_sample_indices(t, ctypes.byref(sp), out, n.value, ctypes.byref(n)), "scn_sample_indices")
+    del keep
+    return list(out[: n.value])
+
+
+def scn_sample(t: int, kind: int, start: int = 0, stop: int = 0, step: int = 1, indices=None) -> int:
+    sp, keep = _spec(kind, start, stop, step, indices)
+    h = c_vp()
+    _check(_lib.scn_sample(t, ctypes.byref(sp), ctypes.byref(h)), "scn_sample")
+    del keep
+    return h.value
+
+
+def scn_seq_length(s: int) -> int:
+    n = c_i64()
+    _check(_lib.scn_seq_length(s, ctypes.byref(n)), "scn_seq_length")
+    return n.value
+
+
+def scn_seq_destroy(s: int) -> None:
+    _check(_lib.scn_seq_destroy(s), "scn_seq_destroy")
+
+
+def scn_seq_sync_status(s: int, stream=None) -> int:
+    return int(_lib.scn_seq_sync_status(s, _stream(stream)))
+
+
+def scn_seq_set_tune(s: int, slices: int = 0, chunk_rows: int = 0, grid: int = 0) -> None:
+    t = scn_tune(slices, chunk_rows, grid)
+    _check(_lib.scn_seq_set_tune(s, ctypes.byref(t)), "scn_seq_set_tune")
+
+
+def scn_seq_get_tune(s: int) -> dict:
+    t = scn_tune()
+    _check(_lib.scn_seq_get_tune(s, ctypes.byref(t)), "scn_seq_get_tune")
+    return dict(slices=t.slices, chunk_rows=t.chunk_rows, grid=t.grid)
+
+
+def scn_hist(s: int, hist, stream=None) -> None:
+    _check(_lib.scn_hist(s, _ptr(hist), _stream(stream)), "scn_hist")
+
+
+def scn_hist_scores(s: int, hist, score, flag, stream=None) -> None:
+    _check(_lib.scn_hist_scores(s, _ptr(hist), _ptr(score), _ptr(flag), _stream(stream)), "scn_hist_scores")
+
+
+def scn_shot_scores(hist, n: int, pixel_count: int, score, flag, stream=None) -> None:
+    _check(_lib.scn_shot_scores(_ptr(hist), n, pixel_count, _ptr(score), _ptr(flag), _stream(stream)),
+           "scn_shot_scores")
+
+
+def scn_resize_norm(s: int, oh: int, ow: int, mean, std, dtype: int, out, stream=None) -> None:
+    m = (ctypes.c_float * 3)(*[float(x) for x in mean])
+    sd = (ctypes.c_float * 3)(*[float(x) for x in std])
+    _check(_lib.scn_resize_norm(s, oh, ow, m, sd, dtype, _ptr(out), _stream(stream)), "scn_resize_norm")
+
+
+def scn_thumbs(s: int, thumb, stream=None) -> None:
+    _check(_lib.scn_thumbs(s, _ptr(thumb), _stream(stream)), "scn_thumbs")

@@ -1,0 +1,38 @@
+"""Seeded synthetic workloads: sizes, seeds and raw random inputs.
+
+Holds no arithmetic of the method (no conversion, binning, scoring or
+resampling).  The CUDA path, the tests and the benchmark take their inputs from
+here; video frames themselves come from each side's own generator.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+MASTER_SEED = 20180805
+
+# 1 synthetic 320x180 video, 240 frames, 8 shots, stride-1
+TINY = dict(width=320, height=180, num_frames=240, num_shots=8)
+# 1 synthetic 1920x1080 video, 7200 frames (22.4 GB of NV12), 60 shots
+HD = dict(width=1920, height=1080, num_frames=7200, num_shots=60)
+HD_GATHER = 1000          # gathered frames of the 1080p video
+HD_STRIDE = 24            # sparse stride of the 1080p video
+HD_GATHER_SEED = 1000     # numpy seed of the gather list
+
+
+def random_nv12(seed: int, n: int, width: int, height: int) -> np.ndarray:
+    """n frames of uniformly random bytes (exercises every clamp and bin)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 256, (n, width * height * 3 // 2), dtype=np.uint8)
+
+
+def random_indices(seed: int, num_frames: int, m: int, distinct: bool = True) -> np.ndarray:
+    """m frame numbers in [0, num_frames): distinct and sorted, or i.i.d. in draw order."""
+    rng = np.random.default_rng(seed)
+    if distinct:
+        return np.sort(rng.choice(num_frames, size=m, replace=False)).astype(np.int64)
+    return rng.integers(0, num_frames, m).astype(np.int64)
+
+
+def hd_gather() -> np.ndarray:
+    """The 1080p gather list: 1000 distinct sorted frames of 7200."""
+    return random_indices(HD_GATHER_SEED, HD["num_frames"], HD_GATHER)

@@ -1,0 +1,373 @@
+"""GPU parity: libscn's kernels against the CPU oracle, through the C ABI.
+
+Integer outputs (generator bytes, histograms, scores, flags, thumbnails) must be
+bit-exact.  The FP32 resize must be within 1e-4 abs of the fp64 oracle; the BF16
+resize must equal round-to-nearest-even of the kernel's own FP32 value and lie
+within one BF16 ulp (plus the FP32 tolerance) of the fp64 oracle rounded to BF16.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from tests.inputs import HD, MASTER_SEED, TINY, hd_gather, random_indices, random_nv12  # noqa: E402
+
+RESIZE_TOL = 1e-4
+MEAN, STD = (0.485, 0.456, 0.406), (0.229, 0.224, 0.225)
+
+
+@pytest.fixture(scope="module")
+def scn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_07339_b300 import scn as s
+    return s
+
+
+class Dev:
+    """A device-resident table over a uint8 CUDA tensor of frames."""
+
+    def __init__(self, scn, frames_u8, W, H, T, rows=None, keyframes=None):
+        self.scn, self.W, self.H, self.T = scn, W, H, T
+        self.buf = frames_u8
+        self.fb = W * H * 3 // 2
+        self.table = scn.scn_table_create(self.buf, W, H, T, rows=rows, keyframes=keyframes)
+
+    def seq(self, kind, **kw):
+        return self.scn.scn_sample(self.table, kind, **kw)
+
+    def hist_scores(self, seq, tune=None):
+        scn = self.scn
+        n = scn.scn_seq_length(seq)
+        if tune:
+            scn.scn_seq_set_tune(seq, **tune)
+        h = torch.full((max(n, 1), 48), 0xDEAD, dtype=torch.int32, device="cuda")
+        s = torch.full((max(n, 1),), 0xBEEF, dtype=torch.int32, device="cuda")
+        f = torch.full((max(n, 1),), 7, dtype=torch.uint8, device="cuda")
+        scn.scn_hist_scores(seq, h, s, f)
+        assert scn.scn_seq_sync_status(seq) == scn.SCN_OK
+        return (h[:n].cpu().numpy().view(np.uint32).reshape(n, 3, 16), s[:n].cpu().numpy().view(np.uint32),
+                f[:n].cpu().numpy())
+
+    def close(self):
+        self.scn.scn_table_destroy(self.table)
+
+
+def _video(scn, cfg, vid=0):
+    return scn.scn_video_create(MASTER_SEED, vid, cfg["width"], cfg["height"], cfg["num_frames"], cfg["num_shots"])
+
+
+def _generate(scn, v, W, H, T):
+    fb = W * H * 3 // 2
+    buf = torch.empty(T * fb, dtype=torch.uint8, device="cuda")
+    scn.scn_generate(v, buf, 0, T, fb)
+    torch.cuda.synchronize()
+    return buf
+
+
+# --------------------------------------------------------------------------- generator
+def test_generator_bytes_tiny_all_frames(scn, orc):
+    W, H, T = TINY["width"], TINY["height"], TINY["num_frames"]
+    v = _video(scn, TINY)
+    try:
+        buf = _generate(scn, v, W, H, T)
+        ref = orc.Video(MASTER_SEED, 0, W, H, T, TINY["num_shots"]).frames(range(T), nthreads=8)
+        got = buf.cpu().numpy().reshape(T, -1)
+        assert np.array_equal(got, ref)
+    finally:
+        scn.scn_video_destroy(v)
+
+
+def test_generator_sparse_frames_hd_and_geometric(scn, orc):
+    cases = [(HD, 0, 1), (dict(width=640, height=360, num_frames=54000, num_shots=0), 5, 1)]
+    for cfg, vid, mode in cases:
+        W, H, T = cfg["width"], cfg["height"], cfg["num_frames"]
+        if cfg["num_shots"] == 0:
+            v = scn.scn_video_create(MASTER_SEED, vid, W, H, T, 0, 1)
+            oref = orc.Video(MASTER_SEED, vid, W, H, T, 0, 1)
+        else:
+            v = scn.scn_video_create(MASTER_SEED, vid, W, H, T, cfg["num_shots"])
+            oref = orc.Video(MASTER_SEED, vid, W, H, T, cfg["num_shots"])
+        try:
+            frames = np.array([0, 1, T // 3, T // 2 + 1, T - 2, T - 1], dtype=np.int64)
+            fb = W * H * 3 // 2
+            out = torch.empty(len(frames) * fb, dtype=torch.uint8, device="cuda")
+            scn.scn_generate_frames(v, torch.from_numpy(frames).cuda(), out, fb)
+            got = out.cpu().numpy().reshape(len(frames), fb)
+            assert np.array_equal(got, oref.frames(frames, nthreads=6))
+        finally:
+            scn.scn_video_destroy(v)
+
+
+# --------------------------------------------------------------------------- hist + scores
+def _oracle_hs(orc, frames_np, W, H, idx):
+    h = orc.hist_batch(frames_np, W, H, idx=idx, nthreads=8)
+    s, f = orc.scores(h, W * H)
+    return h, s, f
+
+
+def test_hist_scores_tiny_stride1_bit_exact(scn, orc):
+    W, H, T = TINY["width"], TINY["height"], TINY["num_frames"]
+    v = _video(scn, TINY)
+    ref_frames = orc.Video(MASTER_SEED, 0, W, H, T, TINY["num_shots"]).frames(range(T), nthreads=8)
+    dev = Dev(scn, _generate(scn, v, W, H, T), W, H, T)
+    try:
+        seq = dev.seq(scn.SCN_STRIDE, start=0, stop=T, step=1)
+        h, s, f = dev.hist_scores(seq)
+        rh, rs, rf = _oracle_hs(orc, ref_frames, W, H, np.arange(T))
+        assert np.array_equal(h, rh)
+        assert np.array_equal(s, rs)
+        assert np.array_equal(f, rf)
+        assert f.sum() >= 1  # the generator's shots are visible
+        # hist-only entry point and the standalone score kernel agree
+        h2 = torch.zeros((T, 48), dtype=torch.int32, device="cuda")
+        scn.scn_hist(seq, h2)
+        s2 = torch.zeros(T, dtype=torch.int32, device="cuda")
+        f2 = torch.zeros(T, dtype=torch.uint8, device="cuda")
+        scn.scn_shot_scores(h2, T, W * H, s2, f2)
+        assert np.array_equal(h2.cpu().numpy().view(np.uint32).reshape(T, 3, 16), rh)
+        assert np.array_equal(s2.cpu().numpy().view(np.uint32), rs)
+        assert np.array_equal(f2.cpu().numpy(), rf)
+        scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+        scn.scn_video_destroy(v)
+
+
+@pytest.mark.parametrize("W,H,n", [(320, 180, 16), (1920, 1080, 3), (16, 2, 9), (48, 6, 5), (1936, 1090, 2),
+                                   (3840, 2160, 2), (640, 360, 33)])
+def test_hist_random_bytes_bit_exact(scn, orc, W, H, n):
+    frames = random_nv12(W * 7 + H, n, W, H)
+    buf = torch.from_numpy(frames.reshape(-1)).cuda()
+    dev = Dev(scn, buf, W, H, n)
+    try:
+        order = random_indices(n, n, 2 * n, distinct=False)
+        seq = dev.seq(scn.SCN_GATHER, indices=order.tolist())
+        h, s, f = dev.hist_scores(seq)
+        rh, rs, rf = _oracle_hs(orc, frames, W, H, order)
+        assert np.array_equal(h, rh)
+        assert np.array_equal(s, rs)
+        assert np.array_equal(f, rf)
+        scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+
+
+@pytest.mark.parametrize("tune", [dict(slices=1), dict(slices=2), dict(slices=3, chunk_rows=6),
+                                  dict(slices=16, chunk_rows=2), dict(slices=7, grid=1), dict(slices=5, grid=3),
+                                  dict(chunk_rows=4, grid=2)])
+def test_hist_launch_shapes_agree(scn, orc, tune):
+    W, H, n = 640, 360, 12
+    frames = random_nv12(99, n, W, H)
+    dev = Dev(scn, torch.from_numpy(frames.reshape(-1)).cuda(), W, H, n)
+    try:
+        seq = dev.seq(scn.SCN_RANGE, start=0, stop=n)
+        h, s, f = dev.hist_scores(seq, tune=tune)
+        rh, rs, rf = _oracle_hs(orc, frames, W, H, np.arange(n))
+        assert np.array_equal(h, rh) and np.array_equal(s, rs) and np.array_equal(f, rf)
+        # a second call on the same sequence (counters reset themselves)
+        h2, s2, f2 = dev.hist_scores(seq)
+        assert np.array_equal(h2, rh) and np.array_equal(s2, rs)
+        scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+
+
+def test_edge_cases(scn, orc):
+    W, H, T = 64, 36, 6
+    frames = random_nv12(5, T, W, H)
+    dev = Dev(scn, torch.from_numpy(frames.reshape(-1)).cuda(), W, H, T, keyframes=[0, 4])
+    try:
+        empty = dev.seq(scn.SCN_STRIDE, start=3, stop=3, step=1)
+        assert scn.scn_seq_length(empty) == 0
+        h = torch.zeros(1, dtype=torch.int32, device="cuda")
+        scn.scn_hist_scores(empty, h, h, torch.zeros(1, dtype=torch.uint8, device="cuda"))
+        scn.scn_seq_destroy(empty)
+        one = dev.seq(scn.SCN_GATHER, indices=[2])
+        hh, s, f = dev.hist_scores(one)
+        assert np.array_equal(hh, orc.hist_frame(frames[2], W, H)[None])
+        assert s.tolist() == [0] and f.tolist() == [0]
+        scn.scn_seq_destroy(one)
+        dup = dev.seq(scn.SCN_GATHER, indices=[1, 1, 1, 5, 5])
+        hh, s, f = dev.hist_scores(dup)
+        assert s[1] == 0 and s[2] == 0 and s[4] == 0 and s[3] > 0
+        scn.scn_seq_destroy(dup)
+        kf = dev.seq(scn.SCN_KEYFRAME)
+        hh, s, f = dev.hist_scores(kf)
+        rh, rs, rf = _oracle_hs(orc, frames, W, H, np.array([0, 4]))
+        assert np.array_equal(hh, rh) and np.array_equal(s, rs)
+        scn.scn_seq_destroy(kf)
+    finally:
+        dev.close()
+
+
+def test_sampling_invariance_and_sparse_table(scn, orc):
+    # the same frame gives the same histogram whichever sampling reaches it, and
+    # a table that stores only some rows (strided storage) gives the same answers
+    W, H, T = 320, 180, 96
+    v = scn.scn_video_create(MASTER_SEED, 3, W, H, T, 5)
+    try:
+        buf = _generate(scn, v, W, H, T)
+        dev = Dev(scn, buf, W, H, T)
+        s1 = dev.seq(scn.SCN_STRIDE, start=0, stop=T, step=1)
+        s24 = dev.seq(scn.SCN_STRIDE, start=0, stop=T, step=24)
+        g = dev.seq(scn.SCN_GATHER, indices=[72, 24, 48])
+        h1, _, _ = dev.hist_scores(s1)
+        h24, _, _ = dev.hist_scores(s24)
+        hg, _, _ = dev.hist_scores(g)
+        assert np.array_equal(h24, h1[0::24])
+        assert np.array_equal(hg, h1[[72, 24, 48]])
+        rows = list(range(0, T, 24))
+        sparse = torch.empty(len(rows) * dev.fb, dtype=torch.uint8, device="cuda")
+        scn.scn_generate_frames(v, torch.tensor(rows, dtype=torch.int64, device="cuda"), sparse, dev.fb)
+        sdev = Dev(scn, sparse, W, H, T, rows=rows)
+        ss = sdev.seq(scn.SCN_STRIDE, start=0, stop=T, step=24)
+        hs, sc, fl = sdev.hist_scores(ss)
+        assert np.array_equal(hs, h24)
+        for q in (s1, s24, g, ss):
+            scn.scn_seq_destroy(q)
+        sdev.close()
+        dev.close()
+    finally:
+        scn.scn_video_destroy(v)
+
+
+@pytest.fixture(scope="module")
+def hd_video(scn):
+    """The full 1080p workload: 7200 frames (22.4 GB) generated on the device."""
+    W, H, T = HD["width"], HD["height"], HD["num_frames"]
+    v = _video(scn, HD)
+    buf = _generate(scn, v, W, H, T)
+    yield v, buf
+    scn.scn_video_destroy(v)
+    del buf
+    torch.cuda.empty_cache()
+
+
+def test_hd_full_size_sampled_parity(scn, orc, hd_video):
+    """Full-size 1080p, the three sampling modes, default (bench) launch shape.
+    Sampled elements are checked against the oracle one by one; every element is
+    checked for histogram mass and for score consistency with its histograms."""
+    v, buf = hd_video
+    W, H, T = HD["width"], HD["height"], HD["num_frames"]
+    dev = Dev(scn, buf, W, H, T)
+    ovid = orc.Video(MASTER_SEED, 0, W, H, T, HD["num_shots"])
+    gather = hd_gather()
+    try:
+        for kind, kw in [(scn.SCN_STRIDE, dict(start=0, stop=T, step=1)),
+                         (scn.SCN_STRIDE, dict(start=0, stop=T, step=24)),
+                         (scn.SCN_GATHER, dict(indices=gather.tolist()))]:
+            idx = np.array(scn.scn_sample_indices(dev.table, kind, **kw))
+            seq = dev.seq(kind, **kw)
+            h, s, f = dev.hist_scores(seq)
+            n = len(idx)
+            assert np.all(h.sum(axis=2) == W * H)
+            hs = h.reshape(n, 48).astype(np.int64)
+            l1 = np.abs(np.diff(hs, axis=0)).sum(axis=1)
+            assert np.array_equal(s[1:], l1) and s[0] == 0
+            assert np.array_equal(f, (2 * s.astype(np.int64) > W * H).astype(np.uint8))
+            pick = sorted(set([1, n // 2, n - 1] + random_indices(kind + 7, n, 5).tolist()) - {0})
+            need = sorted(set(pick) | {p - 1 for p in pick})
+            ref_frames = ovid.frames(idx[need], nthreads=8)
+            rh = orc.hist_batch(ref_frames, W, H, nthreads=8)
+            pos = {k: i for i, k in enumerate(need)}
+            for k in pick:
+                assert np.array_equal(h[k], rh[pos[k]])
+                rs, rf = orc.scores(np.stack([rh[pos[k - 1]], rh[pos[k]]]), W * H)
+                assert s[k] == rs[1] and f[k] == rf[1]
+            scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+
+
+# --------------------------------------------------------------------------- resize + thumbnails
+def _bf16_rne(x: np.ndarray) -> np.ndarray:
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+@pytest.mark.parametrize("W,H,oh,ow,n", [(320, 180, 224, 224, 4), (1920, 1080, 224, 224, 2), (640, 360, 17, 31, 3),
+                                         (64, 36, 224, 224, 2), (3840, 2160, 224, 224, 1)])
+def test_resize_norm_parity(scn, orc, W, H, oh, ow, n):
+    frames = random_nv12(W + oh, n, W, H)
+    dev = Dev(scn, torch.from_numpy(frames.reshape(-1)).cuda(), W, H, n)
+    try:
+        seq = dev.seq(scn.SCN_RANGE, start=0, stop=n)
+        o32 = torch.empty((n, 3, oh, ow), dtype=torch.float32, device="cuda")
+        o16 = torch.empty((n, 3, oh, ow), dtype=torch.bfloat16, device="cuda")
+        scn.scn_resize_norm(seq, oh, ow, MEAN, STD, scn.SCN_F32, o32)
+        scn.scn_resize_norm(seq, oh, ow, MEAN, STD, scn.SCN_BF16, o16)
+        g32 = o32.cpu().numpy()
+        g16 = o16.float().cpu().numpy()
+        for k in range(n):
+            ref = orc.resize_norm_frame(frames[k], W, H, oh, ow, MEAN, STD)
+            assert np.abs(g32[k] - ref).max() <= RESIZE_TOL
+            assert np.array_equal(g16[k], _bf16_rne(g32[k]))
+            r16 = _bf16_rne(ref)
+            mag = np.maximum(np.abs(r16), 2.0 ** -120)
+            ulp = 2.0 ** (np.floor(np.log2(mag)) - 7)
+            # within one BF16 ulp of the rounded fp64 value, plus the FP32 tolerance
+            # (near zero a BF16 ulp is finer than the FP32 error bound)
+            assert np.all(np.abs(g16[k] - r16) <= ulp + RESIZE_TOL)
+        scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+
+
+def test_resize_generator_frames_tiny(scn, orc):
+    W, H, T = TINY["width"], TINY["height"], TINY["num_frames"]
+    v = _video(scn, TINY)
+    try:
+        dev = Dev(scn, _generate(scn, v, W, H, T), W, H, T)
+        idx = [0, 100, 239]
+        seq = dev.seq(scn.SCN_GATHER, indices=idx)
+        out = torch.empty((3, 3, 224, 224), dtype=torch.float32, device="cuda")
+        scn.scn_resize_norm(seq, 224, 224, MEAN, STD, scn.SCN_F32, out)
+        ref_frames = orc.Video(MASTER_SEED, 0, W, H, T, TINY["num_shots"]).frames(idx)
+        for k in range(3):
+            ref = orc.resize_norm_frame(ref_frames[k], W, H, 224, 224, MEAN, STD)
+            assert np.abs(out[k].cpu().numpy() - ref).max() <= RESIZE_TOL
+        scn.scn_seq_destroy(seq)
+        dev.close()
+    finally:
+        scn.scn_video_destroy(v)
+
+
+@pytest.mark.parametrize("W,H", [(320, 180), (640, 360), (1920, 1080), (3840, 2160)])
+def test_thumbs_parity(scn, orc, W, H):
+    n = 3
+    frames = random_nv12(W, n, W, H)
+    dev = Dev(scn, torch.from_numpy(frames.reshape(-1)).cuda(), W, H, n)
+    try:
+        seq = dev.seq(scn.SCN_GATHER, indices=[2, 0, 1])
+        out = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
+        scn.scn_thumbs(seq, out)
+        got = out.cpu().numpy()
+        for j, k in enumerate([2, 0, 1]):
+            assert np.array_equal(got[j], orc.thumb_frame(frames[k], W, H))
+        scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+
+
+def test_argument_errors_before_launch(scn):
+    W, H, n = 64, 36, 2
+    buf = torch.zeros(n * W * H * 3 // 2, dtype=torch.uint8, device="cuda")
+    dev = Dev(scn, buf, W, H, n)
+    try:
+        seq = dev.seq(scn.SCN_RANGE, start=0, stop=n)
+        with pytest.raises(scn.ScnError):
+            scn.scn_hist_scores(seq, None, None, None)
+        odd = torch.zeros(100, dtype=torch.uint8, device="cuda")
+        with pytest.raises(scn.ScnError):
+            scn.scn_hist(seq, odd[1:])  # misaligned histogram pointer
+        with pytest.raises(scn.ScnError):
+            scn.scn_resize_norm(seq, 0, 224, MEAN, STD, scn.SCN_F32, odd)
+        with pytest.raises(scn.ScnError):
+            scn.scn_resize_norm(seq, 224, 224, MEAN, (0.2, 0.0, 0.2), scn.SCN_F32, odd)
+        with pytest.raises(scn.ScnError):
+            scn.scn_seq_set_tune(seq, slices=99)
+        scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
