@@ -23,9 +23,9 @@
  *    as void*, NULL = legacy default stream).  Device-side faults that the
  *    kernels detect themselves (a bounded wait that ran out) are recorded in the
  *    sequence's status word, read by scn_seq_sync_status().
- *  - A sequence carries device scratch (completion counters and per-slice
- *    partial histograms); two calls on the same sequence must not overlap on
- *    the GPU (use one stream per sequence).
+ *  - A sequence carries device scratch (completion counters and cross-CTA
+ *    partial histograms, left zeroed by every call); two calls on the same
+ *    sequence must not overlap on the GPU (use one stream per sequence).
  *  - Layouts: NV12 frame = W*H luma bytes then H/2 rows of W interleaved U,V
  *    bytes; histogram = uint32 [n][3][16] (R, G, B; bin = value >> 4);
  *    score = uint32 [n]; flag = uint8 [n]; resize output = [n][3][oh][ow].
@@ -162,12 +162,12 @@ scn_status scn_seq_destroy(scn_seq* s);
 scn_status scn_seq_sync_status(scn_seq* s, void* stream);
 
 /* ------------------------------------------------------------------------ */
-/* Launch shape of the fused kernel (chosen by the autotuner when not set). */
+/* Launch shape of the fused kernel (chosen automatically when a field is 0). */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int32_t slices;        /* row slices per frame (work items per frame), 1..16 */
     int32_t chunk_rows;    /* luma rows per staged chunk (even), 0 = largest that fits */
-    int32_t grid;          /* CTAs, 0 = one per SM */
+    int32_t grid;          /* CTAs (one per SM at most is resident), 0 = one per SM */
+    int32_t reserved;      /* must be 0 */
 } scn_tune;
 
 scn_status scn_seq_set_tune(scn_seq* s, const scn_tune* tune);

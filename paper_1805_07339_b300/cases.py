@@ -1,0 +1,60 @@
+"""Small, self-contained runs of single kernels, for profiling with ncu.
+
+    python -m paper_1805_07339_b300.cases hist --frames 512 --reps 3
+runs the fused hist+score kernel over the first `frames` frames of a 1080p
+video generated on the device, `reps` times.  Sizes stay a few GB so that a
+profiler capture ends by itself.
+"""
+from __future__ import annotations
+
+import argparse
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("kernel", choices=["hist", "resize", "thumbs"])
+    ap.add_argument("--frames", type=int, default=512)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--stride", type=int, default=1)
+    ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--chunk-rows", type=int, default=0)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    a = ap.parse_args()
+    import torch
+    from . import scn
+    from .workloads import MASTER_SEED
+    W, H, T = a.width, a.height, a.frames
+    fb = W * H * 3 // 2
+    v = scn.scn_video_create(MASTER_SEED, 0, W, H, T, max(1, T // 120))
+    buf = torch.empty(T * fb, dtype=torch.uint8, device="cuda")
+    scn.scn_generate(v, buf, 0, T, fb)
+    t = scn.scn_table_create(buf, W, H, T)
+    seq = scn.scn_sample(t, scn.SCN_STRIDE, start=0, stop=T, step=a.stride)
+    n = scn.scn_seq_length(seq)
+    if a.grid or a.chunk_rows:
+        scn.scn_seq_set_tune(seq, chunk_rows=a.chunk_rows, grid=a.grid)
+    if a.kernel == "hist":
+        h = torch.empty((n, 48), dtype=torch.int32, device="cuda")
+        s = torch.empty(n, dtype=torch.int32, device="cuda")
+        f = torch.empty(n, dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_hist_scores(seq, h, s, f)
+    elif a.kernel == "resize":
+        o = torch.empty((n, 3, 224, 224), dtype=torch.float32, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_resize_norm(seq, 224, 224, (0.485, 0.456, 0.406), (0.229, 0.224, 0.225), scn.SCN_F32, o)
+    else:
+        o = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_thumbs(seq, o)
+    torch.cuda.synchronize()
+    assert scn.scn_seq_sync_status(seq) == scn.SCN_OK
+    scn.scn_seq_destroy(seq)
+    scn.scn_table_destroy(t)
+    scn.scn_video_destroy(v)
+    print(f"ok {a.kernel} frames={n}")
+
+
+if __name__ == "__main__":
+    main()

@@ -10,22 +10,30 @@
 //   flag[k] = 2*score[k] > W*H                                          Sec. 5.2 shots)
 //
 // Design (B300):
-//  * one CTA per SM; a producer warp streams each work item (a slice of rows of
-//    one frame) through kStages shared-memory chunks with 1-D bulk copies
-//    (TMA engine), completion on mbarriers; 8 consumer warps convert and count.
-//  * the bin never needs a clamp: with x = 16*(298Y + k_c) + offset the value
-//    x >> 16 is an "extended" bin in [0, rows_c) covering every byte triple, and
-//    the out-of-range extended bins fold into bins 0 and 15 when the table is
-//    flushed (clamp(x >> 8) >> 4 == clamp(x >> 12, 0, 15)).
-//  * per pixel and channel: one dp2a (byte select + multiply + add of the
-//    chroma term), one prmt (builds the shared address from the bin byte and
-//    the lane's column) and one shared-memory atomic add.  Each lane owns a
-//    column of its warp's table ([row][lane], 256-byte rows shared by two
-//    warps), so the atomics never conflict on a bank.
-//  * a slice's counts are reduced across lanes and warps, written as a
-//    partial; the CTA completing a frame sums its partials into hist[k]; the
+//  * Work split: the sequence is a flat list of "row pairs" (two luma rows and
+//    the chroma row they share) of all sampled frames.  CTA b takes one
+//    contiguous range of it, so every CTA does the same work and crosses only a
+//    few frame boundaries (the paper's work packets, Sec. 4.1, reduced to one
+//    contiguous packet per CTA).
+//  * One CTA per SM: a producer warp streams the range through kStages
+//    shared-memory chunks with 1-D bulk copies (TMA engine), completion on
+//    mbarriers; 16 consumer warps convert and count.
+//  * The bin needs no clamp: with x = 16*(298Y + k_c) + offset, x >> 16 is an
+//    "extended" bin covering every byte triple; extended bins outside [0,16)
+//    fold into bins 0 and 15 when the table is flushed
+//    (clamp(x >> 8, 0, 255) >> 4 == clamp(x >> 12, 0, 15)).
+//  * Per pixel and channel: one dp2a (byte select, multiply, add the chroma
+//    term and the table row base), one prmt (shared address = row byte(s) of
+//    x + the lane's column byte) and one shared-memory reduction.  Each lane
+//    owns a column ([row][lane], 256-byte rows); four warps share a table
+//    region (two column halves x two 16-bit counter halves), so the reductions
+//    never conflict on a bank and 16 warps fit in shared memory.
+//  * At the end of each frame segment the table is flushed (lane columns and
+//    counter halves summed, extended bins folded) and published: directly to
+//    hist[k] when the CTA counted the whole frame, else through an
+//    accumulator that the CTA completing the frame turns into hist[k].  The
 //    CTA completing the second frame of a consecutive pair computes that
-//    pair's score.  Completion uses counters, nobody waits for another CTA.
+//    pair's score.  Completion uses counters; no CTA waits for another.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,9 +49,9 @@ namespace {
 constexpr int kRowsR = 45, kRowsG = 39, kRowsB = 52;
 constexpr int kBaseR = 0, kBaseG = kRowsR, kBaseB = kRowsR + kRowsG;
 constexpr int kOffR = 14, kOffG = 11, kOffB = 18;
-static_assert(kRowsR + kRowsG + kRowsB == kTabRowsPerPair, "table rows");
+static_assert(kRowsR + kRowsG + kRowsB == kTabRowsPerRegion, "table rows");
 
-// x_c = 4768*Y + K_c, K_c = 16*(chroma term + 128 - 298*16 + off_c*4096) + row base
+// x_c = 4768*Y + K_c, K_c = 16*(chroma term + 128 - 298*16 + off_c*4096) + (row base << 16)
 // 4768 = 298*16; chroma weights *16: 409 -> 6544, 516 -> 8256, -100 -> -1600, -208 -> -3328.
 constexpr uint32_t kWY = 4768u;
 constexpr uint32_t kWV_R = 6544u;
@@ -54,6 +62,7 @@ constexpr int32_t kCB = 16 * (-516 * 128 + 128 - 298 * 16 + kOffB * 4096);      
 constexpr int32_t kCG = 16 * (100 * 128 + 208 * 128 + 128 - 298 * 16 + kOffG * 4096);  // 1277440
 static_assert(kCR == 5632 && kCB == 48640 && kCG == 1277440, "chroma constants");
 
+constexpr int kNT = kConsumerWarps * 32;          // consumer threads
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
 struct HistArgs {
@@ -62,7 +71,8 @@ struct HistArgs {
     int W, H;
     const int32_t* slot;
     int64_t n;
-    int slices, rows_per_slice, chunk_rows, stage_bytes;
+    int chunk_rows, stage_bytes, seg_rows;
+    int64_t rp_per_cta;
     uint32_t* hist;
     uint32_t* score;
     uint8_t* flag;
@@ -74,9 +84,9 @@ struct HistArgs {
 };
 
 struct Smem {
-    uint8_t* base;
+    uint8_t* tab;
     uint8_t* stages;
-    uint32_t* acc;      // [2][48]
+    uint32_t* acc;      // [48]
     uint64_t* full;     // [kStages]
     uint64_t* empty;    // [kStages]
     int* abort_flag;
@@ -84,10 +94,10 @@ struct Smem {
 
 __device__ __forceinline__ Smem carve(uint8_t* smem, int stage_bytes) {
     Smem s;
-    s.base = smem;
+    s.tab = smem;
     s.stages = smem + kTabBytes;
     s.acc = reinterpret_cast<uint32_t*>(s.stages + kStages * stage_bytes);
-    s.full = reinterpret_cast<uint64_t*>(s.acc + 96);
+    s.full = reinterpret_cast<uint64_t*>(s.acc + 64);
     s.empty = s.full + kStages;
     s.abort_flag = reinterpret_cast<int*>(s.empty + kStages);
     return s;
@@ -102,25 +112,68 @@ __device__ __forceinline__ bool aborted(const Smem& s) {
     return *reinterpret_cast<volatile int*>(s.abort_flag) != 0;
 }
 
+// Walks a CTA's contiguous range of row pairs chunk by chunk.  A chunk never
+// crosses a frame; a segment (rows counted between two flushes) ends at a frame
+// boundary, at the end of the range, or after seg_rows rows.
+struct Walker {
+    int64_t g, g_end;  // global row-pair cursor and end
+    int64_t k;         // element of the cursor
+    int rp;            // row pair of the cursor within its frame
+    int seg;           // row pairs counted in the current segment
+    int hp, crp, srp;  // row pairs per frame, per chunk, per segment (max)
+
+    __device__ __forceinline__ void init(const HistArgs& a) {
+        hp = a.H / 2;
+        crp = a.chunk_rows / 2;
+        srp = a.seg_rows / 2;
+        const int64_t total = a.n * hp;
+        g = blockIdx.x * a.rp_per_cta;
+        g_end = min(g + a.rp_per_cta, total);
+        k = g / hp;
+        rp = static_cast<int>(g - k * hp);
+        seg = 0;
+    }
+    // Next chunk: element, first luma row, luma rows, whether it ends a segment
+    // and (then) the row pairs of the segment.
+    __device__ __forceinline__ bool next(int64_t& ck, int& r, int& rows, bool& seg_end, int& seg_rp) {
+        if (g >= g_end) return false;
+        int m = min(crp, hp - rp);
+        if (g_end - g < m) m = static_cast<int>(g_end - g);
+        m = min(m, srp - seg);
+        ck = k;
+        r = 2 * rp;
+        rows = 2 * m;
+        g += m;
+        rp += m;
+        seg += m;
+        seg_end = (rp == hp) || (g == g_end) || (seg == srp);
+        seg_rp = seg;
+        if (seg_end) seg = 0;
+        if (rp == hp) {
+            rp = 0;
+            ++k;
+        }
+        return true;
+    }
+};
+
 // ---------------------------------------------------------------------------
-// producer: one thread issues the bulk copies of every chunk of every item
+// producer: one thread issues the bulk copies of every chunk
 // ---------------------------------------------------------------------------
 __device__ void produce(const HistArgs& a, const Smem& s) {
-    const int64_t items = a.n * a.slices;
+    Walker w;
+    w.init(a);
     uint32_t it = 0, issued = 0;
-    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int64_t k = item / a.slices;
-        const int sl = static_cast<int>(item - k * a.slices);
-        const uint8_t* frame = a.nv12 + static_cast<int64_t>(a.slot[k]) * a.stride;
-        const int r0 = sl * a.rows_per_slice;
-        const int r1 = min(r0 + a.rows_per_slice, a.H);
-        for (int r = r0; r < r1; r += a.chunk_rows, ++it) {
-            const int rows = min(a.chunk_rows, r1 - r);
-            const uint32_t st = it % kStages;
-            if (it >= static_cast<uint32_t>(kStages) && !aborted(s)) {
-                if (!ptx::mbar_wait_bounded(&s.empty[st], ((it / kStages) - 1) & 1u, kWaitLimitNs)) fail(a, s);
-            }
-            if (aborted(s)) continue;
+    int64_t k;
+    int r, rows, seg_rp;
+    bool seg_end;
+    while (w.next(k, r, rows, seg_end, seg_rp)) {
+        const uint32_t st = it % kStages;
+        if (it >= static_cast<uint32_t>(kStages) && !aborted(s)) {
+            if (!ptx::mbar_wait_bounded(&s.empty[st], ((it / kStages) - 1) & 1u, kWaitLimitNs)) fail(a, s);
+        }
+        if (!aborted(s)) {
+            const uint8_t* frame = a.nv12 + static_cast<int64_t>(a.slot[k]) * a.stride;
             uint8_t* dst = s.stages + st * a.stage_bytes;
             const uint32_t by = static_cast<uint32_t>(rows) * a.W;
             const uint32_t buv = by / 2;
@@ -130,6 +183,7 @@ __device__ void produce(const HistArgs& a, const Smem& s) {
                           &s.full[st]);
             issued = it + 1;
         }
+        ++it;
     }
     // Let every copy this CTA issued land before the CTA can exit (copies stop
     // being issued after an abort, so chunks [0, issued) are the issued ones).
@@ -144,15 +198,22 @@ __device__ void produce(const HistArgs& a, const Smem& s) {
 // ---------------------------------------------------------------------------
 // consumers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void count3(uint8_t* tab, uint32_t lanereg, uint32_t xr, uint32_t xg, uint32_t xb) {
-    // address = (x >> 16) * 256 + lane column; byte 0 from lanereg, bytes 2,3 of x -> bytes 1,2
-    atomicAdd(reinterpret_cast<uint32_t*>(tab + ptx::prmt(xr, lanereg, 0x5324u)), 1u);
-    atomicAdd(reinterpret_cast<uint32_t*>(tab + ptx::prmt(xg, lanereg, 0x5324u)), 1u);
-    atomicAdd(reinterpret_cast<uint32_t*>(tab + ptx::prmt(xb, lanereg, 0x5324u)), 1u);
+__device__ __forceinline__ void red_shared(uint32_t addr, uint32_t v) {
+    // no memory clobber: the table is only read after a named barrier (which has one)
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+// d.b0 = lane column byte, d.b1/d.b2 = bytes 2/3 of x (the table row), d.b3 = 0
+__device__ __forceinline__ uint32_t tab_addr(uint32_t x, uint32_t lanereg) { return ptx::prmt(x, lanereg, 0x5324u); }
+
+__device__ __forceinline__ void count3(uint32_t lanereg, uint32_t inc, uint32_t xr, uint32_t xg, uint32_t xb) {
+    red_shared(tab_addr(xr, lanereg), inc);
+    red_shared(tab_addr(xg, lanereg), inc);
+    red_shared(tab_addr(xb, lanereg), inc);
 }
 
 // 32 pixels: 16 columns of two luma rows sharing 8 chroma samples.
-__device__ __forceinline__ void count_unit(uint8_t* tab, uint32_t lanereg, uint32_t cR, uint32_t cG, uint32_t cB,
+__device__ __forceinline__ void count_unit(uint32_t lanereg, uint32_t inc, uint32_t cR, uint32_t cG, uint32_t cB,
                                            uint4 y0, uint4 y1, uint4 uv) {
     const uint32_t yw0[4] = {y0.x, y0.y, y0.z, y0.w};
     const uint32_t yw1[4] = {y1.x, y1.y, y1.z, y1.w};
@@ -163,49 +224,54 @@ __device__ __forceinline__ void count_unit(uint8_t* tab, uint32_t lanereg, uint3
     const uint32_t aG = (static_cast<uint32_t>(kWU_G) & 0xFFFFu) | (static_cast<uint32_t>(kWV_G) << 16);
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        // chroma sample (bytes 0,1) serves luma bytes 0,1; (bytes 2,3) serves luma bytes 2,3
+        // chroma sample in bytes 0,1 serves luma bytes 0,1; bytes 2,3 serve luma bytes 2,3
         {
             const uint32_t kr = ptx::dp2a_lo_uu(aR, uvw[w], cR);
             const uint32_t kb = ptx::dp2a_lo_uu(aB, uvw[w], cB);
             const uint32_t kg = static_cast<uint32_t>(ptx::dp2a_lo_su(aG, uvw[w], static_cast<int32_t>(cG)));
-            count3(tab, lanereg, ptx::dp2a_lo_uu(aY0, yw0[w], kr), ptx::dp2a_lo_uu(aY0, yw0[w], kg),
+            count3(lanereg, inc, ptx::dp2a_lo_uu(aY0, yw0[w], kr), ptx::dp2a_lo_uu(aY0, yw0[w], kg),
                    ptx::dp2a_lo_uu(aY0, yw0[w], kb));
-            count3(tab, lanereg, ptx::dp2a_lo_uu(aY1, yw0[w], kr), ptx::dp2a_lo_uu(aY1, yw0[w], kg),
+            count3(lanereg, inc, ptx::dp2a_lo_uu(aY1, yw0[w], kr), ptx::dp2a_lo_uu(aY1, yw0[w], kg),
                    ptx::dp2a_lo_uu(aY1, yw0[w], kb));
-            count3(tab, lanereg, ptx::dp2a_lo_uu(aY0, yw1[w], kr), ptx::dp2a_lo_uu(aY0, yw1[w], kg),
+            count3(lanereg, inc, ptx::dp2a_lo_uu(aY0, yw1[w], kr), ptx::dp2a_lo_uu(aY0, yw1[w], kg),
                    ptx::dp2a_lo_uu(aY0, yw1[w], kb));
-            count3(tab, lanereg, ptx::dp2a_lo_uu(aY1, yw1[w], kr), ptx::dp2a_lo_uu(aY1, yw1[w], kg),
+            count3(lanereg, inc, ptx::dp2a_lo_uu(aY1, yw1[w], kr), ptx::dp2a_lo_uu(aY1, yw1[w], kg),
                    ptx::dp2a_lo_uu(aY1, yw1[w], kb));
         }
         {
             const uint32_t kr = ptx::dp2a_hi_uu(aR, uvw[w], cR);
             const uint32_t kb = ptx::dp2a_hi_uu(aB, uvw[w], cB);
             const uint32_t kg = static_cast<uint32_t>(ptx::dp2a_hi_su(aG, uvw[w], static_cast<int32_t>(cG)));
-            count3(tab, lanereg, ptx::dp2a_hi_uu(aY0, yw0[w], kr), ptx::dp2a_hi_uu(aY0, yw0[w], kg),
+            count3(lanereg, inc, ptx::dp2a_hi_uu(aY0, yw0[w], kr), ptx::dp2a_hi_uu(aY0, yw0[w], kg),
                    ptx::dp2a_hi_uu(aY0, yw0[w], kb));
-            count3(tab, lanereg, ptx::dp2a_hi_uu(aY1, yw0[w], kr), ptx::dp2a_hi_uu(aY1, yw0[w], kg),
+            count3(lanereg, inc, ptx::dp2a_hi_uu(aY1, yw0[w], kr), ptx::dp2a_hi_uu(aY1, yw0[w], kg),
                    ptx::dp2a_hi_uu(aY1, yw0[w], kb));
-            count3(tab, lanereg, ptx::dp2a_hi_uu(aY0, yw1[w], kr), ptx::dp2a_hi_uu(aY0, yw1[w], kg),
+            count3(lanereg, inc, ptx::dp2a_hi_uu(aY0, yw1[w], kr), ptx::dp2a_hi_uu(aY0, yw1[w], kg),
                    ptx::dp2a_hi_uu(aY0, yw1[w], kb));
-            count3(tab, lanereg, ptx::dp2a_hi_uu(aY1, yw1[w], kr), ptx::dp2a_hi_uu(aY1, yw1[w], kg),
+            count3(lanereg, inc, ptx::dp2a_hi_uu(aY1, yw1[w], kr), ptx::dp2a_hi_uu(aY1, yw1[w], kg),
                    ptx::dp2a_hi_uu(aY1, yw1[w], kb));
         }
     }
 }
 
-// Sum this warp's lane columns row by row, fold extended bins, add into acc[48],
-// and leave the table zeroed.
-__device__ __forceinline__ void flush_table(uint8_t* tab, int pair, int half, int lane, uint32_t* acc) {
-    for (int t = lane; t < kTabRowsPerPair; t += 32) {
-        uint8_t* row = tab + (pair * kTabRowsPerPair + t) * 256 + half * 128;
-        uint32_t sum = 0;
+// Cooperative flush by all consumer threads: every table row summed over its
+// 64 words and both 16-bit halves, extended bin folded into the final bin,
+// added into acc[48]; the table is left zeroed.
+__device__ __forceinline__ void flush_table(uint8_t* tab, uint32_t* acc, int ctid) {
+    const int lane = ctid & 31;
+    for (int row = ctid; row < kRegions * kTabRowsPerRegion; row += kNT) {
+        uint8_t* p = tab + row * 256;
+        uint32_t lo = 0, hi = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            uint4* q = reinterpret_cast<uint4*>(row + ((lane + i) & 7) * 16);
+        for (int i = 0; i < 16; ++i) {
+            uint4* q = reinterpret_cast<uint4*>(p + ((lane + i) & 15) * 16);
             const uint4 v = *q;
-            sum += v.x + v.y + v.z + v.w;
+            lo += (v.x & 0xFFFFu) + (v.y & 0xFFFFu) + (v.z & 0xFFFFu) + (v.w & 0xFFFFu);
+            hi += (v.x >> 16) + (v.y >> 16) + (v.z >> 16) + (v.w >> 16);
             *q = make_uint4(0, 0, 0, 0);
         }
+        const uint32_t sum = lo + hi;
+        const int t = row % kTabRowsPerRegion;
         int c, e, off;
         if (t < kBaseG) { c = 0; e = t - kBaseR; off = kOffR; }
         else if (t < kBaseB) { c = 1; e = t - kBaseG; off = kOffG; }
@@ -216,7 +282,7 @@ __device__ __forceinline__ void flush_table(uint8_t* tab, int pair, int half, in
 }
 
 // Score of element k from its histogram (h0: bins lane, h1: bins 32+lane) and
-// its predecessor's, read from global memory.
+// a neighbour's, read from global memory.
 __device__ __forceinline__ void write_score(const HistArgs& a, int64_t k, uint32_t h0, uint32_t h1,
                                             const uint32_t* other, int lane) {
     const uint32_t p0 = ptx::ld_cg_u32(other + lane);
@@ -230,37 +296,32 @@ __device__ __forceinline__ void write_score(const HistArgs& a, int64_t k, uint32
     }
 }
 
-// After the consumer barrier: publish this slice, complete frames and scores.
-__device__ void complete_item(const HistArgs& a, int64_t k, int sl, uint32_t* acc, int lane) {
-    const uint32_t v0 = acc[lane];
-    const uint32_t v1 = lane < 16 ? acc[32 + lane] : 0u;
+// One warp, after the flush: publish the segment's counts of element k (seg_rp
+// row pairs), complete the frame and the scores it unblocks.
+__device__ void publish(const HistArgs& a, int64_t k, int seg_rp, uint32_t* acc, int lane) {
+    uint32_t h0 = acc[lane];
+    uint32_t h1 = lane < 16 ? acc[32 + lane] : 0u;
     acc[lane] = 0;
     if (lane < 16) acc[32 + lane] = 0;
-    uint32_t h0 = v0, h1 = v1;
-    bool complete = true;
-    if (a.slices > 1) {
-        uint32_t* pp = a.partial + (k * a.slices + sl) * 48;
-        pp[lane] = v0;
-        if (lane < 16) pp[32 + lane] = v1;
+    const int hp = a.H / 2;
+    if (seg_rp != hp) {
+        // part of the frame: accumulate; the CTA completing the frame finishes it
+        uint32_t* pk = a.partial + k * 48;
+        if (h0) atomicAdd(pk + lane, h0);
+        if (lane < 16 && h1) atomicAdd(pk + 32 + lane, h1);
         __threadfence();
         __syncwarp();
         uint32_t old = 0;
-        if (lane == 0) old = atomicAdd(&a.done[k], 1u);
+        if (lane == 0) old = atomicAdd(&a.done[k], static_cast<uint32_t>(seg_rp));
         old = __shfl_sync(0xffffffffu, old, 0);
-        complete = (old == static_cast<uint32_t>(a.slices - 1));
-        if (complete) {
-            __threadfence();
-            h0 = 0;
-            h1 = 0;
-            for (int j = 0; j < a.slices; ++j) {
-                const uint32_t* q = a.partial + (k * a.slices + j) * 48;
-                h0 += ptx::ld_cg_u32(q + lane);
-                if (lane < 16) h1 += ptx::ld_cg_u32(q + 32 + lane);
-            }
-            if (lane == 0) a.done[k] = 0;
-        }
+        if (old + static_cast<uint32_t>(seg_rp) != static_cast<uint32_t>(hp)) return;
+        __threadfence();
+        h0 = ptx::ld_cg_u32(pk + lane);
+        h1 = lane < 16 ? ptx::ld_cg_u32(pk + 32 + lane) : 0u;
+        pk[lane] = 0;  // leave the accumulator zeroed for the next call
+        if (lane < 16) pk[32 + lane] = 0;
+        if (lane == 0) a.done[k] = 0;
     }
-    if (!complete) return;
     a.hist[k * 48 + lane] = h0;
     if (lane < 16) a.hist[k * 48 + 32 + lane] = h1;
     if (!a.score) return;
@@ -293,64 +354,73 @@ __device__ void complete_item(const HistArgs& a, int64_t k, int sl, uint32_t* ac
     }
 }
 
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+
 __device__ void consume(const HistArgs& a, const Smem& s, int warp, int lane) {
     const int ctid = warp * 32 + lane;
-    constexpr int NT = kConsumerWarps * 32;
-    const int pair = warp >> 1, half = warp & 1;
-    const uint32_t lanereg = static_cast<uint32_t>(lane * 4 + half * 128);
-    const uint32_t rowbase = static_cast<uint32_t>(pair * kTabRowsPerPair) << 16;
+    const int region = warp / kGroupWarps;
+    const uint32_t lanereg = static_cast<uint32_t>(lane * 4 + (warp & 1) * 128);
+    const uint32_t inc = (warp & 2) ? 65536u : 1u;
+    // table row of x = (x >> 16): shared base / 256 + region rows + channel rows + extended bin
+    const uint32_t rowbase = ((ptx::smem_u32(s.tab) >> 8) + static_cast<uint32_t>(region * kTabRowsPerRegion)) << 16;
     const uint32_t cR = static_cast<uint32_t>(kCR) + rowbase + (static_cast<uint32_t>(kBaseR) << 16);
     const uint32_t cG = static_cast<uint32_t>(kCG) + rowbase + (static_cast<uint32_t>(kBaseG) << 16);
     const uint32_t cB = static_cast<uint32_t>(kCB) + rowbase + (static_cast<uint32_t>(kBaseB) << 16);
     const int W = a.W;
     const int wv = W / 16;
-    const int sp = NT / wv, sc = NT % wv;
-    uint8_t* tab = s.base;
-    const int64_t items = a.n * a.slices;
+    const int sp = kNT / wv, sc = kNT % wv;
+    // byte step of the luma / chroma address per kNT units; a column wrap adds
+    // one more row pair and removes a row of columns: luma +2W-W, chroma +W-W
+    const uint32_t dY = static_cast<uint32_t>(sp * 2 * W + sc * 16);
+    const uint32_t dU = static_cast<uint32_t>(sp * W + sc * 16);
+    const uint32_t stages = ptx::smem_u32(s.stages);
+    Walker wk;
+    wk.init(a);
     uint32_t it = 0;
     int rot = 0;
-    int buf = 0;
-    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int64_t k = item / a.slices;
-        const int sl = static_cast<int>(item - k * a.slices);
-        const int r0 = sl * a.rows_per_slice;
-        const int r1 = min(r0 + a.rows_per_slice, a.H);
-        for (int r = r0; r < r1; r += a.chunk_rows, ++it) {
-            const int rows = min(a.chunk_rows, r1 - r);
-            const uint32_t st = it % kStages;
-            if (!aborted(s)) {
-                if (!ptx::mbar_wait_bounded(&s.full[st], (it / kStages) & 1u, kWaitLimitNs)) fail(a, s);
-            }
-            const uint8_t* ybuf = s.stages + st * a.stage_bytes;
-            const uint8_t* uvbuf = ybuf + a.chunk_rows * W;
-            const int units = (rows / 2) * wv;
-            int u = ctid - rot;
-            if (u < 0) u += NT;
-            int p = u / wv;
-            int c = u - p * wv;
-            for (; u < units; u += NT) {
-                const uint8_t* yp = ybuf + (2 * p) * W + 16 * c;
-                const uint4 y0 = *reinterpret_cast<const uint4*>(yp);
-                const uint4 y1 = *reinterpret_cast<const uint4*>(yp + W);
-                const uint4 uv = *reinterpret_cast<const uint4*>(uvbuf + p * W + 16 * c);
-                count_unit(tab, lanereg, cR, cG, cB, y0, y1, uv);
-                c += sc;
-                p += sp;
-                if (c >= wv) {
-                    c -= wv;
-                    ++p;
-                }
-            }
-            rot = (rot + units) % NT;
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&s.empty[st]);
+    int64_t k;
+    int r, rows, seg_rp;
+    bool seg_end;
+    while (wk.next(k, r, rows, seg_end, seg_rp)) {
+        const uint32_t st = it % kStages;
+        if (!aborted(s)) {
+            if (!ptx::mbar_wait_bounded(&s.full[st], (it / kStages) & 1u, kWaitLimitNs)) fail(a, s);
         }
-        uint32_t* acc = s.acc + buf * 48;
+        const uint32_t ybase = stages + st * a.stage_bytes;
+        const int units = (rows / 2) * wv;
+        int u = ctid - rot;
+        if (u < 0) u += kNT;
+        const int p0 = u / wv;
+        int c = u - p0 * wv;
+        uint32_t ya = ybase + p0 * 2 * W + c * 16;
+        uint32_t ua = ybase + a.chunk_rows * W + p0 * W + c * 16;
+        for (; u < units; u += kNT) {
+            const uint4 y0 = lds128(ya);
+            const uint4 y1 = lds128(ya + W);
+            const uint4 uv = lds128(ua);
+            count_unit(lanereg, inc, cR, cG, cB, y0, y1, uv);
+            ya += dY;
+            ua += dU;
+            c += sc;
+            if (c >= wv) {
+                c -= wv;
+                ya += W;
+            }
+        }
+        rot = (rot + units) % kNT;
         __syncwarp();
-        flush_table(tab, pair, half, lane, acc);
-        ptx::named_bar_sync(1, NT);
-        if (warp == 0) complete_item(a, k, sl, acc, lane);
-        buf ^= 1;
+        if (lane == 0) ptx::mbar_arrive(&s.empty[st]);
+        ++it;
+        if (seg_end) {
+            ptx::named_bar_sync(1, kNT);  // every consumer has counted the segment
+            flush_table(s.tab, s.acc, ctid);
+            ptx::named_bar_sync(1, kNT);  // table zeroed, acc complete
+            if (warp == 0) publish(a, k, seg_rp, s.acc, lane);
+        }
     }
 }
 
@@ -360,7 +430,7 @@ __global__ void __launch_bounds__(kHistThreads, 1) hist_kernel(HistArgs a) {
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kTabBytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
-    if (tid < 96) s.acc[tid] = 0;
+    if (tid < 64) s.acc[tid] = 0;
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
             ptx::mbar_init(&s.full[i], 1);
@@ -400,7 +470,7 @@ __global__ void scores_kernel(const uint32_t* hist, int64_t n, int64_t pixel_cou
     }
 }
 
-bool g_attr_set = false;
+int g_attr_device = -1;
 
 }  // namespace
 
@@ -414,32 +484,15 @@ HistShape resolve_hist_shape(const scn_seq* s) {
     const int cr_max = std::max(2, (kStageBudget / (W * 3 / 2)) & ~1);
     if (cr <= 0 || cr > cr_max) cr = cr_max;
     cr = std::min(cr, H);
-    // slices: enough items to keep every CTA busy with a small tail
-    int slices = s->tune.slices;
-    const int64_t n = std::max<int64_t>(s->n, 1);
-    if (slices <= 0) {
-        slices = 1;
-        double best = 0.0;
-        for (int c = 1; c <= s->max_slices; ++c) {
-            const int64_t items = n * c;
-            const int64_t rounds = (items + sms - 1) / sms;
-            const double eff = static_cast<double>(items) / static_cast<double>(rounds * sms);
-            if (eff > best + 0.02) {
-                best = eff;
-                slices = c;
-            }
-            if (eff >= 0.97) break;
-        }
-    }
-    slices = std::min(slices, std::max(1, H / 2));
-    int rps = ((H / 2 + slices - 1) / slices) * 2;
-    slices = (H + rps - 1) / rps;
-    sh.slices = slices;
-    sh.rows_per_slice = rps;
     sh.chunk_rows = cr;
-    const int64_t items = n * slices;
-    int grid = s->tune.grid > 0 ? s->tune.grid : sms;
-    sh.grid = static_cast<int>(std::min<int64_t>(grid, items));
+    // rows between flushes: bounded so a 16-bit lane counter cannot overflow
+    const int64_t seg = std::max<int64_t>(2, (kSegmentPixels / W) & ~int64_t(1));
+    sh.seg_rows = static_cast<int>(std::min<int64_t>(seg, H));
+    const int64_t total_rp = std::max<int64_t>(s->n, 1) * (H / 2);
+    const int grid = s->tune.grid > 0 ? s->tune.grid : sms;
+    sh.grid = static_cast<int>(std::min<int64_t>(grid, total_rp));
+    sh.rp_per_cta = (total_rp + sh.grid - 1) / sh.grid;
+    sh.grid = static_cast<int>((total_rp + sh.rp_per_cta - 1) / sh.rp_per_cta);
     sh.stage_bytes = ((cr * W * 3 / 2) + 127) & ~127;
     sh.smem = static_cast<size_t>(kTabBytes) + static_cast<size_t>(kStages) * sh.stage_bytes + kSmemMisc;
     return sh;
@@ -452,9 +505,11 @@ static scn_status run_hist(scn_seq* s, uint32_t* d_hist, uint32_t* d_score, uint
     if (s->n == 0) return SCN_OK;
     const HistShape sh = resolve_hist_shape(s);
     if (sh.smem > static_cast<size_t>(kSmemLimit)) return SCN_EUNSUPPORTED;
-    if (!g_attr_set) {
+    int dev = 0;
+    SCN_CUDA_TRY(cudaGetDevice(&dev));
+    if (g_attr_device != dev) {
         SCN_CUDA_TRY(cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-        g_attr_set = true;
+        g_attr_device = dev;
     }
     HistArgs a;
     a.nv12 = s->table->d_nv12;
@@ -463,10 +518,10 @@ static scn_status run_hist(scn_seq* s, uint32_t* d_hist, uint32_t* d_score, uint
     a.H = s->table->H;
     a.slot = s->d_slot;
     a.n = s->n;
-    a.slices = sh.slices;
-    a.rows_per_slice = sh.rows_per_slice;
     a.chunk_rows = sh.chunk_rows;
     a.stage_bytes = sh.stage_bytes;
+    a.seg_rows = sh.seg_rows;
+    a.rp_per_cta = sh.rp_per_cta;
     a.hist = d_hist;
     a.score = d_score;
     a.flag = d_flag;

@@ -347,12 +347,10 @@ scn_status scn_sample(const scn_table* t, const scn_sample_spec* spec, scn_seq**
     s->table = t;
     s->n = static_cast<int64_t>(f.size());
     s->frames = std::move(f);
-    // Row slicing only pays when there are too few elements to fill the GPU.
-    s->max_slices = s->n <= 8192 ? kMaxSlices : 1;
     const size_t n = static_cast<size_t>(std::max<int64_t>(s->n, 1));
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b_slot = up(n * 4), b_done = up(n * 4), b_pair = up(n * 4);
-    const size_t b_part = up(n * static_cast<size_t>(s->max_slices) * 48 * 4), b_stat = 256;
+    const size_t b_part = up(n * 48 * 4), b_stat = 256;
     const size_t total = b_slot + b_done + b_pair + b_part + b_stat;
     cudaError_t e = cudaMalloc(&s->d_block, total);
     if (e != cudaSuccess) {
@@ -408,9 +406,8 @@ scn_status scn_seq_sync_status(scn_seq* s, void* stream) {
 
 scn_status scn_seq_set_tune(scn_seq* s, const scn_tune* tune) {
     if (!s || !tune) return SCN_EINVAL;
-    if (tune->slices < 0 || tune->slices > s->max_slices) return SCN_ERANGE;
     if (tune->chunk_rows < 0 || (tune->chunk_rows % 2)) return SCN_EINVAL;
-    if (tune->grid < 0) return SCN_EINVAL;
+    if (tune->grid < 0 || tune->reserved != 0) return SCN_EINVAL;
     s->tune = *tune;
     return SCN_OK;
 }
@@ -418,9 +415,9 @@ scn_status scn_seq_set_tune(scn_seq* s, const scn_tune* tune) {
 scn_status scn_seq_get_tune(const scn_seq* s, scn_tune* tune) {
     if (!s || !tune) return SCN_EINVAL;
     const HistShape sh = resolve_hist_shape(s);
-    tune->slices = sh.slices;
     tune->chunk_rows = sh.chunk_rows;
     tune->grid = sh.grid;
+    tune->reserved = 0;
     return SCN_OK;
 }
 

@@ -24,21 +24,23 @@ void set_cuda_error(cudaError_t e);
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Maximum row slices per frame.
-constexpr int kMaxSlices = 16;
-
 // Device status word bits (per sequence).
 constexpr int kStatusTimeout = 1;
 
 // Histogram kernel geometry (fixed at compile time).
-constexpr int kConsumerWarps = 8;                    // warps that convert + count
+constexpr int kConsumerWarps = 16;                        // warps that convert + count
 constexpr int kHistThreads = (kConsumerWarps + 1) * 32;  // + one producer warp (bulk copies)
-constexpr int kStages = 3;                           // staged chunks in flight
-constexpr int kTabRowsPerPair = 136;                 // 45 (R) + 39 (G) + 52 (B) extended bins
-constexpr int kTabBytes = (kConsumerWarps / 2) * kTabRowsPerPair * 256;
-constexpr int kSmemLimit = 232448;                   // 227 KB opt-in per CTA
-constexpr int kSmemMisc = 1024;                      // accumulators + barriers + flags
+constexpr int kStages = 3;                                // staged chunks in flight
+constexpr int kGroupWarps = 4;                            // warps sharing one table region
+constexpr int kRegions = kConsumerWarps / kGroupWarps;
+constexpr int kTabRowsPerRegion = 136;                    // 45 (R) + 39 (G) + 52 (B) extended bins
+constexpr int kTabBytes = kRegions * kTabRowsPerRegion * 256;
+constexpr int kSmemLimit = 232448;                        // 227 KB opt-in per CTA
+constexpr int kSmemMisc = 1024;                           // accumulators + barriers + flags
 constexpr int kStageBudget = (kSmemLimit - kTabBytes - kSmemMisc) / kStages;
+// Pixels a CTA may count between two table flushes: keeps every 16-bit lane
+// counter below 2^16 (each of the 512 consumer threads sees at most 1/512 of them).
+constexpr int64_t kSegmentPixels = int64_t(1) << 24;
 
 }  // namespace scn
 
@@ -64,22 +66,21 @@ struct scn_seq {
     // device memory (one allocation, carved)
     void* d_block = nullptr;
     int32_t* d_slot = nullptr;       // storage slot per element [n]
-    uint32_t* d_done = nullptr;      // per-element completed slices [n]
+    uint32_t* d_done = nullptr;      // per-element counted row pairs [n] (kept zero)
     uint32_t* d_pair = nullptr;      // per-element arrivals of the score stencil [n]
-    uint32_t* d_partial = nullptr;   // [n][max_slices][48]
+    uint32_t* d_partial = nullptr;   // [n][48] cross-CTA histogram accumulators (kept zero)
     int* d_status = nullptr;         // device status word
-    int32_t max_slices = 1;
     scn_tune tune{0, 0, 0};          // 0 fields: chosen per call
 };
 
 namespace scn {
 // Launch shape resolved for a sequence (see scn_hist.cu).
 struct HistShape {
-    int slices;
-    int rows_per_slice;
-    int chunk_rows;
-    int grid;
-    int stage_bytes;
+    int chunk_rows;      // luma rows per staged chunk (even)
+    int grid;            // CTAs
+    int stage_bytes;     // bytes per stage buffer
+    int seg_rows;        // luma rows counted between two table flushes (even)
+    int64_t rp_per_cta;  // row pairs (2 luma rows + 1 chroma row) per CTA
     size_t smem;
 };
 HistShape resolve_hist_shape(const scn_seq* s);

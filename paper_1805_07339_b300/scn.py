@@ -49,7 +49,7 @@ class scn_sample_spec(ctypes.Structure):
 
 
 class scn_tune(ctypes.Structure):
-    _fields_ = [("slices", c_i32), ("chunk_rows", c_i32), ("grid", c_i32)]
+    _fields_ = [("chunk_rows", c_i32), ("grid", c_i32), ("reserved", c_i32)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/scn.h
@@ -245,15 +245,15 @@ def scn_seq_sync_status(s: int, stream=None) -> int:
     return int(_lib.scn_seq_sync_status(s, _stream(stream)))
 
 
-def scn_seq_set_tune(s: int, slices: int = 0, chunk_rows: int = 0, grid: int = 0) -> None:
-    t = scn_tune(slices, chunk_rows, grid)
+def scn_seq_set_tune(s: int, chunk_rows: int = 0, grid: int = 0) -> None:
+    t = scn_tune(chunk_rows, grid, 0)
     _check(_lib.scn_seq_set_tune(s, ctypes.byref(t)), "scn_seq_set_tune")
 
 
 def scn_seq_get_tune(s: int) -> dict:
     t = scn_tune()
     _check(_lib.scn_seq_get_tune(s, ctypes.byref(t)), "scn_seq_get_tune")
-    return dict(slices=t.slices, chunk_rows=t.chunk_rows, grid=t.grid)
+    return dict(chunk_rows=t.chunk_rows, grid=t.grid)
 
 
 def scn_hist(s: int, hist, stream=None) -> None:

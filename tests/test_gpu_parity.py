@@ -155,9 +155,9 @@ def test_hist_random_bytes_bit_exact(scn, orc, W, H, n):
         dev.close()
 
 
-@pytest.mark.parametrize("tune", [dict(slices=1), dict(slices=2), dict(slices=3, chunk_rows=6),
-                                  dict(slices=16, chunk_rows=2), dict(slices=7, grid=1), dict(slices=5, grid=3),
-                                  dict(chunk_rows=4, grid=2)])
+@pytest.mark.parametrize("tune", [dict(grid=1), dict(grid=2), dict(grid=3, chunk_rows=6), dict(grid=7),
+                                  dict(chunk_rows=2, grid=16), dict(grid=1000), dict(chunk_rows=4, grid=2),
+                                  dict(chunk_rows=10)])
 def test_hist_launch_shapes_agree(scn, orc, tune):
     W, H, n = 640, 360, 12
     frames = random_nv12(99, n, W, H)
@@ -367,7 +367,7 @@ def test_argument_errors_before_launch(scn):
         with pytest.raises(scn.ScnError):
             scn.scn_resize_norm(seq, 224, 224, MEAN, (0.2, 0.0, 0.2), scn.SCN_F32, odd)
         with pytest.raises(scn.ScnError):
-            scn.scn_seq_set_tune(seq, slices=99)
+            scn.scn_seq_set_tune(seq, chunk_rows=3)
         scn.scn_seq_destroy(seq)
     finally:
         dev.close()
