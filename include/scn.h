@@ -188,6 +188,29 @@ scn_status scn_shot_scores(const uint32_t* d_hist, int64_t n, int64_t pixel_coun
 scn_status scn_hist_scores(scn_seq* s, uint32_t* d_hist, uint32_t* d_score, uint8_t* d_flag,
                            void* stream);
 
+/* Allocation-free form of scn_hist_scores, for callers that cannot allocate
+ * device memory: code running where cudaMalloc is off limits (an allocator
+ * hook, a host that owns every device buffer and hands out fixed regions,
+ * real-time paths that must not touch the allocator).  The paper has no
+ * counterpart; this is a property of the library only.
+ *   d_nv12: device frames, frame s at d_nv12 + s*frame_stride (16-byte aligned,
+ *   frame_stride >= W*H*3/2 and % 16 == 0); d_slots: device int32 [n], the
+ *   frame of each sampled element (every slot must name a stored frame; they are
+ *   not checked); outputs as scn_hist_scores.
+ * It uses a fixed scratch array inside the library, sized for at most 16384
+ * elements (about 3.3 MB, held on every GPU that loads the library until the
+ * process exits): n > 16384 returns SCN_ERANGE, n = 0 writes nothing.  It
+ * calls no allocating routine.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  Each call clears the part of the
+ * array it uses (an async memset on stream) and then launches the kernel.  All
+ * calls share the one array: calls that overlap on the GPU (different streams
+ * without ordering) race and give wrong results.  A device-side wait timeout
+ * is recorded in the array but not reported. */
+scn_status scn_hist_scores_noalloc(const uint8_t* d_nv12, int32_t width, int32_t height, int64_t frame_stride,
+                                   const int32_t* d_slots, int64_t n, uint32_t* d_hist, uint32_t* d_score,
+                                   uint8_t* d_flag, void* stream);
+
 typedef enum { SCN_F32 = 0, SCN_BF16 = 1 } scn_dtype;
 /* Bilinear resize (half-pixel centres, no antialias, stretch) of the RGB
  * frame to oh x ow, then (v/255 - mean[c]) / std[c]; output [n][3][oh][ow]

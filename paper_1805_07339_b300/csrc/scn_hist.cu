@@ -563,3 +563,91 @@ scn_status scn_shot_scores(const uint32_t* d_hist, int64_t n, int64_t pixel_coun
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of scn_hist_scores (see scn_hist_scores_noalloc in
+// scn.h).  Its scratch lives in a fixed device array of this library instead
+// of memory allocated per sequence.
+// ---------------------------------------------------------------------------
+namespace scn {
+namespace {
+
+constexpr int64_t kNoAllocMaxElems = 16384;
+// per element: 48 partial-histogram words + 1 done counter + 1 pair counter; + status
+constexpr int64_t kNoAllocWords = kNoAllocMaxElems * 50 + 64;
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+
+constexpr int kMaxDevices = 64;
+uint32_t* g_noalloc_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+}  // namespace
+}  // namespace scn
+
+extern "C" scn_status scn_hist_scores_noalloc(const uint8_t* d_nv12, int32_t width, int32_t height,
+                                              int64_t frame_stride, const int32_t* d_slots, int64_t n,
+                                              uint32_t* d_hist, uint32_t* d_score, uint8_t* d_flag, void* stream) {
+    using namespace scn;
+    if (n < 0) return SCN_EINVAL;
+    if (n > kNoAllocMaxElems) return SCN_ERANGE;
+    if (n == 0) return SCN_OK;
+    if (width < 16 || height < 2 || (width % 16) || (height % 2)) return SCN_EINVAL;
+    const int64_t fb = static_cast<int64_t>(width) * height * 3 / 2;
+    if (frame_stride < fb || (frame_stride % 16)) return SCN_EINVAL;
+    if (!d_nv12 || !aligned16(d_nv12) || !d_slots || !d_hist || !d_score || !d_flag) return SCN_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_slots) & 3u) || (reinterpret_cast<uintptr_t>(d_hist) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_score) & 3u))
+        return SCN_EINVAL;
+    int dev = 0;
+    SCN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return SCN_EUNSUPPORTED;
+    if (!g_noalloc_ptr[dev]) {
+        // once per device, with that device current: the host-side name of the
+        // array is not a device address, so ask the runtime for it
+        void* p = nullptr;
+        SCN_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    if (g_attr_device != dev) {
+        SCN_CUDA_TRY(cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        g_attr_device = dev;
+    }
+    // the launch shape of the regular entry point, from a stack-only description
+    scn_table t;
+    t.W = width;
+    t.H = height;
+    t.num_frames = n;
+    t.frame_stride = frame_stride;
+    t.d_nv12 = d_nv12;
+    scn_seq q;
+    q.table = &t;
+    q.n = n;
+    const HistShape sh = resolve_hist_shape(&q);
+    if (sh.smem > static_cast<size_t>(kSmemLimit)) return SCN_EUNSUPPORTED;
+    // scratch of this call: partial [n][48], done [n], pair [n], status; zeroed first
+    uint32_t* base = g_noalloc_ptr[dev];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SCN_CUDA_TRY(cudaMemsetAsync(base, 0, static_cast<size_t>(n * 50 + 1) * sizeof(uint32_t), st));
+    HistArgs a;
+    a.nv12 = d_nv12;
+    a.stride = frame_stride;
+    a.W = width;
+    a.H = height;
+    a.slot = d_slots;
+    a.n = n;
+    a.chunk_rows = sh.chunk_rows;
+    a.stage_bytes = sh.stage_bytes;
+    a.seg_rows = sh.seg_rows;
+    a.rp_per_cta = sh.rp_per_cta;
+    a.hist = d_hist;
+    a.score = d_score;
+    a.flag = d_flag;
+    a.partial = base;
+    a.done = base + n * 48;
+    a.pair = base + n * 49;
+    a.status = reinterpret_cast<int*>(base + n * 50);
+    a.pixel_count = static_cast<int64_t>(width) * height;
+    hist_kernel<<<sh.grid, kHistThreads, sh.smem, st>>>(a);
+    SCN_CUDA_TRY(cudaGetLastError());
+    return SCN_OK;
+}

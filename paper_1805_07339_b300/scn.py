@@ -78,6 +78,7 @@ SIGNATURES = [
     ("scn_hist", c_i32, [c_vp, c_vp, c_vp]),
     ("scn_shot_scores", c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
     ("scn_hist_scores", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    ("scn_hist_scores_noalloc", c_i32, [c_vp, c_i32, c_i32, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp]),
     ("scn_resize_norm", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_i32, c_vp, c_vp]),
     ("scn_thumbs", c_i32, [c_vp, c_vp, c_vp]),
 ]
@@ -262,6 +263,14 @@ def scn_hist(s: int, hist, stream=None) -> None:
 
 def scn_hist_scores(s: int, hist, score, flag, stream=None) -> None:
     _check(_lib.scn_hist_scores(s, _ptr(hist), _ptr(score), _ptr(flag), _stream(stream)), "scn_hist_scores")
+
+
+def scn_hist_scores_noalloc(nv12, width: int, height: int, frame_stride: int, slots, hist, score, flag,
+                            stream=None) -> None:
+    """Allocation-free hist+scores: slots is a device int32 tensor of frame slots."""
+    _check(_lib.scn_hist_scores_noalloc(_ptr(nv12), width, height, frame_stride, _ptr(slots), slots.numel(),
+                                        _ptr(hist), _ptr(score), _ptr(flag), _stream(stream)),
+           "scn_hist_scores_noalloc")
 
 
 def scn_shot_scores(hist, n: int, pixel_count: int, score, flag, stream=None) -> None:
