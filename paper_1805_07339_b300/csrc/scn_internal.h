@@ -30,7 +30,7 @@ constexpr int kStatusTimeout = 1;
 // Histogram kernel geometry (fixed at compile time).
 constexpr int kConsumerWarps = 16;                        // warps that convert + count
 constexpr int kHistThreads = (kConsumerWarps + 1) * 32;  // + one producer warp (bulk copies)
-constexpr int kStages = 3;                                // staged chunks in flight
+constexpr int kStages = 2;                                // staged chunks in flight (2 x ~30 KB measured best)
 constexpr int kGroupWarps = 4;                            // warps sharing one table region
 constexpr int kRegions = kConsumerWarps / kGroupWarps;
 constexpr int kTabRowsPerRegion = 136;                    // 45 (R) + 39 (G) + 52 (B) extended bins
