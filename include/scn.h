@@ -167,7 +167,7 @@ scn_status scn_seq_sync_status(scn_seq* s, void* stream);
 typedef struct {
     int32_t chunk_rows;    /* luma rows per staged chunk (even), 0 = largest that fits */
     int32_t grid;          /* CTAs (one per SM at most is resident), 0 = one per SM */
-    int32_t reserved;      /* must be 0 */
+    int32_t item_kpx;      /* target kilo-pixels per work item (a frame or part of one), 0 = automatic */
 } scn_tune;
 
 scn_status scn_seq_set_tune(scn_seq* s, const scn_tune* tune);
@@ -210,6 +210,42 @@ scn_status scn_hist_scores(scn_seq* s, uint32_t* d_hist, uint32_t* d_score, uint
 scn_status scn_hist_scores_noalloc(const uint8_t* d_nv12, int32_t width, int32_t height, int64_t frame_stride,
                                    const int32_t* d_slots, int64_t n, uint32_t* d_hist, uint32_t* d_score,
                                    uint8_t* d_flag, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched plans: many sequences (of any tables, resolutions, lengths and    */
+/* sampling patterns) histogrammed and scored by ONE persistent launch fed   */
+/* by a device work queue of (sequence, frame, row-range) items - the        */
+/* paper's work packets distributed over graph instances (Sec. 4.1).         */
+/* ------------------------------------------------------------------------ */
+typedef struct scn_plan scn_plan;
+
+/* Build a plan over nseq distinct sequences with their outputs (device,
+ * caller-owned; entry i as in scn_hist_scores for seqs[i]).  tune may be NULL
+ * (automatic shapes).  Uploads the job and item lists (synchronous).  The
+ * sequences' scratch is used by the plan's launches: do not run a sequence
+ * and a plan containing it concurrently.  Errors: SCN_EINVAL (NULL entries,
+ * repeated sequence, misaligned outputs), SCN_ECUDA. */
+scn_status scn_plan_create(scn_seq* const* seqs, int32_t nseq, uint32_t* const* d_hist, uint32_t* const* d_score,
+                           uint8_t* const* d_flag, const scn_tune* tune, scn_plan** out);
+scn_status scn_plan_destroy(scn_plan* p);
+/* Change the launch shape (rebuilds the item list, drops a captured graph). */
+scn_status scn_plan_set_tune(scn_plan* p, const scn_tune* tune);
+scn_status scn_plan_get_tune(const scn_plan* p, scn_tune* tune);
+/* Work items, sampled frames, NV12 bytes read per run, and CTAs of a run. */
+scn_status scn_plan_info(const scn_plan* p, int64_t* n_items, int64_t* n_frames, int64_t* nv12_bytes, int32_t* grid);
+/* One asynchronous run on stream. */
+scn_status scn_plan_run(scn_plan* p, void* stream);
+/* Capture one run into a CUDA graph owned by the plan (stream must not be the
+ * legacy default stream); scn_plan_replay launches it. */
+scn_status scn_plan_capture_graph(scn_plan* p, void* stream);
+scn_status scn_plan_replay(scn_plan* p, void* stream);
+/* Synchronise stream, read and clear the plan's device status word. */
+scn_status scn_plan_sync_status(scn_plan* p, void* stream);
+/* Autotuner: time candidate shapes (item size x chunk rows) with `reps`
+ * runs each on stream (synchronous), keep the fastest; returns it and its
+ * mean time per run (either pointer may be NULL).  Outputs are overwritten by
+ * identical results. */
+scn_status scn_plan_autotune(scn_plan* p, int32_t reps, void* stream, scn_tune* best, float* best_ms);
 
 typedef enum { SCN_F32 = 0, SCN_BF16 = 1 } scn_dtype;
 /* Bilinear resize (half-pixel centres, no antialias, stretch) of the RGB

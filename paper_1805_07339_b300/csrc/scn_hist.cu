@@ -1,7 +1,8 @@
-// Fused BT.601 convert + 3x16-bin histogram + shot score over a sampled
-// sequence of NV12 frames, one persistent launch.
+// Fused BT.601 convert + 3x16-bin histogram + shot score over sampled
+// sequences of NV12 frames, one persistent launch for one sequence or for a
+// batch of sequences of different tables and resolutions.
 //
-// What it computes (per sampled element k, frame slot[k]):
+// What it computes (per sampled element k of a sequence, frame slot[k]):
 //   R = clamp((298(Y-16) + 409(V-128) + 128) >> 8, 0, 255)
 //   G = clamp((298(Y-16) - 100(U-128) - 208(V-128) + 128) >> 8, 0, 255)
 //   B = clamp((298(Y-16) + 516(U-128) + 128) >> 8, 0, 255)
@@ -10,14 +11,15 @@
 //   flag[k] = 2*score[k] > W*H                                          Sec. 5.2 shots)
 //
 // Design (B300):
-//  * Work split: the sequence is a flat list of "row pairs" (two luma rows and
-//    the chroma row they share) of all sampled frames.  CTA b takes one
-//    contiguous range of it, so every CTA does the same work and crosses only a
-//    few frame boundaries (the paper's work packets, Sec. 4.1, reduced to one
-//    contiguous packet per CTA).
-//  * One CTA per SM: a producer warp streams the range through kStages
+//  * Work queue: the work is a list of items, each a range of "row pairs" (two
+//    luma rows and the chroma row they share) of one frame of one sequence
+//    (the paper's work packets, Sec. 4.1).  Each CTA's producer warp pops items
+//    with an atomic counter; the last CTA to find the queue empty resets it, so
+//    a launch leaves the counters zero and needs no memset (graph replays too).
+//  * One CTA per SM: the producer streams each item through kStages
 //    shared-memory chunks with 1-D bulk copies (TMA engine), completion on
-//    mbarriers; 16 consumer warps convert and count.
+//    mbarriers, with the chunk's description (sequence, element, rows) in
+//    shared memory beside the data; 16 consumer warps convert and count.
 //  * The bin needs no clamp: with x = 16*(298Y + k_c) + offset, x >> 16 is an
 //    "extended" bin covering every byte triple; extended bins outside [0,16)
 //    fold into bins 0 and 15 when the table is flushed
@@ -28,12 +30,12 @@
 //    owns a column ([row][lane], 256-byte rows); four warps share a table
 //    region (two column halves x two 16-bit counter halves), so the reductions
 //    never conflict on a bank and 16 warps fit in shared memory.
-//  * At the end of each frame segment the table is flushed (lane columns and
-//    counter halves summed, extended bins folded) and published: directly to
-//    hist[k] when the CTA counted the whole frame, else through an
-//    accumulator that the CTA completing the frame turns into hist[k].  The
-//    CTA completing the second frame of a consecutive pair computes that
-//    pair's score.  Completion uses counters; no CTA waits for another.
+//  * After each item the table is flushed (lane columns and counter halves
+//    summed, extended bins folded) and published: directly to hist[k] when the
+//    item is the whole frame, else through an accumulator that the CTA
+//    completing the frame turns into hist[k].  The CTA completing the second
+//    frame of a consecutive pair computes that pair's score.  Completion uses
+//    counters; no CTA waits for another.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,30 +64,19 @@ constexpr int32_t kCB = 16 * (-516 * 128 + 128 - 298 * 16 + kOffB * 4096);      
 constexpr int32_t kCG = 16 * (100 * 128 + 208 * 128 + 128 - 298 * 16 + kOffG * 4096);  // 1277440
 static_assert(kCR == 5632 && kCB == 48640 && kCG == 1277440, "chroma constants");
 
-constexpr int kNT = kConsumerWarps * 32;          // consumer threads
+constexpr int kNT = kConsumerThreads;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
-struct HistArgs {
-    const uint8_t* nv12;
-    int64_t stride;
-    int W, H;
-    const int32_t* slot;
-    int64_t n;
-    int chunk_rows, stage_bytes, seg_rows;
-    int64_t rp_per_cta;
-    uint32_t* hist;
-    uint32_t* score;
-    uint8_t* flag;
-    uint32_t* partial;
-    uint32_t* done;
-    uint32_t* pair;
-    int* status;
-    int64_t pixel_count;
+// Description of one staged chunk, written by the producer before it arms the
+// stage's barrier.  job < 0 marks the end of the CTA's work.
+struct ChunkMeta {
+    int32_t job, k, rows, seg_end, seg_rp, pad[3];
 };
 
 struct Smem {
     uint8_t* tab;
     uint8_t* stages;
+    ChunkMeta* meta;    // [kStages]
     uint32_t* acc;      // [48]
     uint64_t* full;     // [kStages]
     uint64_t* empty;    // [kStages]
@@ -96,101 +87,142 @@ __device__ __forceinline__ Smem carve(uint8_t* smem, int stage_bytes) {
     Smem s;
     s.tab = smem;
     s.stages = smem + kTabBytes;
-    s.acc = reinterpret_cast<uint32_t*>(s.stages + kStages * stage_bytes);
+    s.meta = reinterpret_cast<ChunkMeta*>(s.stages + kStages * stage_bytes);
+    s.acc = reinterpret_cast<uint32_t*>(s.meta + kStages);
     s.full = reinterpret_cast<uint64_t*>(s.acc + 64);
     s.empty = s.full + kStages;
     s.abort_flag = reinterpret_cast<int*>(s.empty + kStages);
     return s;
 }
+static_assert(kStages * sizeof(ChunkMeta) + 64 * 4 + 2 * kStages * 8 + 16 <= kSmemMisc, "misc smem");
 
-__device__ __forceinline__ void fail(const HistArgs& a, const Smem& s) {
+__device__ __forceinline__ const Job& job_of(const Launch& L, int j) { return L.jobs ? L.jobs[j] : L.job0; }
+
+__device__ __forceinline__ void fail(const Launch& L, const Smem& s) {
     *reinterpret_cast<volatile int*>(s.abort_flag) = 1;
-    atomicOr(a.status, kStatusTimeout);
+    atomicOr(L.status, kStatusTimeout);
 }
 
 __device__ __forceinline__ bool aborted(const Smem& s) {
     return *reinterpret_cast<volatile int*>(s.abort_flag) != 0;
 }
 
-// Walks a CTA's contiguous range of row pairs chunk by chunk.  A chunk never
-// crosses a frame; a segment (rows counted between two flushes) ends at a frame
-// boundary, at the end of the range, or after seg_rows rows.
-struct Walker {
-    int64_t g, g_end;  // global row-pair cursor and end
-    int64_t k;         // element of the cursor
-    int rp;            // row pair of the cursor within its frame
-    int seg;           // row pairs counted in the current segment
-    int hp, crp, srp;  // row pairs per frame, per chunk, per segment (max)
+__device__ __forceinline__ Item item_at(const Launch& L, int64_t i) {
+    if (L.items) return L.items[i];
+    const Job& J = L.job0;
+    Item it;
+    it.job = 0;
+    it.k = static_cast<int32_t>(i / J.items_per_frame);
+    const int part = static_cast<int>(i - static_cast<int64_t>(it.k) * J.items_per_frame);
+    it.rp0 = part * J.item_rp;
+    it.nrp = min(J.item_rp, J.H / 2 - it.rp0);
+    return it;
+}
 
-    __device__ __forceinline__ void init(const HistArgs& a) {
-        hp = a.H / 2;
-        crp = a.chunk_rows / 2;
-        srp = a.seg_rows / 2;
-        const int64_t total = a.n * hp;
-        g = blockIdx.x * a.rp_per_cta;
-        g_end = min(g + a.rp_per_cta, total);
-        k = g / hp;
-        rp = static_cast<int>(g - k * hp);
-        seg = 0;
-    }
-    // Next chunk: element, first luma row, luma rows, whether it ends a segment
-    // and (then) the row pairs of the segment.
-    __device__ __forceinline__ bool next(int64_t& ck, int& r, int& rows, bool& seg_end, int& seg_rp) {
-        if (g >= g_end) return false;
-        int m = min(crp, hp - rp);
-        if (g_end - g < m) m = static_cast<int>(g_end - g);
-        m = min(m, srp - seg);
-        ck = k;
-        r = 2 * rp;
-        rows = 2 * m;
-        g += m;
-        rp += m;
-        seg += m;
-        seg_end = (rp == hp) || (g == g_end) || (seg == srp);
-        seg_rp = seg;
-        if (seg_end) seg = 0;
-        if (rp == hp) {
-            rp = 0;
-            ++k;
+// ---------------------------------------------------------------------------
+// producer: one thread walks this CTA's work (popped items, or one contiguous
+// range of row pairs) and issues the bulk copies of its chunks
+// ---------------------------------------------------------------------------
+
+// Stage one chunk: rows [r, r + rows) of element k of job j.  Returns false
+// when the wait for the stage gave up.
+__device__ __forceinline__ bool stage_chunk(const Launch& L, const Smem& s, uint32_t it, int j, const Job& J,
+                                            int32_t k, int r, int rows, bool seg_end, int seg_rp) {
+    const uint32_t st = it % kStages;
+    if (it >= static_cast<uint32_t>(kStages)) {
+        if (!ptx::mbar_wait_bounded(&s.empty[st], ((it / kStages) - 1) & 1u, kWaitLimitNs)) {
+            fail(L, s);
+            return false;
         }
-        return true;
     }
-};
+    const uint8_t* frame = J.nv12 + static_cast<int64_t>(J.slot[k]) * J.stride;
+    ChunkMeta& m = s.meta[st];
+    m.job = j;
+    m.k = k;
+    m.rows = rows;
+    m.seg_end = seg_end;
+    m.seg_rp = seg_rp;
+    uint8_t* dst = s.stages + st * L.stage_bytes;
+    const uint32_t by = static_cast<uint32_t>(rows) * J.W;
+    const uint32_t buv = by / 2;
+    ptx::mbar_arrive_expect_tx(&s.full[st], by + buv);
+    ptx::bulk_g2s(dst, frame + static_cast<int64_t>(r) * J.W, by, &s.full[st]);
+    ptx::bulk_g2s(dst + J.chunk_rows * J.W, frame + static_cast<int64_t>(J.W) * J.H + (r / 2) * J.W, buv,
+                  &s.full[st]);
+    return true;
+}
 
-// ---------------------------------------------------------------------------
-// producer: one thread issues the bulk copies of every chunk
-// ---------------------------------------------------------------------------
-__device__ void produce(const HistArgs& a, const Smem& s) {
-    Walker w;
-    w.init(a);
+__device__ void produce(const Launch& L, const Smem& s) {
     uint32_t it = 0, issued = 0;
-    int64_t k;
-    int r, rows, seg_rp;
-    bool seg_end;
-    while (w.next(k, r, rows, seg_end, seg_rp)) {
-        const uint32_t st = it % kStages;
-        if (it >= static_cast<uint32_t>(kStages) && !aborted(s)) {
-            if (!ptx::mbar_wait_bounded(&s.empty[st], ((it / kStages) - 1) & 1u, kWaitLimitNs)) fail(a, s);
+    if (L.rp_per_cta > 0) {
+        // Contiguous split of job0's row pairs: every CTA does the same work and
+        // flushes only at frame edges or every item_rp row pairs (16-bit bound).
+        const Job& J = L.job0;
+        const int hp = J.H / 2, crp = J.chunk_rows / 2, srp = J.item_rp;
+        int64_t g = blockIdx.x * L.rp_per_cta;
+        const int64_t g_end = min(g + L.rp_per_cta, J.n * hp);
+        int64_t k = g / hp;
+        int rp = static_cast<int>(g - k * hp);
+        int seg = 0;
+        while (g < g_end && !aborted(s)) {
+            int m = min(crp, hp - rp);
+            if (g_end - g < m) m = static_cast<int>(g_end - g);
+            m = min(m, srp - seg);
+            const int nseg = seg + m;
+            const bool seg_end = (rp + m == hp) || (g + m == g_end) || (nseg == srp);
+            if (!stage_chunk(L, s, it, 0, J, static_cast<int32_t>(k), 2 * rp, 2 * m, seg_end, nseg)) break;
+            issued = ++it;
+            g += m;
+            rp += m;
+            seg = seg_end ? 0 : nseg;
+            if (rp == hp) {
+                rp = 0;
+                ++k;
+            }
         }
-        if (!aborted(s)) {
-            const uint8_t* frame = a.nv12 + static_cast<int64_t>(a.slot[k]) * a.stride;
-            uint8_t* dst = s.stages + st * a.stage_bytes;
-            const uint32_t by = static_cast<uint32_t>(rows) * a.W;
-            const uint32_t buv = by / 2;
-            ptx::mbar_arrive_expect_tx(&s.full[st], by + buv);
-            ptx::bulk_g2s(dst, frame + static_cast<int64_t>(r) * a.W, by, &s.full[st]);
-            ptx::bulk_g2s(dst + a.chunk_rows * a.W, frame + static_cast<int64_t>(a.W) * a.H + (r / 2) * a.W, buv,
-                          &s.full[st]);
-            issued = it + 1;
+    } else {
+        while (!aborted(s)) {
+            const uint64_t i = atomicAdd(reinterpret_cast<unsigned long long*>(L.queue), 1ull);
+            if (i >= static_cast<uint64_t>(L.n_items)) break;
+            const Item item = item_at(L, static_cast<int64_t>(i));
+            const Job& J = job_of(L, item.job);
+            const int r_end = 2 * (item.rp0 + item.nrp);
+            bool ok = true;
+            for (int r = 2 * item.rp0; r < r_end && ok && !aborted(s); r += J.chunk_rows) {
+                const int rows = min(J.chunk_rows, r_end - r);
+                ok = stage_chunk(L, s, it, item.job, J, item.k, r, rows, r + rows == r_end, item.nrp);
+                if (ok) issued = ++it;
+            }
         }
-        ++it;
+        // the last CTA done with the queue resets it (every other CTA has made
+        // its last pop by then)
+        const uint32_t old = atomicAdd(&L.queue[2], 1u);
+        if (old == gridDim.x - 1) {
+            atomicExch(reinterpret_cast<unsigned long long*>(L.queue), 0ull);
+            atomicExch(&L.queue[2], 0u);
+        }
     }
-    // Let every copy this CTA issued land before the CTA can exit (copies stop
-    // being issued after an abort, so chunks [0, issued) are the issued ones).
+    // Let every copy this CTA issued land (copies stop being issued after an
+    // abort, so chunks [0, issued) are the issued ones).  This comes before the
+    // end marker below: a parity wait only tells the last two phases apart, and
+    // the marker completes one more phase of a stage's barrier.
     for (uint32_t j = issued > kStages ? issued - kStages : 0; j < issued; ++j) {
         if (!ptx::mbar_wait_bounded(&s.full[j % kStages], (j / kStages) & 1u, kWaitLimitNs)) {
-            fail(a, s);
+            fail(L, s);
             break;
+        }
+    }
+    // Tell the consumers: a stage with job = -1 and no bytes.
+    if (!aborted(s)) {
+        const uint32_t st = it % kStages;
+        bool ok = true;
+        if (it >= static_cast<uint32_t>(kStages)) {
+            ok = ptx::mbar_wait_bounded(&s.empty[st], ((it / kStages) - 1) & 1u, kWaitLimitNs);
+            if (!ok) fail(L, s);
+        }
+        if (ok) {
+            s.meta[st].job = -1;
+            ptx::mbar_arrive(&s.full[st]);
         }
     }
 }
@@ -283,36 +315,36 @@ __device__ __forceinline__ void flush_table(uint8_t* tab, uint32_t* acc, int cti
 
 // Score of element k from its histogram (h0: bins lane, h1: bins 32+lane) and
 // a neighbour's, read from global memory.
-__device__ __forceinline__ void write_score(const HistArgs& a, int64_t k, uint32_t h0, uint32_t h1,
-                                            const uint32_t* other, int lane) {
+__device__ __forceinline__ void write_score(const Job& J, int64_t k, uint32_t h0, uint32_t h1, const uint32_t* other,
+                                            int lane) {
     const uint32_t p0 = ptx::ld_cg_u32(other + lane);
     const uint32_t p1 = lane < 16 ? ptx::ld_cg_u32(other + 32 + lane) : 0u;
     uint32_t d = (h0 > p0 ? h0 - p0 : p0 - h0);
     if (lane < 16) d += (h1 > p1 ? h1 - p1 : p1 - h1);
     const uint32_t s = __reduce_add_sync(0xffffffffu, d);
     if (lane == 0) {
-        a.score[k] = s;
-        a.flag[k] = (2ull * s > static_cast<uint64_t>(a.pixel_count)) ? 1 : 0;
+        J.score[k] = s;
+        J.flag[k] = (2ull * s > static_cast<uint64_t>(J.W) * J.H) ? 1 : 0;
     }
 }
 
-// One warp, after the flush: publish the segment's counts of element k (seg_rp
+// One warp, after the flush: publish an item's counts of element k (seg_rp
 // row pairs), complete the frame and the scores it unblocks.
-__device__ void publish(const HistArgs& a, int64_t k, int seg_rp, uint32_t* acc, int lane) {
+__device__ void publish(const Job& J, int64_t k, int seg_rp, uint32_t* acc, int lane) {
     uint32_t h0 = acc[lane];
     uint32_t h1 = lane < 16 ? acc[32 + lane] : 0u;
     acc[lane] = 0;
     if (lane < 16) acc[32 + lane] = 0;
-    const int hp = a.H / 2;
+    const int hp = J.H / 2;
     if (seg_rp != hp) {
         // part of the frame: accumulate; the CTA completing the frame finishes it
-        uint32_t* pk = a.partial + k * 48;
+        uint32_t* pk = J.partial + k * 48;
         if (h0) atomicAdd(pk + lane, h0);
         if (lane < 16 && h1) atomicAdd(pk + 32 + lane, h1);
         __threadfence();
         __syncwarp();
         uint32_t old = 0;
-        if (lane == 0) old = atomicAdd(&a.done[k], static_cast<uint32_t>(seg_rp));
+        if (lane == 0) old = atomicAdd(&J.done[k], static_cast<uint32_t>(seg_rp));
         old = __shfl_sync(0xffffffffu, old, 0);
         if (old + static_cast<uint32_t>(seg_rp) != static_cast<uint32_t>(hp)) return;
         __threadfence();
@@ -320,36 +352,36 @@ __device__ void publish(const HistArgs& a, int64_t k, int seg_rp, uint32_t* acc,
         h1 = lane < 16 ? ptx::ld_cg_u32(pk + 32 + lane) : 0u;
         pk[lane] = 0;  // leave the accumulator zeroed for the next call
         if (lane < 16) pk[32 + lane] = 0;
-        if (lane == 0) a.done[k] = 0;
+        if (lane == 0) J.done[k] = 0;
     }
-    a.hist[k * 48 + lane] = h0;
-    if (lane < 16) a.hist[k * 48 + 32 + lane] = h1;
-    if (!a.score) return;
+    J.hist[k * 48 + lane] = h0;
+    if (lane < 16) J.hist[k * 48 + 32 + lane] = h1;
+    if (!J.score) return;
     __threadfence();
     __syncwarp();
     if (k == 0) {
         if (lane == 0) {
-            a.score[0] = 0;
-            a.flag[0] = 0;
+            J.score[0] = 0;
+            J.flag[0] = 0;
         }
     } else {
         uint32_t old = 0;
-        if (lane == 0) old = atomicAdd(&a.pair[k], 1u);
+        if (lane == 0) old = atomicAdd(&J.pair[k], 1u);
         old = __shfl_sync(0xffffffffu, old, 0);
         if (old == 1) {
             __threadfence();
-            write_score(a, k, h0, h1, a.hist + (k - 1) * 48, lane);
-            if (lane == 0) a.pair[k] = 0;
+            write_score(J, k, h0, h1, J.hist + (k - 1) * 48, lane);
+            if (lane == 0) J.pair[k] = 0;
         }
     }
-    if (k + 1 < a.n) {
+    if (k + 1 < J.n) {
         uint32_t old = 0;
-        if (lane == 0) old = atomicAdd(&a.pair[k + 1], 1u);
+        if (lane == 0) old = atomicAdd(&J.pair[k + 1], 1u);
         old = __shfl_sync(0xffffffffu, old, 0);
         if (old == 1) {
             __threadfence();
-            write_score(a, k + 1, h0, h1, a.hist + (k + 1) * 48, lane);
-            if (lane == 0) a.pair[k + 1] = 0;
+            write_score(J, k + 1, h0, h1, J.hist + (k + 1) * 48, lane);
+            if (lane == 0) J.pair[k + 1] = 0;
         }
     }
 }
@@ -360,7 +392,7 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
     return v;
 }
 
-__device__ void consume(const HistArgs& a, const Smem& s, int warp, int lane) {
+__device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
     const int ctid = warp * 32 + lane;
     const int region = warp / kGroupWarps;
     const uint32_t lanereg = static_cast<uint32_t>(lane * 4 + (warp & 1) * 128);
@@ -370,41 +402,39 @@ __device__ void consume(const HistArgs& a, const Smem& s, int warp, int lane) {
     const uint32_t cR = static_cast<uint32_t>(kCR) + rowbase + (static_cast<uint32_t>(kBaseR) << 16);
     const uint32_t cG = static_cast<uint32_t>(kCG) + rowbase + (static_cast<uint32_t>(kBaseG) << 16);
     const uint32_t cB = static_cast<uint32_t>(kCB) + rowbase + (static_cast<uint32_t>(kBaseB) << 16);
-    const int W = a.W;
-    const int wv = W / 16;
-    const int sp = kNT / wv, sc = kNT % wv;
-    // byte step of the luma / chroma address per kNT units; a column wrap adds
-    // one more row pair and removes a row of columns: luma +2W-W, chroma +W-W
-    const uint32_t dY = static_cast<uint32_t>(sp * 2 * W + sc * 16);
-    const uint32_t dU = static_cast<uint32_t>(sp * W + sc * 16);
     const uint32_t stages = ptx::smem_u32(s.stages);
-    Walker wk;
-    wk.init(a);
     uint32_t it = 0;
     int rot = 0;
-    int64_t k;
-    int r, rows, seg_rp;
-    bool seg_end;
-    while (wk.next(k, r, rows, seg_end, seg_rp)) {
+    for (;; ++it) {
         const uint32_t st = it % kStages;
-        if (!aborted(s)) {
-            if (!ptx::mbar_wait_bounded(&s.full[st], (it / kStages) & 1u, kWaitLimitNs)) fail(a, s);
+        // Every consumer reaches the same chunk before any of them gives up, so
+        // they leave the loop together (no named barrier is left half-full).
+        if (aborted(s)) break;
+        if (!ptx::mbar_wait_bounded(&s.full[st], (it / kStages) & 1u, kWaitLimitNs)) {
+            fail(L, s);
+            break;
         }
-        const uint32_t ybase = stages + st * a.stage_bytes;
-        const int units = (rows / 2) * wv;
+        const ChunkMeta m = s.meta[st];
+        if (m.job < 0) break;
+        const Job& J = job_of(L, m.job);
+        const int W = J.W, wv = J.wv, sc = J.sc;
+        const uint32_t ybase = stages + st * L.stage_bytes;
+        const int units = (m.rows / 2) * wv;
         int u = ctid - rot;
         if (u < 0) u += kNT;
-        const int p0 = u / wv;
+        const int p0 = static_cast<int>((static_cast<float>(u) + 0.5f) * J.inv_wv);
         int c = u - p0 * wv;
         uint32_t ya = ybase + p0 * 2 * W + c * 16;
-        uint32_t ua = ybase + a.chunk_rows * W + p0 * W + c * 16;
+        uint32_t ua = ybase + J.chunk_rows * W + p0 * W + c * 16;
         for (; u < units; u += kNT) {
             const uint4 y0 = lds128(ya);
             const uint4 y1 = lds128(ya + W);
             const uint4 uv = lds128(ua);
             count_unit(lanereg, inc, cR, cG, cB, y0, y1, uv);
-            ya += dY;
-            ua += dU;
+            // next unit: kNT units on; a column wrap adds one more row pair and
+            // removes a row of columns (luma +2W-W, chroma +W-W)
+            ya += J.dY;
+            ua += J.dU;
             c += sc;
             if (c >= wv) {
                 c -= wv;
@@ -414,19 +444,18 @@ __device__ void consume(const HistArgs& a, const Smem& s, int warp, int lane) {
         rot = (rot + units) % kNT;
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&s.empty[st]);
-        ++it;
-        if (seg_end) {
-            ptx::named_bar_sync(1, kNT);  // every consumer has counted the segment
+        if (m.seg_end) {
+            ptx::named_bar_sync(1, kNT);  // every consumer has counted the item
             flush_table(s.tab, s.acc, ctid);
             ptx::named_bar_sync(1, kNT);  // table zeroed, acc complete
-            if (warp == 0) publish(a, k, seg_rp, s.acc, lane);
+            if (warp == 0) publish(J, m.k, m.seg_rp, s.acc, lane);
         }
     }
 }
 
-__global__ void __launch_bounds__(kHistThreads, 1) hist_kernel(HistArgs a) {
+__global__ void __launch_bounds__(kHistThreads, 1) hist_kernel(const __grid_constant__ Launch L) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    const Smem s = carve(smem, a.stage_bytes);
+    const Smem s = carve(smem, L.stage_bytes);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kTabBytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
@@ -441,10 +470,10 @@ __global__ void __launch_bounds__(kHistThreads, 1) hist_kernel(HistArgs a) {
     }
     __syncthreads();
     if (warp == kConsumerWarps) {
-        if (lane == 0) produce(a, s);
+        if (lane == 0) produce(L, s);
         return;
     }
-    consume(a, s, warp, lane);
+    consume(L, s, warp, lane);
 }
 
 // One warp per element: score[k] from hist[k-1], hist[k].
@@ -474,28 +503,119 @@ int g_attr_device = -1;
 
 }  // namespace
 
+int chunk_rows_for(int W, int H, int requested) {
+    const int cr_max = std::max(2, (kStageBudget / (W * 3 / 2)) & ~1);
+    int cr = requested;
+    if (cr <= 0 || cr > cr_max) cr = cr_max;
+    return std::min(cr, H);
+}
+
+void fill_job_consts(Job& j) {
+    j.wv = j.W / 16;
+    j.sp = kNT / j.wv;
+    j.sc = kNT % j.wv;
+    j.dY = static_cast<uint32_t>(j.sp * 2 * j.W + j.sc * 16);
+    j.dU = static_cast<uint32_t>(j.sp * j.W + j.sc * 16);
+    j.inv_wv = 1.0f / static_cast<float>(j.wv);
+}
+
+void choose_items(Job& j, int64_t item_px, int grid) {
+    const int hp = j.H / 2;
+    const int64_t frame_px = static_cast<int64_t>(j.W) * j.H;
+    int64_t ipf;
+    if (item_px > 0) {
+        ipf = (frame_px + item_px - 1) / item_px;
+    } else {
+        // whole frames when there are plenty of them; else split frames so the
+        // queue holds about 8 items per CTA
+        const int64_t want = 8LL * grid;
+        const int64_t n = std::max<int64_t>(j.n, 1);
+        ipf = n >= want ? 1 : (want + n - 1) / n;
+    }
+    // an item stays under the 16-bit counter bound and holds at least one chunk
+    const int64_t min_ipf = (frame_px + kItemPixelsMax - 1) / kItemPixelsMax;
+    const int64_t max_ipf = std::max(1, hp / std::max(1, j.chunk_rows / 2));
+    ipf = std::max(min_ipf, std::min(ipf, max_ipf));
+    ipf = std::max<int64_t>(1, std::min<int64_t>(ipf, hp));
+    j.item_rp = static_cast<int32_t>((hp + ipf - 1) / ipf);
+    j.items_per_frame = (hp + j.item_rp - 1) / j.item_rp;
+}
+
+scn_status prepare_hist() {
+    int dev = 0;
+    SCN_CUDA_TRY(cudaGetDevice(&dev));
+    if (g_attr_device != dev) {
+        SCN_CUDA_TRY(cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        g_attr_device = dev;
+    }
+    return SCN_OK;
+}
+
+scn_status launch_hist(const Launch& L, cudaStream_t st) {
+    const size_t smem = static_cast<size_t>(kTabBytes) + static_cast<size_t>(kStages) * L.stage_bytes + kSmemMisc;
+    if (smem > static_cast<size_t>(kSmemLimit)) return SCN_EUNSUPPORTED;
+    if (L.n_items <= 0 || L.grid <= 0) return SCN_OK;
+    const scn_status sp = prepare_hist();
+    if (sp != SCN_OK) return sp;
+    hist_kernel<<<L.grid, kHistThreads, smem, st>>>(L);
+    SCN_CUDA_TRY(cudaGetLastError());
+    return SCN_OK;
+}
+
 HistShape resolve_hist_shape(const scn_seq* s) {
     HistShape sh;
     const int W = s->table->W, H = s->table->H;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
-    // chunk rows: largest even count whose NV12 bytes fit one stage
-    int cr = s->tune.chunk_rows;
-    const int cr_max = std::max(2, (kStageBudget / (W * 3 / 2)) & ~1);
-    if (cr <= 0 || cr > cr_max) cr = cr_max;
-    cr = std::min(cr, H);
-    sh.chunk_rows = cr;
-    // rows between flushes: bounded so a 16-bit lane counter cannot overflow
-    const int64_t seg = std::max<int64_t>(2, (kSegmentPixels / W) & ~int64_t(1));
-    sh.seg_rows = static_cast<int>(std::min<int64_t>(seg, H));
-    const int64_t total_rp = std::max<int64_t>(s->n, 1) * (H / 2);
+    Job j{};
+    j.W = W;
+    j.H = H;
+    j.n = std::max<int64_t>(s->n, 1);
+    j.chunk_rows = chunk_rows_for(W, H, s->tune.chunk_rows);
     const int grid = s->tune.grid > 0 ? s->tune.grid : sms;
-    sh.grid = static_cast<int>(std::min<int64_t>(grid, total_rp));
-    sh.rp_per_cta = (total_rp + sh.grid - 1) / sh.grid;
-    sh.grid = static_cast<int>((total_rp + sh.rp_per_cta - 1) / sh.rp_per_cta);
-    sh.stage_bytes = ((cr * W * 3 / 2) + 127) & ~127;
+    choose_items(j, static_cast<int64_t>(s->tune.item_kpx) * 1000, grid);
+    sh.chunk_rows = j.chunk_rows;
+    sh.item_rp = j.item_rp;
+    sh.items_per_frame = j.items_per_frame;
+    const int64_t items = j.n * j.items_per_frame;
+    sh.grid = static_cast<int>(std::min<int64_t>(grid, items));
+    sh.rp_per_cta = 0;
+    if (s->tune.item_kpx == 0 && j.n < 8LL * grid) {
+        // no item size asked for and too few frames for whole-frame queue items:
+        // one contiguous range of row pairs per CTA (perfect balance), flushed at
+        // frame edges and at most every kItemPixelsMax pixels
+        const int64_t total_rp = j.n * (H / 2);
+        const int g = static_cast<int>(std::min<int64_t>(grid, total_rp));
+        sh.rp_per_cta = (total_rp + g - 1) / g;
+        sh.grid = static_cast<int>((total_rp + sh.rp_per_cta - 1) / sh.rp_per_cta);
+        sh.item_rp = static_cast<int>(std::min<int64_t>(H / 2, std::max<int64_t>(1, kItemPixelsMax / (2LL * W))));
+    }
+    sh.stage_bytes = ((j.chunk_rows * W * 3 / 2) + 127) & ~127;
     sh.smem = static_cast<size_t>(kTabBytes) + static_cast<size_t>(kStages) * sh.stage_bytes + kSmemMisc;
     return sh;
+}
+
+// A single-sequence launch description (outputs and scratch filled in by the caller).
+static Launch single_launch(const scn_table* t, int64_t n, const int32_t* slot, const HistShape& sh) {
+    Launch L{};
+    Job& j = L.job0;
+    j.nv12 = t->d_nv12;
+    j.stride = t->frame_stride;
+    j.slot = slot;
+    j.n = n;
+    j.W = t->W;
+    j.H = t->H;
+    j.chunk_rows = sh.chunk_rows;
+    j.item_rp = sh.item_rp;
+    j.items_per_frame = sh.items_per_frame;
+    fill_job_consts(j);
+    L.jobs = nullptr;
+    L.items = nullptr;
+    L.n_items = n * sh.items_per_frame;
+    L.rp_per_cta = sh.rp_per_cta;
+    L.stage_bytes = sh.stage_bytes;
+    L.grid = sh.grid;
+    return L;
 }
 
 static scn_status run_hist(scn_seq* s, uint32_t* d_hist, uint32_t* d_score, uint8_t* d_flag, void* stream) {
@@ -504,35 +624,16 @@ static scn_status run_hist(scn_seq* s, uint32_t* d_hist, uint32_t* d_score, uint
         return SCN_EINVAL;
     if (s->n == 0) return SCN_OK;
     const HistShape sh = resolve_hist_shape(s);
-    if (sh.smem > static_cast<size_t>(kSmemLimit)) return SCN_EUNSUPPORTED;
-    int dev = 0;
-    SCN_CUDA_TRY(cudaGetDevice(&dev));
-    if (g_attr_device != dev) {
-        SCN_CUDA_TRY(cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-        g_attr_device = dev;
-    }
-    HistArgs a;
-    a.nv12 = s->table->d_nv12;
-    a.stride = s->table->frame_stride;
-    a.W = s->table->W;
-    a.H = s->table->H;
-    a.slot = s->d_slot;
-    a.n = s->n;
-    a.chunk_rows = sh.chunk_rows;
-    a.stage_bytes = sh.stage_bytes;
-    a.seg_rows = sh.seg_rows;
-    a.rp_per_cta = sh.rp_per_cta;
-    a.hist = d_hist;
-    a.score = d_score;
-    a.flag = d_flag;
-    a.partial = s->d_partial;
-    a.done = s->d_done;
-    a.pair = s->d_pair;
-    a.status = s->d_status;
-    a.pixel_count = static_cast<int64_t>(a.W) * a.H;
-    hist_kernel<<<sh.grid, kHistThreads, sh.smem, static_cast<cudaStream_t>(stream)>>>(a);
-    SCN_CUDA_TRY(cudaGetLastError());
-    return SCN_OK;
+    Launch L = single_launch(s->table, s->n, s->d_slot, sh);
+    L.job0.hist = d_hist;
+    L.job0.score = d_score;
+    L.job0.flag = d_flag;
+    L.job0.partial = s->d_partial;
+    L.job0.done = s->d_done;
+    L.job0.pair = s->d_pair;
+    L.queue = s->d_queue;
+    L.status = s->d_status;
+    return launch_hist(L, static_cast<cudaStream_t>(stream));
 }
 
 }  // namespace scn
@@ -573,7 +674,8 @@ namespace scn {
 namespace {
 
 constexpr int64_t kNoAllocMaxElems = 16384;
-// per element: 48 partial-histogram words + 1 done counter + 1 pair counter; + status
+// per element: 48 partial-histogram words + 1 done counter + 1 pair counter;
+// then the status word and the work-queue counters
 constexpr int64_t kNoAllocWords = kNoAllocMaxElems * 50 + 64;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
@@ -608,10 +710,6 @@ extern "C" scn_status scn_hist_scores_noalloc(const uint8_t* d_nv12, int32_t wid
         SCN_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
     }
-    if (g_attr_device != dev) {
-        SCN_CUDA_TRY(cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-        g_attr_device = dev;
-    }
     // the launch shape of the regular entry point, from a stack-only description
     scn_table t;
     t.W = width;
@@ -623,31 +721,18 @@ extern "C" scn_status scn_hist_scores_noalloc(const uint8_t* d_nv12, int32_t wid
     q.table = &t;
     q.n = n;
     const HistShape sh = resolve_hist_shape(&q);
-    if (sh.smem > static_cast<size_t>(kSmemLimit)) return SCN_EUNSUPPORTED;
-    // scratch of this call: partial [n][48], done [n], pair [n], status; zeroed first
+    // scratch of this call: partial [n][48], done [n], pair [n], status, queue; zeroed first
     uint32_t* base = g_noalloc_ptr[dev];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    SCN_CUDA_TRY(cudaMemsetAsync(base, 0, static_cast<size_t>(n * 50 + 1) * sizeof(uint32_t), st));
-    HistArgs a;
-    a.nv12 = d_nv12;
-    a.stride = frame_stride;
-    a.W = width;
-    a.H = height;
-    a.slot = d_slots;
-    a.n = n;
-    a.chunk_rows = sh.chunk_rows;
-    a.stage_bytes = sh.stage_bytes;
-    a.seg_rows = sh.seg_rows;
-    a.rp_per_cta = sh.rp_per_cta;
-    a.hist = d_hist;
-    a.score = d_score;
-    a.flag = d_flag;
-    a.partial = base;
-    a.done = base + n * 48;
-    a.pair = base + n * 49;
-    a.status = reinterpret_cast<int*>(base + n * 50);
-    a.pixel_count = static_cast<int64_t>(width) * height;
-    hist_kernel<<<sh.grid, kHistThreads, sh.smem, st>>>(a);
-    SCN_CUDA_TRY(cudaGetLastError());
-    return SCN_OK;
+    SCN_CUDA_TRY(cudaMemsetAsync(base, 0, static_cast<size_t>(n * 50 + 8) * sizeof(uint32_t), st));
+    Launch L = single_launch(&t, n, d_slots, sh);
+    L.job0.hist = d_hist;
+    L.job0.score = d_score;
+    L.job0.flag = d_flag;
+    L.job0.partial = base;
+    L.job0.done = base + n * 48;
+    L.job0.pair = base + n * 49;
+    L.status = reinterpret_cast<int*>(base + n * 50);
+    L.queue = base + n * 50 + 2;  // 8-byte aligned: (n * 50 + 2) * 4 is a multiple of 8
+    return launch_hist(L, st);
 }

@@ -364,6 +364,7 @@ scn_status scn_sample(const scn_table* t, const scn_sample_spec* spec, scn_seq**
     s->d_pair = reinterpret_cast<uint32_t*>(p + b_slot + b_done);
     s->d_partial = reinterpret_cast<uint32_t*>(p + b_slot + b_done + b_pair);
     s->d_status = reinterpret_cast<int*>(p + b_slot + b_done + b_pair + b_part);
+    s->d_queue = reinterpret_cast<uint32_t*>(p + b_slot + b_done + b_pair + b_part + 64);
     e = cudaMemset(s->d_block, 0, total);
     if (e == cudaSuccess && s->n > 0)
         e = cudaMemcpy(s->d_slot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice);
@@ -407,7 +408,7 @@ scn_status scn_seq_sync_status(scn_seq* s, void* stream) {
 scn_status scn_seq_set_tune(scn_seq* s, const scn_tune* tune) {
     if (!s || !tune) return SCN_EINVAL;
     if (tune->chunk_rows < 0 || (tune->chunk_rows % 2)) return SCN_EINVAL;
-    if (tune->grid < 0 || tune->reserved != 0) return SCN_EINVAL;
+    if (tune->grid < 0 || tune->item_kpx < 0) return SCN_EINVAL;
     s->tune = *tune;
     return SCN_OK;
 }
@@ -417,7 +418,8 @@ scn_status scn_seq_get_tune(const scn_seq* s, scn_tune* tune) {
     const HistShape sh = resolve_hist_shape(s);
     tune->chunk_rows = sh.chunk_rows;
     tune->grid = sh.grid;
-    tune->reserved = 0;
+    tune->item_kpx = sh.rp_per_cta > 0 ? 0
+                                       : static_cast<int32_t>((static_cast<int64_t>(sh.item_rp) * 2 * s->table->W + 999) / 1000);
     return SCN_OK;
 }
 

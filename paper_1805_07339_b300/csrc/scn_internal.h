@@ -38,9 +38,11 @@ constexpr int kTabBytes = kRegions * kTabRowsPerRegion * 256;
 constexpr int kSmemLimit = 232448;                        // 227 KB opt-in per CTA
 constexpr int kSmemMisc = 1024;                           // accumulators + barriers + flags
 constexpr int kStageBudget = (kSmemLimit - kTabBytes - kSmemMisc) / kStages;
-// Pixels a CTA may count between two table flushes: keeps every 16-bit lane
-// counter below 2^16 (each of the 512 consumer threads sees at most 1/512 of them).
-constexpr int64_t kSegmentPixels = int64_t(1) << 24;
+constexpr int kConsumerThreads = kConsumerWarps * 32;
+// Pixels of one work item at most: the table is flushed after every item, and
+// this keeps every 16-bit lane counter below 2^16 (each of the 512 consumer
+// threads counts at most 1/512 of an item's pixels, plus one unit).
+constexpr int64_t kItemPixelsMax = int64_t(1) << 24;
 
 }  // namespace scn
 
@@ -70,17 +72,72 @@ struct scn_seq {
     uint32_t* d_pair = nullptr;      // per-element arrivals of the score stencil [n]
     uint32_t* d_partial = nullptr;   // [n][48] cross-CTA histogram accumulators (kept zero)
     int* d_status = nullptr;         // device status word
+    uint32_t* d_queue = nullptr;     // work-queue counters (2 words, left zero)
     scn_tune tune{0, 0, 0};          // 0 fields: chosen per call
 };
 
 namespace scn {
-// Launch shape resolved for a sequence (see scn_hist.cu).
+
+// One sampled sequence as the fused kernel sees it (host-filled, device-read).
+struct Job {
+    const uint8_t* nv12;   // frames of the table
+    int64_t stride;        // bytes between stored frames
+    const int32_t* slot;   // stored frame of each element [n]
+    uint32_t* hist;        // [n][48]
+    uint32_t* score;       // [n], null: histograms only
+    uint8_t* flag;         // [n]
+    uint32_t* partial;     // [n][48] cross-CTA accumulators (left zero)
+    uint32_t* done;        // [n] counted row pairs (left zero)
+    uint32_t* pair;        // [n] score stencil arrivals (left zero)
+    int64_t n;
+    int32_t W, H;
+    int32_t chunk_rows;    // luma rows per staged chunk (even)
+    int32_t item_rp;       // row pairs per work item
+    int32_t items_per_frame;
+    int32_t wv, sp, sc;    // 16-byte columns per row; consumer threads / wv; consumer threads % wv
+    uint32_t dY, dU;       // luma / chroma byte step per consumer-thread stride of units
+    float inv_wv;          // 1 / wv
+};
+
+// One work item: row pairs [rp0, rp0 + nrp) of element k of job `job`.
+struct Item {
+    int32_t job, k, rp0, nrp;
+};
+
+// Everything one launch of the fused kernel needs.
+struct Launch {
+    Job job0;              // the job of a single-sequence launch
+    const Job* jobs;       // device array of jobs (batched plans), null: job0 only
+    const Item* items;     // device array of items (batched plans), null: implicit items of job0
+    int64_t n_items;
+    int64_t rp_per_cta;    // > 0: no queue; CTA b takes row pairs [b*rp_per_cta, (b+1)*rp_per_cta) of job0
+    uint32_t* queue;       // [0..1] next item (64-bit), [2] CTAs done with the queue; left zero
+    int* status;           // device status word
+    int stage_bytes;       // bytes per stage (>= chunk_rows * W * 3/2 of every job)
+    int grid;
+};
+
+// Luma rows per chunk for width W (largest even count that fits a stage), or
+// the requested count when it is smaller.
+int chunk_rows_for(int W, int H, int requested);
+// Fill the derived consumer constants of a job (wv, sp, sc, dY, dU, inv_wv).
+void fill_job_consts(Job& j);
+// Row pairs per item and items per frame for a job, given a target of pixels
+// per item (0: automatic for n elements over grid CTAs).
+void choose_items(Job& j, int64_t item_px, int grid);
+// Launch the fused kernel.
+scn_status launch_hist(const Launch& L, cudaStream_t st);
+// One-time per-device kernel setup (shared-memory attribute); call outside stream capture.
+scn_status prepare_hist();
+
+// Launch shape resolved for a sequence.
 struct HistShape {
     int chunk_rows;      // luma rows per staged chunk (even)
     int grid;            // CTAs
+    int item_rp;         // row pairs per work item
+    int items_per_frame;
+    int64_t rp_per_cta;  // > 0: contiguous row-pair range per CTA instead of the queue
     int stage_bytes;     // bytes per stage buffer
-    int seg_rows;        // luma rows counted between two table flushes (even)
-    int64_t rp_per_cta;  // row pairs (2 luma rows + 1 chroma row) per CTA
     size_t smem;
 };
 HistShape resolve_hist_shape(const scn_seq* s);

@@ -49,7 +49,7 @@ class scn_sample_spec(ctypes.Structure):
 
 
 class scn_tune(ctypes.Structure):
-    _fields_ = [("chunk_rows", c_i32), ("grid", c_i32), ("reserved", c_i32)]
+    _fields_ = [("chunk_rows", c_i32), ("grid", c_i32), ("item_kpx", c_i32)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/scn.h
@@ -79,6 +79,16 @@ SIGNATURES = [
     ("scn_shot_scores", c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
     ("scn_hist_scores", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     ("scn_hist_scores_noalloc", c_i32, [c_vp, c_i32, c_i32, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp, c_vp]),
+    ("scn_plan_create", c_i32, [_P(c_vp), c_i32, _P(c_vp), _P(c_vp), _P(c_vp), _P(scn_tune), _P(c_vp)]),
+    ("scn_plan_destroy", c_i32, [c_vp]),
+    ("scn_plan_set_tune", c_i32, [c_vp, _P(scn_tune)]),
+    ("scn_plan_get_tune", c_i32, [c_vp, _P(scn_tune)]),
+    ("scn_plan_info", c_i32, [c_vp, _P(c_i64), _P(c_i64), _P(c_i64), _P(c_i32)]),
+    ("scn_plan_run", c_i32, [c_vp, c_vp]),
+    ("scn_plan_capture_graph", c_i32, [c_vp, c_vp]),
+    ("scn_plan_replay", c_i32, [c_vp, c_vp]),
+    ("scn_plan_sync_status", c_i32, [c_vp, c_vp]),
+    ("scn_plan_autotune", c_i32, [c_vp, c_i32, c_vp, _P(scn_tune), _P(ctypes.c_float)]),
     ("scn_resize_norm", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_i32, c_vp, c_vp]),
     ("scn_thumbs", c_i32, [c_vp, c_vp, c_vp]),
 ]
@@ -246,15 +256,15 @@ def scn_seq_sync_status(s: int, stream=None) -> int:
     return int(_lib.scn_seq_sync_status(s, _stream(stream)))
 
 
-def scn_seq_set_tune(s: int, chunk_rows: int = 0, grid: int = 0) -> None:
-    t = scn_tune(chunk_rows, grid, 0)
+def scn_seq_set_tune(s: int, chunk_rows: int = 0, grid: int = 0, item_kpx: int = 0) -> None:
+    t = scn_tune(chunk_rows, grid, item_kpx)
     _check(_lib.scn_seq_set_tune(s, ctypes.byref(t)), "scn_seq_set_tune")
 
 
 def scn_seq_get_tune(s: int) -> dict:
     t = scn_tune()
     _check(_lib.scn_seq_get_tune(s, ctypes.byref(t)), "scn_seq_get_tune")
-    return dict(chunk_rows=t.chunk_rows, grid=t.grid)
+    return dict(chunk_rows=t.chunk_rows, grid=t.grid, item_kpx=t.item_kpx)
 
 
 def scn_hist(s: int, hist, stream=None) -> None:
@@ -276,6 +286,61 @@ def scn_hist_scores_noalloc(nv12, width: int, height: int, frame_stride: int, sl
 def scn_shot_scores(hist, n: int, pixel_count: int, score, flag, stream=None) -> None:
     _check(_lib.scn_shot_scores(_ptr(hist), n, pixel_count, _ptr(score), _ptr(flag), _stream(stream)),
            "scn_shot_scores")
+
+
+def scn_plan_create(seqs, hists, scores, flags, tune: dict | None = None) -> int:
+    """seqs: sequence handles; hists/scores/flags: CUDA tensors (one per sequence)."""
+    n = len(seqs)
+    arr = lambda xs: (c_vp * n)(*[None if x is None else (x if isinstance(x, int) else x.data_ptr()) for x in xs])
+    t = scn_tune(**tune) if tune else None
+    h = c_vp()
+    _check(_lib.scn_plan_create(arr(seqs), n, arr(hists), arr(scores), arr(flags),
+                                ctypes.byref(t) if t is not None else None, ctypes.byref(h)), "scn_plan_create")
+    return h.value
+
+
+def scn_plan_destroy(p: int) -> None:
+    _check(_lib.scn_plan_destroy(p), "scn_plan_destroy")
+
+
+def scn_plan_set_tune(p: int, chunk_rows: int = 0, grid: int = 0, item_kpx: int = 0) -> None:
+    t = scn_tune(chunk_rows, grid, item_kpx)
+    _check(_lib.scn_plan_set_tune(p, ctypes.byref(t)), "scn_plan_set_tune")
+
+
+def scn_plan_get_tune(p: int) -> dict:
+    t = scn_tune()
+    _check(_lib.scn_plan_get_tune(p, ctypes.byref(t)), "scn_plan_get_tune")
+    return dict(chunk_rows=t.chunk_rows, grid=t.grid, item_kpx=t.item_kpx)
+
+
+def scn_plan_info(p: int) -> dict:
+    a, b, c, g = c_i64(), c_i64(), c_i64(), c_i32()
+    _check(_lib.scn_plan_info(p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(g)), "scn_plan_info")
+    return dict(items=a.value, frames=b.value, nv12_bytes=c.value, grid=g.value)
+
+
+def scn_plan_run(p: int, stream=None) -> None:
+    _check(_lib.scn_plan_run(p, _stream(stream)), "scn_plan_run")
+
+
+def scn_plan_capture_graph(p: int, stream=None) -> None:
+    _check(_lib.scn_plan_capture_graph(p, _stream(stream)), "scn_plan_capture_graph")
+
+
+def scn_plan_replay(p: int, stream=None) -> None:
+    _check(_lib.scn_plan_replay(p, _stream(stream)), "scn_plan_replay")
+
+
+def scn_plan_sync_status(p: int, stream=None) -> int:
+    return int(_lib.scn_plan_sync_status(p, _stream(stream)))
+
+
+def scn_plan_autotune(p: int, reps: int = 3, stream=None) -> tuple[dict, float]:
+    t = scn_tune()
+    ms = ctypes.c_float()
+    _check(_lib.scn_plan_autotune(p, reps, _stream(stream), ctypes.byref(t), ctypes.byref(ms)), "scn_plan_autotune")
+    return dict(chunk_rows=t.chunk_rows, grid=t.grid, item_kpx=t.item_kpx), float(ms.value)
 
 
 def scn_resize_norm(s: int, oh: int, ow: int, mean, std, dtype: int, out, stream=None) -> None:

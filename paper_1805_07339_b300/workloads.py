@@ -36,3 +36,36 @@ def random_indices(seed: int, num_frames: int, m: int, distinct: bool = True) ->
 def hd_gather() -> np.ndarray:
     """The 1080p gather list: 1000 distinct sorted frames of 7200."""
     return random_indices(HD_GATHER_SEED, HD["num_frames"], HD_GATHER)
+
+
+# Batched uneven workload: videos of four resolution classes, uniform lengths,
+# and one of four sampling patterns each.
+RESOLUTIONS = [(640, 360), (1280, 720), (1920, 1080), (3840, 2160)]
+SAMPLINGS = ["stride1", "stride24", "range", "gather5"]
+BATCH_SEED = 3
+
+
+def batched_spec(nvideos: int = 64, min_len: int = 200, max_len: int = 3000, seed: int = BATCH_SEED,
+                 resolutions=None) -> list[dict]:
+    """Per video: id, width, height, frames, shots (one per 120 frames) and the
+    sampled frame numbers (sorted for stride/range, in draw order for gather)."""
+    rng = np.random.default_rng(seed)
+    res = resolutions or RESOLUTIONS
+    out = []
+    for v in range(nvideos):
+        W, H = res[int(rng.integers(0, len(res)))]
+        T = int(rng.integers(min_len, max_len + 1))
+        kind = SAMPLINGS[int(rng.integers(0, len(SAMPLINGS)))]
+        if kind == "stride1":
+            idx = np.arange(T)
+        elif kind == "stride24":
+            idx = np.arange(0, T, 24)
+        elif kind == "range":
+            a, b = sorted(int(x) for x in rng.choice(T + 1, size=2, replace=False))
+            idx = np.arange(a, b)
+        else:
+            m = max(1, T // 20)
+            idx = np.sort(rng.choice(T, size=m, replace=False))
+        out.append(dict(video_id=1000 + v, width=W, height=H, num_frames=T, num_shots=max(1, T // 120),
+                        sampling=kind, frames=idx.astype(np.int64)))
+    return out
