@@ -126,3 +126,22 @@ def test_gen_params_rejected():
         p.update(kw)
         with pytest.raises(scn.ScnError):
             scn.scn_gen_shots(1, 0, p["width"], p["height"], p["num_frames"], p["num_shots"])
+
+
+def test_autotune_cache_key_and_file(tmp_path, monkeypatch):
+    from paper_1805_07339_b300 import autotune
+    import numpy as np
+    vids = [dict(width=640, height=360, sampling="stride1", frames=np.arange(100)),
+            dict(width=1920, height=1080, sampling="gather5", frames=np.arange(7))]
+    k1 = autotune.plan_key("B300", vids)
+    k2 = autotune.plan_key("B300", list(reversed(vids)))
+    assert k1 == k2 and "640x360:1" in k1 and "gather5:1" in k1
+    calls = []
+    monkeypatch.setattr(autotune.scn, "scn_plan_autotune",
+                        lambda p, reps=3, stream=None: (calls.append(p) or ({"chunk_rows": 0, "grid": 0, "item_kpx": 2100}, 1.5)))
+    applied = []
+    monkeypatch.setattr(autotune.scn, "scn_plan_set_tune", lambda p, **t: applied.append(t))
+    path = str(tmp_path / "c.json")
+    r1 = autotune.tune_plan(7, k1, path)
+    r2 = autotune.tune_plan(8, k1, path)
+    assert not r1["cached"] and r2["cached"] and calls == [7] and applied == [r1["tune"]]
