@@ -247,6 +247,54 @@ scn_status scn_plan_sync_status(scn_plan* p, void* stream);
  * identical results. */
 scn_status scn_plan_autotune(scn_plan* p, int32_t reps, void* stream, scn_tune* best, float* best_ms);
 
+/* ------------------------------------------------------------------------ */
+/* Learned boundary proposal: a tiny BF16 CNN (FP32 accumulation, tcgen05    */
+/* tensor cores for the convolutions) over pairs of 36x64 luma thumbnails.    */
+/* The paper runs DNNs on sampled frames (Sec. 3.1, Sec. 5.1.2) but fixes no   */
+/* proposal network; this one is the build's:                               */
+/*   x = [(Yprev-128)/64, (Ycur-128)/64] (2x36x64) -> conv3x3/s2/p1 2->16 ->  */
+/*   16->32 -> 32->32 (each + bias + ReLU) -> mean over 5x8 -> FC 32->64 +    */
+/*   ReLU -> FC 64->1 = logit.  16369 parameters, flat fp32 in that order    */
+/*   (conv weights [co][ci][3][3]).                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct scn_cnn scn_cnn;
+
+/* Number of parameters (16369). */
+int64_t scn_cnn_num_params(void);
+/* Allocate a network with room for max_batch pairs per launch (activations,
+ * gradients, Adam state).  Parameters start at zero: set them first. */
+scn_status scn_cnn_create(int64_t max_batch, scn_cnn** out);
+scn_status scn_cnn_destroy(scn_cnn* c);
+/* Copy n = scn_cnn_num_params() fp32 parameters from the host; resets the
+ * optimiser state.  Synchronous. */
+scn_status scn_cnn_set_params(scn_cnn* c, const float* h_params, int64_t n);
+scn_status scn_cnn_get_params(const scn_cnn* c, float* h_params, int64_t n);
+/* Logits of n thumbnail pairs.  d_thumbs: uint8 [*][36][64] (device).  Pair b
+ * is (d_prev[b], d_cur[b]) (device int32 thumbnail indices) or, when both are
+ * NULL, (b, b+1).  Runs in chunks of max_batch pairs; the activations of the
+ * last chunk stay readable through scn_cnn_activation. */
+scn_status scn_cnn_forward(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
+                           int64_t n, float* d_logits, void* stream);
+/* Gradients of the batch-mean BCE-with-logits loss (positive weight
+ * pos_weight > 0) over `batch` pairs (1..max_batch) with labels d_labels
+ * (device float 0/1): d_grads (device, num_params floats, parameter order) and
+ * d_loss (device float); either may be NULL.  Gradients are taken w.r.t. the
+ * BF16 weights the forward uses. */
+scn_status scn_cnn_gradients(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
+                             const float* d_labels, int64_t batch, float pos_weight, float* d_loss, float* d_grads,
+                             void* stream);
+/* One training step: gradients as above, then Adam (beta 0.9 / 0.999, eps
+ * 1e-8, bias-corrected) on the fp32 master weights and a refresh of the BF16
+ * copies.  Asynchronous on stream. */
+scn_status scn_cnn_train_step(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
+                              const float* d_labels, int64_t batch, float pos_weight, float lr, float* d_loss,
+                              void* stream);
+/* Device pointer to the BF16 NHWC output of conv layer 1, 2 or 3 of the last
+ * forward chunk ([pairs][positions][channels]). */
+scn_status scn_cnn_activation(const scn_cnn* c, int32_t layer, const void** d_ptr);
+/* Synchronise stream, read and clear the network's device status word. */
+scn_status scn_cnn_sync_status(scn_cnn* c, void* stream);
+
 typedef enum { SCN_F32 = 0, SCN_BF16 = 1 } scn_dtype;
 /* Bilinear resize (half-pixel centres, no antialias, stretch) of the RGB
  * frame to oh x ow, then (v/255 - mean[c]) / std[c]; output [n][3][oh][ow]

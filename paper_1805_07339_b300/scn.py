@@ -89,6 +89,16 @@ SIGNATURES = [
     ("scn_plan_replay", c_i32, [c_vp, c_vp]),
     ("scn_plan_sync_status", c_i32, [c_vp, c_vp]),
     ("scn_plan_autotune", c_i32, [c_vp, c_i32, c_vp, _P(scn_tune), _P(ctypes.c_float)]),
+    ("scn_cnn_num_params", c_i64, []),
+    ("scn_cnn_create", c_i32, [c_i64, _P(c_vp)]),
+    ("scn_cnn_destroy", c_i32, [c_vp]),
+    ("scn_cnn_set_params", c_i32, [c_vp, _P(ctypes.c_float), c_i64]),
+    ("scn_cnn_get_params", c_i32, [c_vp, _P(ctypes.c_float), c_i64]),
+    ("scn_cnn_forward", c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, c_vp]),
+    ("scn_cnn_gradients", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.c_float, c_vp, c_vp, c_vp]),
+    ("scn_cnn_train_step", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.c_float, ctypes.c_float, c_vp, c_vp]),
+    ("scn_cnn_activation", c_i32, [c_vp, c_i32, _P(c_vp)]),
+    ("scn_cnn_sync_status", c_i32, [c_vp, c_vp]),
     ("scn_resize_norm", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_i32, c_vp, c_vp]),
     ("scn_thumbs", c_i32, [c_vp, c_vp, c_vp]),
 ]
@@ -341,6 +351,60 @@ def scn_plan_autotune(p: int, reps: int = 3, stream=None) -> tuple[dict, float]:
     ms = ctypes.c_float()
     _check(_lib.scn_plan_autotune(p, reps, _stream(stream), ctypes.byref(t), ctypes.byref(ms)), "scn_plan_autotune")
     return dict(chunk_rows=t.chunk_rows, grid=t.grid, item_kpx=t.item_kpx), float(ms.value)
+
+
+def scn_cnn_num_params() -> int:
+    return int(_lib.scn_cnn_num_params())
+
+
+def scn_cnn_create(max_batch: int) -> int:
+    h = c_vp()
+    _check(_lib.scn_cnn_create(max_batch, ctypes.byref(h)), "scn_cnn_create")
+    return h.value
+
+
+def scn_cnn_destroy(c: int) -> None:
+    _check(_lib.scn_cnn_destroy(c), "scn_cnn_destroy")
+
+
+def scn_cnn_set_params(c: int, params) -> None:
+    import numpy as np
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(_lib.scn_cnn_set_params(c, a.ctypes.data_as(_P(ctypes.c_float)), a.size), "scn_cnn_set_params")
+
+
+def scn_cnn_get_params(c: int):
+    import numpy as np
+    a = np.empty(scn_cnn_num_params(), dtype=np.float32)
+    _check(_lib.scn_cnn_get_params(c, a.ctypes.data_as(_P(ctypes.c_float)), a.size), "scn_cnn_get_params")
+    return a
+
+
+def scn_cnn_forward(c: int, thumbs, n: int, logits, prev=None, cur=None, stream=None) -> None:
+    _check(_lib.scn_cnn_forward(c, _ptr(thumbs), _ptr(prev), _ptr(cur), n, _ptr(logits), _stream(stream)),
+           "scn_cnn_forward")
+
+
+def scn_cnn_gradients(c: int, thumbs, labels, batch: int, pos_weight: float, loss=None, grads=None, prev=None,
+                      cur=None, stream=None) -> None:
+    _check(_lib.scn_cnn_gradients(c, _ptr(thumbs), _ptr(prev), _ptr(cur), _ptr(labels), batch, pos_weight,
+                                  _ptr(loss), _ptr(grads), _stream(stream)), "scn_cnn_gradients")
+
+
+def scn_cnn_train_step(c: int, thumbs, labels, batch: int, pos_weight: float, lr: float, loss=None, prev=None,
+                       cur=None, stream=None) -> None:
+    _check(_lib.scn_cnn_train_step(c, _ptr(thumbs), _ptr(prev), _ptr(cur), _ptr(labels), batch, pos_weight, lr,
+                                   _ptr(loss), _stream(stream)), "scn_cnn_train_step")
+
+
+def scn_cnn_activation(c: int, layer: int) -> int:
+    p = c_vp()
+    _check(_lib.scn_cnn_activation(c, layer, ctypes.byref(p)), "scn_cnn_activation")
+    return p.value
+
+
+def scn_cnn_sync_status(c: int, stream=None) -> int:
+    return int(_lib.scn_cnn_sync_status(c, _stream(stream)))
 
 
 def scn_resize_norm(s: int, oh: int, ow: int, mean, std, dtype: int, out, stream=None) -> None:
