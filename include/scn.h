@@ -295,6 +295,28 @@ scn_status scn_cnn_activation(const scn_cnn* c, int32_t layer, const void** d_pt
 /* Synchronise stream, read and clear the network's device status word. */
 scn_status scn_cnn_sync_status(scn_cnn* c, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Gated exact path: a gate proposes boundary candidates, only the frames of */
+/* proposed pairs go through the exact kernel, which remains the judge.      */
+/* ------------------------------------------------------------------------ */
+/* d_gate[k] (device float, k >= 1) scores pair (k-1, k) of the sequence; pair
+ * k is proposed when d_gate[k] > tau (d_gate[0] is ignored).  Writes
+ * d_proposed[k] (0/1); d_score / d_flag get the exact score and flag of every
+ * proposed pair and 0 elsewhere.  Synchronises the stream once (the number of
+ * proposals is read back; *h_nproposed receives it when not NULL).  The
+ * sequence's gated workspace is allocated on the first call. */
+scn_status scn_gated_hist_scores(scn_seq* s, const float* d_gate, float tau, uint8_t* d_proposed, uint32_t* d_score,
+                                 uint8_t* d_flag, int64_t* h_nproposed, void* stream);
+/* The learned proposal path: thumbnails of the sequence into d_thumbs
+ * (caller-owned [n][36][64]), the network's logit of every consecutive pair
+ * into d_logits[1..n-1] (pair k-1, k), then scn_gated_hist_scores with tau. */
+scn_status scn_proposal_hist_scores(scn_seq* s, scn_cnn* net, float tau, uint8_t* d_thumbs, float* d_logits,
+                                    uint8_t* d_proposed, uint32_t* d_score, uint8_t* d_flag, int64_t* h_nproposed,
+                                    void* stream);
+/* The non-learned gate: d_diff[k] = mean |thumb[k] - thumb[k-1]| over the
+ * 2304 samples (d_diff[0] = 0); d_thumbs 4-byte aligned. */
+scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, void* stream);
+
 typedef enum { SCN_F32 = 0, SCN_BF16 = 1 } scn_dtype;
 /* Bilinear resize (half-pixel centres, no antialias, stretch) of the RGB
  * frame to oh x ow, then (v/255 - mean[c]) / std[c]; output [n][3][oh][ow]

@@ -596,7 +596,7 @@ HistShape resolve_hist_shape(const scn_seq* s) {
 }
 
 // A single-sequence launch description (outputs and scratch filled in by the caller).
-static Launch single_launch(const scn_table* t, int64_t n, const int32_t* slot, const HistShape& sh) {
+Launch single_launch(const scn_table* t, int64_t n, const int32_t* slot, const HistShape& sh) {
     Launch L{};
     Job& j = L.job0;
     j.nv12 = t->d_nv12;

@@ -73,6 +73,7 @@ struct scn_seq {
     uint32_t* d_partial = nullptr;   // [n][48] cross-CTA histogram accumulators (kept zero)
     int* d_status = nullptr;         // device status word
     uint32_t* d_queue = nullptr;     // work-queue counters (2 words, left zero)
+    void* gate_ws = nullptr;         // gated-path workspace, made on first use
     scn_tune tune{0, 0, 0};          // 0 fields: chosen per call
 };
 
@@ -141,5 +142,10 @@ struct HistShape {
     size_t smem;
 };
 HistShape resolve_hist_shape(const scn_seq* s);
+// A single-sequence launch over n elements with the given storage slots
+// (outputs, scratch, queue and status are filled in by the caller).
+Launch single_launch(const scn_table* t, int64_t n, const int32_t* slot, const HistShape& sh);
 int device_sm_count();
+// Release a sequence's gated-path workspace (scn_proposal.cu).
+void free_gate_workspace(scn_seq* s);
 }  // namespace scn

@@ -1,0 +1,214 @@
+// Gated exact path: a cheap gate (the proposal network's logits, or any score)
+// proposes candidate boundaries between consecutive sampled frames, and only
+// the frames of proposed pairs go through the exact convert + histogram +
+// score kernel, which stays the judge: an unproposed pair gets score 0 and
+// flag 0, a proposed pair gets its exact score and flag.
+//
+// Steps: proposals -> compacted list of proposed elements k (pair k-1, k) ->
+// storage slots of both frames of every proposed pair -> one launch of the
+// fused kernel over that 2m-element sequence -> scatter of each pair's score.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "scn_internal.h"
+
+namespace scn {
+namespace {
+
+struct GateWs {
+    void* block = nullptr;
+    int64_t cap = 0;          // elements of the sequence it was made for
+    int32_t* list = nullptr;  // [cap] proposed elements
+    int32_t* slots2 = nullptr;  // [2 cap]
+    uint32_t* hist2 = nullptr;  // [2 cap][48]
+    uint32_t* score2 = nullptr;
+    uint8_t* flag2 = nullptr;
+    uint32_t* partial = nullptr;  // [2 cap][48] (left zero)
+    uint32_t* done = nullptr;
+    uint32_t* pair = nullptr;
+    uint32_t* queue = nullptr;
+    int* status = nullptr;
+    int* count = nullptr;
+};
+
+__global__ void propose_kernel(const float* gate, int64_t n, float tau, uint8_t* proposed, int32_t* list, int* count,
+                               uint32_t* score, uint8_t* flag) {
+    for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+         k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const bool p = k >= 1 && gate[k] > tau;
+        proposed[k] = p ? 1 : 0;
+        score[k] = 0;
+        flag[k] = 0;
+        if (p) list[atomicAdd(count, 1)] = static_cast<int32_t>(k);
+    }
+}
+
+__global__ void pair_slots(const int32_t* list, int64_t m, const int32_t* slot, int32_t* slots2) {
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= m) return;
+    const int32_t k = list[i];
+    slots2[2 * i] = slot[k - 1];
+    slots2[2 * i + 1] = slot[k];
+}
+
+__global__ void scatter_scores(const int32_t* list, int64_t m, const uint32_t* score2, const uint8_t* flag2,
+                               uint32_t* score, uint8_t* flag) {
+    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (i >= m) return;
+    const int32_t k = list[i];
+    score[k] = score2[2 * i + 1];
+    flag[k] = flag2[2 * i + 1];
+}
+
+// mean |thumb[k] - thumb[k-1]| over the 2304 samples, 0 for k = 0
+__global__ void __launch_bounds__(256) thumb_diff_kernel(const uint8_t* thumbs, int64_t n, float* diff) {
+    const int64_t k = blockIdx.x;
+    if (k >= n) return;
+    __shared__ unsigned part[8];
+    unsigned s = 0;
+    if (k > 0) {
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(thumbs + k * 2304);
+        const uint32_t* b = reinterpret_cast<const uint32_t*>(thumbs + (k - 1) * 2304);
+        for (int i = threadIdx.x; i < 576; i += 256) s = __vsadu4(a[i], b[i]) + s;
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < 8; ++w) t += part[w];
+        diff[k] = static_cast<float>(t) / 2304.f;
+    }
+}
+
+scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
+    ws = static_cast<GateWs*>(s->gate_ws);
+    if (ws && ws->cap >= s->n) return SCN_OK;
+    if (ws) {
+        if (ws->block) cudaFree(ws->block);
+        delete ws;
+        s->gate_ws = nullptr;
+    }
+    ws = new (std::nothrow) GateWs;
+    if (!ws) return SCN_ENOMEM;
+    const int64_t c = std::max<int64_t>(s->n, 1);
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t parts[] = {up(c * 4), up(2 * c * 4), up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c),
+                            up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c * 4), 256, 256, 256};
+    size_t total = 0;
+    for (size_t p : parts) total += p;
+    cudaError_t e = cudaMalloc(&ws->block, total);
+    if (e == cudaSuccess) e = cudaMemset(ws->block, 0, total);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        if (ws->block) cudaFree(ws->block);
+        delete ws;
+        ws = nullptr;
+        return SCN_ECUDA;
+    }
+    char* p = static_cast<char*>(ws->block);
+    void** dst[] = {reinterpret_cast<void**>(&ws->list),    reinterpret_cast<void**>(&ws->slots2),
+                    reinterpret_cast<void**>(&ws->hist2),   reinterpret_cast<void**>(&ws->score2),
+                    reinterpret_cast<void**>(&ws->flag2),   reinterpret_cast<void**>(&ws->partial),
+                    reinterpret_cast<void**>(&ws->done),    reinterpret_cast<void**>(&ws->pair),
+                    reinterpret_cast<void**>(&ws->queue),   reinterpret_cast<void**>(&ws->status),
+                    reinterpret_cast<void**>(&ws->count)};
+    for (int i = 0; i < 11; ++i) {
+        *dst[i] = p;
+        p += parts[i];
+    }
+    ws->cap = c;
+    s->gate_ws = ws;
+    return SCN_OK;
+}
+
+}  // namespace
+
+void free_gate_workspace(scn_seq* s) {
+    GateWs* ws = static_cast<GateWs*>(s->gate_ws);
+    if (!ws) return;
+    if (ws->block) cudaFree(ws->block);
+    delete ws;
+    s->gate_ws = nullptr;
+}
+
+}  // namespace scn
+
+using namespace scn;
+
+extern "C" {
+
+scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, void* stream) {
+    if (n < 0) return SCN_EINVAL;
+    if (n == 0) return SCN_OK;
+    if (!d_thumbs || !d_diff || (reinterpret_cast<uintptr_t>(d_thumbs) & 3u)) return SCN_EINVAL;
+    if (n > 0x7fffffff) return SCN_ERANGE;
+    thumb_diff_kernel<<<static_cast<unsigned>(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_thumbs, n, d_diff);
+    SCN_CUDA_TRY(cudaGetLastError());
+    return SCN_OK;
+}
+
+scn_status scn_gated_hist_scores(scn_seq* s, const float* d_gate, float tau, uint8_t* d_proposed, uint32_t* d_score,
+                                 uint8_t* d_flag, int64_t* h_nproposed, void* stream) {
+    if (!s || !d_gate || !d_proposed || !d_score || !d_flag) return SCN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_score) & 3u) return SCN_EINVAL;
+    if (h_nproposed) *h_nproposed = 0;
+    if (s->n == 0) return SCN_OK;
+    GateWs* ws = nullptr;
+    scn_status st = ensure_ws(s, ws);
+    if (st != SCN_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    SCN_CUDA_TRY(cudaMemsetAsync(ws->count, 0, sizeof(int), cs));
+    const int64_t blocks = std::min<int64_t>((s->n + 255) / 256, 148 * 8);
+    propose_kernel<<<static_cast<unsigned>(blocks), 256, 0, cs>>>(d_gate, s->n, tau, d_proposed, ws->list, ws->count,
+                                                                  d_score, d_flag);
+    SCN_CUDA_TRY(cudaGetLastError());
+    int m = 0;
+    SCN_CUDA_TRY(cudaMemcpyAsync(&m, ws->count, sizeof(int), cudaMemcpyDeviceToHost, cs));
+    SCN_CUDA_TRY(cudaStreamSynchronize(cs));
+    if (h_nproposed) *h_nproposed = m;
+    if (m == 0) return SCN_OK;
+    pair_slots<<<(m + 255) / 256, 256, 0, cs>>>(ws->list, m, s->d_slot, ws->slots2);
+    SCN_CUDA_TRY(cudaGetLastError());
+    // the exact kernel over the 2m frames of the proposed pairs
+    scn_seq q;
+    q.table = s->table;
+    q.n = 2 * static_cast<int64_t>(m);
+    q.tune = s->tune;
+    const HistShape sh = resolve_hist_shape(&q);
+    Launch L = single_launch(s->table, q.n, ws->slots2, sh);
+    L.job0.hist = ws->hist2;
+    L.job0.score = ws->score2;
+    L.job0.flag = ws->flag2;
+    L.job0.partial = ws->partial;
+    L.job0.done = ws->done;
+    L.job0.pair = ws->pair;
+    L.queue = ws->queue;
+    L.status = s->d_status;
+    st = launch_hist(L, cs);
+    if (st != SCN_OK) return st;
+    scatter_scores<<<(m + 255) / 256, 256, 0, cs>>>(ws->list, m, ws->score2, ws->flag2, d_score, d_flag);
+    SCN_CUDA_TRY(cudaGetLastError());
+    return SCN_OK;
+}
+
+scn_status scn_proposal_hist_scores(scn_seq* s, scn_cnn* net, float tau, uint8_t* d_thumbs, float* d_logits,
+                                    uint8_t* d_proposed, uint32_t* d_score, uint8_t* d_flag, int64_t* h_nproposed,
+                                    void* stream) {
+    if (!s || !net || !d_thumbs || !d_logits) return SCN_EINVAL;
+    if (h_nproposed) *h_nproposed = 0;
+    if (s->n == 0) return SCN_OK;
+    scn_status st = scn_thumbs(s, d_thumbs, stream);
+    if (st != SCN_OK) return st;
+    if (s->n > 1) {
+        // pair (k-1, k) -> logit k
+        st = scn_cnn_forward(net, d_thumbs, nullptr, nullptr, s->n - 1, d_logits + 1, stream);
+        if (st != SCN_OK) return st;
+    }
+    return scn_gated_hist_scores(s, d_logits, tau, d_proposed, d_score, d_flag, h_nproposed, stream);
+}
+
+}  // extern "C"

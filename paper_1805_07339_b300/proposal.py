@@ -1,0 +1,233 @@
+"""The learned boundary proposal: data, training, threshold choice and evaluation.
+
+Every number crunched here runs in libscn's kernels (generator, thumbnails,
+exact histogram/score path, the network's forward/backward/Adam, the gated exact
+path); this module only sequences the calls and counts.
+
+Data (the build's reading of the proposal workload): 1080p synthetic videos of
+7200 frames and 60 shots; a training pair is two consecutive frames (k-1, k)
+labelled by the exact detector's flag of frame k.  Training, threshold and
+evaluation videos use disjoint video ids.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import scn
+from .workloads import MASTER_SEED
+
+HD = (1920, 1080, 7200, 60)
+TRAIN_IDS = list(range(2000, 2028))     # 28 videos: 201,572 consecutive pairs
+VAL_IDS = list(range(3000, 3008))       # threshold choice (~470 boundaries)
+EVAL_IDS = list(range(4000, 4014))      # 14 x 7200 = 100,800 fresh frames
+
+
+def he_uniform(seed: int) -> np.ndarray:
+    """Initial parameters: He-uniform weights (variance 2/fan_in), zero biases."""
+    rng = np.random.default_rng(seed)
+    shapes = [(16, 2, 3, 3), (16,), (32, 16, 3, 3), (32,), (32, 32, 3, 3), (32,), (64, 32), (64,), (1, 64), (1,)]
+    out = []
+    for sh in shapes:
+        if len(sh) > 1:
+            fan_in = int(np.prod(sh[1:]))
+            out.append(rng.uniform(-1, 1, sh) * np.sqrt(6.0 / fan_in))
+        else:
+            out.append(np.zeros(sh))
+    flat = np.concatenate([o.ravel() for o in out]).astype(np.float32)
+    assert flat.size == scn.scn_cnn_num_params()
+    return flat
+
+
+class VideoSource:
+    """Generates one synthetic 1080p video at a time into a reusable device buffer."""
+
+    def __init__(self, torch, W=HD[0], H=HD[1], T=HD[2], S=HD[3]):
+        self.torch, self.W, self.H, self.T, self.S = torch, W, H, T, S
+        self.fb = W * H * 3 // 2
+        self.buf = torch.empty(T * self.fb, dtype=torch.uint8, device="cuda")
+        self.table = scn.scn_table_create(self.buf, W, H, T)
+        self.seq = scn.scn_sample(self.table, scn.SCN_STRIDE, start=0, stop=T, step=1)
+        t = torch
+        self.hist = t.empty((T, 48), dtype=t.int32, device="cuda")
+        self.score = t.empty(T, dtype=t.int32, device="cuda")
+        self.flag = t.empty(T, dtype=t.uint8, device="cuda")
+
+    def load(self, video_id: int) -> None:
+        v = scn.scn_video_create(MASTER_SEED, video_id, self.W, self.H, self.T, self.S)
+        scn.scn_generate(v, self.buf, 0, self.T, self.fb)
+        scn.scn_video_destroy(v)
+
+    def exact(self):
+        scn.scn_hist_scores(self.seq, self.hist, self.score, self.flag)
+        return self.flag
+
+    def thumbs(self, out) -> None:
+        scn.scn_thumbs(self.seq, out)
+
+    def close(self) -> None:
+        scn.scn_seq_destroy(self.seq)
+        scn.scn_table_destroy(self.table)
+
+
+def build_pairs(torch, src: VideoSource, ids: list[int]):
+    """Thumbnails of every frame, and (prev, cur, label) of every consecutive pair."""
+    T = src.T
+    thumbs = torch.empty((len(ids) * T, 36, 64), dtype=torch.uint8, device="cuda")
+    labels = []
+    for i, vid in enumerate(ids):
+        src.load(vid)
+        src.thumbs(thumbs[i * T:(i + 1) * T])
+        labels.append(src.exact()[1:].float().clone())
+    base = (torch.arange(len(ids), device="cuda") * T).repeat_interleave(T - 1)
+    within = torch.arange(1, T, device="cuda").repeat(len(ids))
+    cur = (base + within).int()
+    prev = cur - 1
+    return thumbs, prev.contiguous(), cur.contiguous(), torch.cat(labels)
+
+
+def train(torch, net: int, thumbs, prev, cur, labels, steps: int = 2500, batch: int = 256, lr: float = 1e-3,
+          seed: int = 0, log_every: int = 250, cosine: bool = True):
+    """Adam on uniformly drawn batches of pairs; positive weight = negatives / positives;
+    learning rate decayed to zero along a half cosine when `cosine` is set."""
+    npos = float(labels.sum().item())
+    pos_weight = (labels.numel() - npos) / max(npos, 1.0)
+    rng = np.random.default_rng(seed)
+    draws = torch.from_numpy(rng.integers(0, labels.numel(), (steps, batch)).astype(np.int64)).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    curve = []
+    bp = torch.empty(batch, dtype=torch.int32, device="cuda")
+    bc = torch.empty(batch, dtype=torch.int32, device="cuda")
+    by = torch.empty(batch, dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    for s in range(steps):
+        ix = draws[s]
+        torch.index_select(prev, 0, ix, out=bp)
+        torch.index_select(cur, 0, ix, out=bc)
+        torch.index_select(labels, 0, ix, out=by)
+        lr_s = lr * 0.5 * (1.0 + np.cos(np.pi * s / steps)) if cosine else lr
+        scn.scn_cnn_train_step(net, thumbs, by, batch, pos_weight, max(lr_s, 1e-6), loss=loss, prev=bp, cur=bc)
+        if log_every and (s % log_every == 0 or s == steps - 1):
+            curve.append((s, float(loss.item())))
+    torch.cuda.synchronize()
+    return {"pos_weight": pos_weight, "steps": steps, "batch": batch, "lr": lr, "curve": curve,
+            "seconds": time.perf_counter() - t0}
+
+
+def logits(torch, net: int, thumbs, prev, cur):
+    z = torch.empty(prev.numel(), dtype=torch.float32, device="cuda")
+    scn.scn_cnn_forward(net, thumbs, prev.numel(), z, prev=prev, cur=cur)
+    return z
+
+
+def tau_for_recall(score: np.ndarray, labels: np.ndarray, recall: float = 0.99) -> float:
+    """Largest threshold t with recall(score > t) >= recall on these labels."""
+    pos = np.sort(score[labels > 0.5])
+    if len(pos) == 0:
+        return float("inf")
+    keep = int(np.ceil(recall * len(pos)))  # positives that must score above t
+    t = pos[len(pos) - keep]
+    return float(np.nextafter(np.float32(t), np.float32(-np.inf)))
+
+
+def choose_tau(score: np.ndarray, labels: np.ndarray, recall: float = 0.995, fp_rate: float = 1e-3) -> float:
+    """Threshold picked on held-out pairs: low enough for `recall` of the
+    positives, and further down to where the negatives' upper tail begins
+    (their 1 - fp_rate quantile), since proposals below that cost almost nothing."""
+    t_rec = tau_for_recall(score, labels, recall)
+    neg = score[labels < 0.5]
+    t_neg = float(np.quantile(neg, 1.0 - fp_rate)) if len(neg) else t_rec
+    return min(t_rec, t_neg)
+
+
+def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids: list[int], reps: int = 3):
+    """Per video: the plain exact path over all frames vs the learned gate and the
+    thumbnail-difference gate (thumbnails + gate + exact path on proposed pairs)."""
+    T = src.T
+    thumbs = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
+    zl = torch.full((T,), -1e30, dtype=torch.float32, device="cuda")
+    diff = torch.empty(T, dtype=torch.float32, device="cuda")
+    prop = torch.empty(T, dtype=torch.uint8, device="cuda")
+    sc = torch.empty(T, dtype=torch.int32, device="cuda")
+    fl = torch.empty(T, dtype=torch.uint8, device="cuda")
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))  # noqa: E731
+    tot = dict(frames=0, boundaries=0, t_plain=0.0, t_learned=0.0, t_diff=0.0)
+    for gate in ("learned", "diff"):
+        tot[gate] = dict(tp=0, proposed=0, exact_equal=True)
+    for vid in ids:
+        src.load(vid)
+        torch.cuda.synchronize()
+        exact = src.exact().clone()
+        ex = exact.cpu().numpy()[1:].astype(bool)
+        tot["frames"] += T
+        tot["boundaries"] += int(ex.sum())
+        # plain exact path
+        a, b = ev()
+        a.record()
+        for _ in range(reps):
+            src.exact()
+        b.record()
+        torch.cuda.synchronize()
+        tot["t_plain"] += a.elapsed_time(b) / reps
+        for gate in ("learned", "diff"):
+            a, b = ev()
+            a.record()
+            for _ in range(reps):
+                if gate == "learned":
+                    scn.scn_proposal_hist_scores(src.seq, net, tau, thumbs, zl, prop, sc, fl)
+                else:
+                    src.thumbs(thumbs)
+                    scn.scn_thumb_diff(thumbs, T, diff)
+                    scn.scn_gated_hist_scores(src.seq, diff, tau_diff, prop, sc, fl)
+            b.record()
+            torch.cuda.synchronize()
+            tot["t_" + gate] += a.elapsed_time(b) / reps
+            p = prop.cpu().numpy()[1:].astype(bool)
+            r = tot[gate]
+            r["tp"] += int((p & ex).sum())
+            r["proposed"] += int(p.sum())
+            # the gated path reproduces the exact flag on every proposed pair
+            fl_np = fl.cpu().numpy()[1:]
+            r["exact_equal"] &= bool(np.array_equal(fl_np[p], ex[p].astype(np.uint8))) and not fl_np[~p].any()
+    out = {"frames": tot["frames"], "boundaries": tot["boundaries"], "t_plain_ms": tot["t_plain"]}
+    for gate in ("learned", "diff"):
+        r = tot[gate]
+        out[gate] = {"recall": r["tp"] / max(tot["boundaries"], 1), "precision": r["tp"] / max(r["proposed"], 1),
+                     "proposed": r["proposed"], "t_ms": tot["t_" + gate],
+                     "speedup": tot["t_plain"] / max(tot["t_" + gate], 1e-9), "exact_on_proposed": r["exact_equal"]}
+    return out
+
+
+def run(torch, steps: int = 6000, batch: int = 256, lr: float = 1e-3, seed: int = 0, train_ids=None, val_ids=None,
+        eval_ids=None) -> dict:
+    """Build data, train on the GPU, pick thresholds on held-out videos (choose_tau), evaluate."""
+    src = VideoSource(torch)
+    try:
+        th, pv, cu, lab = build_pairs(torch, src, train_ids or TRAIN_IDS)
+        net = scn.scn_cnn_create(batch)
+        fwd = scn.scn_cnn_create(4096)
+        try:
+            scn.scn_cnn_set_params(net, he_uniform(seed))
+            tr = train(torch, net, th, pv, cu, lab, steps=steps, batch=batch, lr=lr, seed=seed)
+            scn.scn_cnn_set_params(fwd, scn.scn_cnn_get_params(net))
+            del th, pv, cu
+            vth, vp, vc, vl = build_pairs(torch, src, val_ids or VAL_IDS)
+            z = logits(torch, fwd, vth, vp, vc).cpu().numpy()
+            vlab = vl.cpu().numpy()
+            tau = choose_tau(z, vlab)
+            d = torch.empty(vth.shape[0], dtype=torch.float32, device="cuda")
+            scn.scn_thumb_diff(vth, vth.shape[0], d)
+            dd = d.cpu().numpy()
+            # diff of pair (k-1, k) sits at thumbnail k; pairs never span two videos
+            tau_d = choose_tau(dd[vc.cpu().numpy()], vlab)
+            res = evaluate(torch, fwd, tau, tau_d, src, eval_ids or EVAL_IDS)
+            res.update({"train": tr, "tau": tau, "tau_diff": tau_d, "train_pairs": int(lab.numel()),
+                        "train_positives": int(lab.sum().item()), "val_pairs": int(vl.numel()),
+                        "params": scn.scn_cnn_get_params(fwd)})
+            return res
+        finally:
+            scn.scn_cnn_destroy(net)
+            scn.scn_cnn_destroy(fwd)
+    finally:
+        src.close()

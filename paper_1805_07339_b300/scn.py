@@ -99,6 +99,9 @@ SIGNATURES = [
     ("scn_cnn_train_step", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.c_float, ctypes.c_float, c_vp, c_vp]),
     ("scn_cnn_activation", c_i32, [c_vp, c_i32, _P(c_vp)]),
     ("scn_cnn_sync_status", c_i32, [c_vp, c_vp]),
+    ("scn_gated_hist_scores", c_i32, [c_vp, c_vp, ctypes.c_float, c_vp, c_vp, c_vp, _P(c_i64), c_vp]),
+    ("scn_proposal_hist_scores", c_i32, [c_vp, c_vp, ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_vp, _P(c_i64), c_vp]),
+    ("scn_thumb_diff", c_i32, [c_vp, c_i64, c_vp, c_vp]),
     ("scn_resize_norm", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_i32, c_vp, c_vp]),
     ("scn_thumbs", c_i32, [c_vp, c_vp, c_vp]),
 ]
@@ -405,6 +408,24 @@ def scn_cnn_activation(c: int, layer: int) -> int:
 
 def scn_cnn_sync_status(c: int, stream=None) -> int:
     return int(_lib.scn_cnn_sync_status(c, _stream(stream)))
+
+
+def scn_gated_hist_scores(s: int, gate, tau: float, proposed, score, flag, stream=None) -> int:
+    m = c_i64()
+    _check(_lib.scn_gated_hist_scores(s, _ptr(gate), tau, _ptr(proposed), _ptr(score), _ptr(flag), ctypes.byref(m),
+                                      _stream(stream)), "scn_gated_hist_scores")
+    return m.value
+
+
+def scn_proposal_hist_scores(s: int, net: int, tau: float, thumbs, logits, proposed, score, flag, stream=None) -> int:
+    m = c_i64()
+    _check(_lib.scn_proposal_hist_scores(s, net, tau, _ptr(thumbs), _ptr(logits), _ptr(proposed), _ptr(score),
+                                         _ptr(flag), ctypes.byref(m), _stream(stream)), "scn_proposal_hist_scores")
+    return m.value
+
+
+def scn_thumb_diff(thumbs, n: int, diff, stream=None) -> None:
+    _check(_lib.scn_thumb_diff(_ptr(thumbs), n, _ptr(diff), _stream(stream)), "scn_thumb_diff")
 
 
 def scn_resize_norm(s: int, oh: int, ow: int, mean, std, dtype: int, out, stream=None) -> None:
