@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-proposal", action="store_true")
     return ap.parse_args()
 
 
@@ -299,6 +300,23 @@ def main():
         torch.cuda.empty_cache()
         batched = run_batched(args, scn, torch, stream)
 
+    # ---- learned proposal: train on the GPU, threshold on held-out videos, speedup at >= 99% recall
+    prop = None
+    if not args.no_proposal:
+        from paper_1805_07339_b300 import proposal
+        torch.cuda.empty_cache()
+        res = proposal.run(torch)
+        res.pop("params", None)
+        prop = {"workload": "train 201,572 consecutive 1080p pairs (28 videos), thresholds on 8 held-out videos, "
+                            "evaluate 100,800 fresh frames (14 videos)",
+                "recall": res["learned"]["recall"], "precision": res["learned"]["precision"],
+                "speedup": res["learned"]["speedup"], "t_plain_ms": res["t_plain_ms"],
+                "t_proposal_ms": res["learned"]["t_ms"], "boundaries": res["boundaries"],
+                "proposed": res["learned"]["proposed"], "tau": res["tau"],
+                "exact_on_proposed": res["learned"]["exact_on_proposed"],
+                "train_seconds": res["train"]["seconds"], "train_steps": res["train"]["steps"],
+                "thumbnail_difference_gate": res["diff"]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ncores = os.cpu_count() or 1
@@ -321,7 +339,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_GB_per_s": frames_per_step * ALG_BYTES_PER_FRAME / (ms_step / 1000) / 1e9,
             "kernels": kern, "roofline": roofline, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
-            "e2e": e2e, "cpu_baseline": cpu, "batched": batched,
+            "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "proposal": prop,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

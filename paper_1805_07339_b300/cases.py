@@ -12,7 +12,7 @@ import argparse
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("kernel", choices=["hist", "resize", "thumbs"])
+    ap.add_argument("kernel", choices=["hist", "resize", "thumbs", "proposal"])
     ap.add_argument("--frames", type=int, default=512)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--stride", type=int, default=1)
@@ -44,10 +44,28 @@ def main() -> None:
         o = torch.empty((n, 3, 224, 224), dtype=torch.float32, device="cuda")
         for _ in range(a.reps):
             scn.scn_resize_norm(seq, 224, 224, (0.485, 0.456, 0.406), (0.229, 0.224, 0.225), scn.SCN_F32, o)
-    else:
+    elif a.kernel == "thumbs":
         o = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
         for _ in range(a.reps):
             scn.scn_thumbs(seq, o)
+    else:
+        # learned proposal path with He-uniform weights and a threshold that
+        # proposes about 1% of the pairs
+        from .proposal import he_uniform
+        net = scn.scn_cnn_create(4096)
+        scn.scn_cnn_set_params(net, he_uniform(0))
+        th = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
+        z = torch.full((n,), -1e30, dtype=torch.float32, device="cuda")
+        scn.scn_thumbs(seq, th)
+        scn.scn_cnn_forward(net, th, n - 1, z[1:])
+        tau = float(torch.quantile(z[1:], 0.99).item())
+        pr = torch.empty(n, dtype=torch.uint8, device="cuda")
+        sc = torch.empty(n, dtype=torch.int32, device="cuda")
+        fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_proposal_hist_scores(seq, net, tau, th, z, pr, sc, fl)
+        assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
+        scn.scn_cnn_destroy(net)
     torch.cuda.synchronize()
     assert scn.scn_seq_sync_status(seq) == scn.SCN_OK
     scn.scn_seq_destroy(seq)
