@@ -32,6 +32,24 @@ METRIC = "1080p sampled frames/s + HBM GB/s (hist+shot score); proposal speedup 
 FRAME_BYTES = 1920 * 1080 * 3 // 2
 ALG_BYTES_PER_FRAME = FRAME_BYTES + 48 * 4 + 4 + 1  # NV12 read + hist, score, flag written
 
+# DRAM traffic of hist_kernel from one ncu capture (profiles/hist_kernel_1080p_512frames.md:
+# dram__bytes_read.sum + dram__bytes_write.sum over 512 frames), per frame; it scales with the
+# frames of a launch.  Valid only for the kernel sources it was taken on (hash below).
+PROFILED_TRAFFIC = {"bytes_per_frame": 3118278.1, "frames_captured": 512,
+                    "sources": ("scn_hist.cu", "scn_internal.h", "scn_ptx.cuh"), "sha256_16": "b229473060189a65"}
+
+
+def profiled_traffic(frames: int):
+    """Per-launch DRAM bytes for `frames` frames, or None if the kernel changed since the capture."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in PROFILED_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_1805_07339_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != PROFILED_TRAFFIC["sha256_16"]:
+        return None
+    return PROFILED_TRAFFIC["bytes_per_frame"] * frames
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -280,7 +298,7 @@ def main():
         peak = 6400.0
     dom = kern["stride1"]
     roofline = {"bound": "hbm", "achieved": dom["GB_per_s"], "peak": peak, "unit": "GB/s",
-                "frac": dom["GB_per_s"] / peak, "traffic": None, "peak_source": peak_kind,
+                "frac": dom["GB_per_s"] / peak, "traffic": profiled_traffic(dom["frames"]), "peak_source": peak_kind,
                 "kernel": "hist_kernel (scn_hist_scores, stride-1, 7200 frames)",
                 "alg_bytes_per_launch": dom["frames"] * ALG_BYTES_PER_FRAME}
 
