@@ -269,10 +269,13 @@ scn_status scn_cnn_destroy(scn_cnn* c);
  * optimiser state.  Synchronous. */
 scn_status scn_cnn_set_params(scn_cnn* c, const float* h_params, int64_t n);
 scn_status scn_cnn_get_params(const scn_cnn* c, float* h_params, int64_t n);
-/* Logits of n thumbnail pairs.  d_thumbs: uint8 [*][36][64] (device).  Pair b
- * is (d_prev[b], d_cur[b]) (device int32 thumbnail indices) or, when both are
- * NULL, (b, b+1).  Runs in chunks of max_batch pairs; the activations of the
- * last chunk stay readable through scn_cnn_activation. */
+/* Logits of n thumbnail pairs (any n; inference, Sec. 5.1.2 DNN over sampled
+ * frames).  d_thumbs: uint8 [*][36][64] (device, 16-byte aligned, else
+ * SCN_EINVAL).  Pair b is (d_prev[b], d_cur[b]) (device int32 thumbnail
+ * indices, which the caller keeps inside the thumbnail array) or, when both are
+ * NULL, (b, b+1).  One launch of a fused kernel that keeps every activation on
+ * chip; it stores no activations (scn_cnn_activation shows the last training
+ * batch). */
 scn_status scn_cnn_forward(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
                            int64_t n, float* d_logits, void* stream);
 /* Gradients of the batch-mean BCE-with-logits loss (positive weight
@@ -290,7 +293,7 @@ scn_status scn_cnn_train_step(scn_cnn* c, const uint8_t* d_thumbs, const int32_t
                               const float* d_labels, int64_t batch, float pos_weight, float lr, float* d_loss,
                               void* stream);
 /* Device pointer to the BF16 NHWC output of conv layer 1, 2 or 3 of the last
- * forward chunk ([pairs][positions][channels]). */
+ * scn_cnn_gradients / scn_cnn_train_step batch ([pairs][positions][channels]). */
 scn_status scn_cnn_activation(const scn_cnn* c, int32_t layer, const void** d_ptr);
 /* Synchronise stream, read and clear the network's device status word. */
 scn_status scn_cnn_sync_status(scn_cnn* c, void* stream);

@@ -356,6 +356,532 @@ scn_status forward_chunk(Net* n, const uint8_t* thumbs, const int32_t* prev, con
 }
 
 // ---------------------------------------------------------------------------
+// fused forward (inference): the whole network in one persistent kernel
+// ---------------------------------------------------------------------------
+// A CTA takes kFzPairs pairs at a time and keeps every activation in shared
+// memory.  Each convolution is an implicit GEMM whose A operand the tensor core
+// reads straight out of the activation buffer, one filter tap per MMA (no
+// im2col copy): the buffers are laid out so that, for a fixed tap, the 8-row
+// core matrices of the output positions sit at one constant stride.  Stride 2
+// is absorbed by keeping even and odd input columns (for layer 1 also even and
+// odd input rows) in separate planes; the zero padding of the convolutions is
+// stored as explicit zero rows and entries.  One "entry" is 8 bf16 (16 bytes):
+// 8 channels of one pixel, or for layer 1 the 2 channels of 3 neighbouring
+// columns plus 2 zeros.
+//
+// Tiles are 16 groups of 8 output positions (M = 128).  Groups are enumerated
+// so that consecutive groups are consecutive output rows (layer 1: 4 groups per
+// row); the last tile of a layer starts at G - 16 and keeps only the groups it
+// adds, and group slots past a pair's last output row are computed and dropped.
+constexpr int kFzPairs = 2;  // the zero-row lists of phases 0 and 2 are written for two pairs
+constexpr int kFzThreads = 256;
+// layer 1 input X1: planes O1 (odd input rows; row 0 of a pair = zero padding
+// above the image) and E1 (even input rows; row 18 of a pair = zeros); a plane
+// row holds the 32 output columns ox, entry ox = [prev, cur] at input columns
+// 2ox-1, 2ox, 2ox+1, then 2 zeros
+constexpr int kFzR1 = 19;
+constexpr int kFzX1Rows = kFzPairs * kFzR1 + 1;
+constexpr int kFzX1Plane = kFzX1Rows * 512;
+constexpr int kFzG1 = kFzPairs * kFzR1 * 4;
+constexpr int kFzT1 = (kFzG1 + 15) / 16;
+// layer 2 input A1 (a1, 16 channels = 2 chunks): per chunk an even-column plane
+// (16 entries per row, entry m = column 2m) and an odd-column plane (17 entries,
+// entry u = column 2u-1, entry 0 = zero padding); row 0 of a pair = zero padding,
+// rows 1..18 = a1 rows, row 19 spare
+constexpr int kFzR2 = 20;
+constexpr int kFzA1Rows = kFzPairs * kFzR2 + 1;
+constexpr int kFzE2Pitch = 16 * 16, kFzO2Pitch = 17 * 16;
+constexpr int kFzE2Plane = kFzA1Rows * kFzE2Pitch, kFzO2Plane = kFzA1Rows * kFzO2Pitch;
+constexpr int kFzG2 = kFzPairs * 10;  // groups per column half (9 output rows + 1 dropped)
+// layer 3 input A2 (a2, 32 channels = 4 chunks): even plane 8 entries, odd plane
+// 9 entries; row 0 of each pair and row kFzPairs*10 = zero padding (row 10 of a
+// pair is row 0 of the next).  Dropped groups read past a plane into the next
+// one or into the head's scratch that follows; every such read stays in region 0.
+constexpr int kFzR3 = 10;
+constexpr int kFzA2Rows = kFzPairs * kFzR3 + 1;
+constexpr int kFzE3Pitch = 8 * 16, kFzO3Pitch = 9 * 16;
+constexpr int kFzE3Plane = kFzA2Rows * kFzE3Pitch, kFzO3Plane = kFzA2Rows * kFzO3Pitch;
+constexpr int kFzA2Bytes = 4 * (kFzE3Plane + kFzO3Plane);
+constexpr int kFzG3 = kFzPairs * 5;
+// head scratch in region 0 after a2 (phases 2-4): F1 transposed (fp32 [32][64]), pooled g, hidden v
+constexpr int kFzF1T = 24576;
+constexpr int kFzGs = kFzF1T + 32 * 64 * 4;
+constexpr int kFzVs = kFzGs + kFzPairs * 32 * 4;
+// MMA descriptor table: conv1 2 per tile, conv2 9 per tile, conv3 18
+constexpr int kFzD1 = 0, kFzD2 = kFzD1 + 2 * kFzT1, kFzD3 = kFzD2 + 4 * 9, kFzNDesc = kFzD3 + 18;
+// shared-memory map (bytes)
+constexpr int kFzW1 = 0;                           // [16][32]  core layout, k = dy*8 + dx*2 + c
+constexpr int kFzW2 = kFzW1 + 16 * 32 * 2;         // 9 x [32][16]
+constexpr int kFzW3 = kFzW2 + 9 * 32 * 16 * 2;     // 9 x [32][32]
+constexpr int kFzBias = kFzW3 + 9 * 32 * 32 * 2;   // floats: b1 16, b2 32, b3 32, c1 64, f2 64, c2 1
+constexpr int kFzDesc = kFzBias + 1024;            // kFzNDesc x (A, B) descriptors
+constexpr int kFzBar = kFzDesc + kFzNDesc * 16;    // mbarriers, TMEM address
+constexpr int kFzNBar = kFzT1 + 8 + 3;  // conv1 tiles, conv2 tile x tap range, conv3 tap range
+constexpr int kFzReg0 = kFzBar + 256;              // X1, later a2 + head scratch
+constexpr int kFzReg0Bytes = 2 * kFzX1Plane;
+constexpr int kFzReg1 = kFzReg0 + kFzReg0Bytes;    // A1, later a3 (fp32) over its first plane
+constexpr int kFzReg1Bytes = 2 * kFzE2Plane + 2 * kFzO2Plane;
+constexpr int kFzSmem = kFzReg1 + kFzReg1Bytes;
+constexpr int kFzG3Bytes = kFzPairs * 40 * 32 * 4;
+static_assert(kFzNBar * 8 + 4 <= 256, "barrier area");
+static_assert(kFzG3Bytes <= kFzE2Plane - kFzE2Pitch, "a3 overlays the first a1 plane except its last row");
+static_assert(kFzSmem <= 115712, "two CTAs per SM");
+static_assert(kFzG1 >= 16 && kFzG2 >= 16, "every layer-1/2 tile lies inside the buffers");
+// every row the MMAs read lies inside its plane (layers 1, 2) or inside region 0 (layer 3)
+static_assert((kFzG1 - 1) / 4 + 1 < kFzX1Rows, "layer-1 reads");
+static_assert(2 * (kFzG2 - 1) + 2 < kFzA1Rows, "layer-2 reads");
+static_assert(4 * kFzE3Plane + 3 * kFzO3Plane + (2 * 15 + 2 + 1) * kFzO3Pitch <= kFzF1T, "layer-3 reads");
+static_assert(kFzA2Bytes <= kFzF1T && kFzVs + kFzPairs * 64 * 4 <= kFzReg0Bytes, "region 0 in phases 2-4");
+
+struct FusedArgs {
+    const uint8_t* thumbs;
+    const int32_t* prev;      // null: pair b = (b, b + 1)
+    const int32_t* cur;
+    int64_t pairs;
+    const __nv_bfloat16* w1b;  // [16][32], k = tap*2 + c
+    const __nv_bfloat16* w2b;  // [32][144], k = tap*16 + ci
+    const __nv_bfloat16* w3b;  // [32][288], k = tap*32 + ci
+    const float* master;       // fp32 parameters (biases)
+    const __nv_bfloat16* f1b;
+    const __nv_bfloat16* f2b;
+    float* logits;
+    int* status;
+};
+
+// (byte k of w - 128) / 64 as fp32: the byte placed in the mantissa of 2^23
+// (one prmt) gives 2^23 + byte exactly; one fma scales and shifts it, exactly
+// (the result needs 23 significant bits at most)
+template <int K>
+__device__ __forceinline__ float thumb_at(const uint32_t (&w)[8]) {
+    const uint32_t m = ptx::prmt(w[K >> 2], 0x4B000000u, 0x7540u | (K & 3));
+    return fmaf(__uint_as_float(m), 1.f / 64.f, -(8388608.f / 64.f + 2.f));
+}
+
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// entry i of a 32-column block: [prev, cur] at block columns 2i-1, 2i, 2i+1, zeros
+template <int I>
+__device__ __forceinline__ void x1_entry(uint8_t* row, const uint32_t (&p)[8], const uint32_t (&q)[8], uint32_t w0) {
+    if constexpr (I > 0) w0 = bf16x2(thumb_at<2 * I - 1>(p), thumb_at<2 * I - 1>(q));
+    const uint32_t w1 = bf16x2(thumb_at<2 * I>(p), thumb_at<2 * I>(q));
+    const uint32_t w2 = bf16x2(thumb_at<2 * I + 1>(p), thumb_at<2 * I + 1>(q));
+    *reinterpret_cast<uint4*>(row + I * 16) = make_uint4(w0, w1, w2, 0u);
+}
+
+// 16 layer-1 input entries of one input row (32 columns from column 32 hh) of one
+// pair; w0 = the entry-0 word for column 32 hh - 1 (zero padding when hh = 0)
+__device__ __forceinline__ void x1_entries(uint8_t* row, const uint32_t (&p)[8], const uint32_t (&q)[8], uint32_t w0) {
+    x1_entry<0>(row, p, q, w0);
+    x1_entry<1>(row, p, q, 0);
+    x1_entry<2>(row, p, q, 0);
+    x1_entry<3>(row, p, q, 0);
+    x1_entry<4>(row, p, q, 0);
+    x1_entry<5>(row, p, q, 0);
+    x1_entry<6>(row, p, q, 0);
+    x1_entry<7>(row, p, q, 0);
+    x1_entry<8>(row, p, q, 0);
+    x1_entry<9>(row, p, q, 0);
+    x1_entry<10>(row, p, q, 0);
+    x1_entry<11>(row, p, q, 0);
+    x1_entry<12>(row, p, q, 0);
+    x1_entry<13>(row, p, q, 0);
+    x1_entry<14>(row, p, q, 0);
+    x1_entry<15>(row, p, q, 0);
+}
+
+__device__ __forceinline__ bool fz_wait(uint64_t* bar, uint32_t par, bool ok, int* status) {
+    if (ok && !ptx::mbar_wait_bounded(bar, par, kWaitNs)) {
+        atomicOr(status, kStatusTimeout);
+        ok = false;
+    }
+    __syncwarp();
+    tc::fence_after_sync();
+    return ok;
+}
+
+__device__ __forceinline__ void fz_sync() {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_constant__ FusedArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = 32 * quad + lane;  // TMEM lane = tile row of this thread in epilogues
+    float* bias = reinterpret_cast<float*>(smem + kFzBias);  // b1 @0, b2 @16, b3 @48, c1 @80, f2 @144, c2 @208
+    uint64_t* desc = reinterpret_cast<uint64_t*>(smem + kFzDesc);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kFzBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kFzBar + kFzNBar * 8);
+    uint8_t* reg0 = smem + kFzReg0;
+    uint8_t* reg1 = smem + kFzReg1;
+    uint8_t* O1 = reg0;
+    uint8_t* E1 = reg0 + kFzX1Plane;
+    uint8_t* E3 = reg0;
+    uint8_t* O3 = reg0 + 4 * kFzE3Plane;
+    float* f1t = reinterpret_cast<float*>(reg0 + kFzF1T);
+    float* gs = reinterpret_cast<float*>(reg0 + kFzGs);
+    float* vs = reinterpret_cast<float*>(reg0 + kFzVs);
+    uint8_t* E2 = reg1;
+    uint8_t* O2 = reg1 + 2 * kFzE2Plane;
+    float* a3 = reinterpret_cast<float*>(reg1);
+    const uint32_t sbase = ptx::smem_u32(smem);
+
+    // ---- once: weights in tensor-core layouts, biases, descriptors, zeroed A1, barriers, TMEM
+    for (int e = tid; e < 16 * 4; e += kFzThreads) {  // W1: 16 rows x 4 entries
+        const int n = e >> 2, j = e & 3;
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint16_t h[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int k = 8 * j + 2 * q + s, dy = k >> 3, rem = k & 7, dx = rem >> 1, c = rem & 1;
+                h[s] = (dy < 3 && rem < 6) ? __bfloat16_as_ushort(a.w1b[n * 32 + (dy * 3 + dx) * 2 + c]) : 0;
+            }
+            w[q] = static_cast<uint32_t>(h[0]) | (static_cast<uint32_t>(h[1]) << 16);
+        }
+        *reinterpret_cast<uint4*>(smem + kFzW1 + tc::core_offset(n, 8 * j, 32)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    for (int e = tid; e < 9 * 32 * 2; e += kFzThreads) {  // W2: tap x 32 rows x 2 entries
+        const int t = e / 64, n = (e >> 1) & 31, j = e & 1;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w2b + n * 144 + t * 16 + 8 * j));
+        *reinterpret_cast<uint4*>(smem + kFzW2 + t * 1024 + tc::core_offset(n, 8 * j, 16)) = v;
+    }
+    for (int e = tid; e < 9 * 32 * 4; e += kFzThreads) {  // W3: tap x 32 rows x 4 entries
+        const int t = e / 128, n = (e >> 2) & 31, j = e & 3;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w3b + n * 288 + t * 32 + 8 * j));
+        *reinterpret_cast<uint4*>(smem + kFzW3 + t * 2048 + tc::core_offset(n, 8 * j, 32)) = v;
+    }
+    if (tid < 16) bias[tid] = a.master[kB1 + tid];
+    if (tid < 32) {
+        bias[16 + tid] = a.master[kB2 + tid];
+        bias[48 + tid] = a.master[kB3 + tid];
+    }
+    if (tid < 64) {
+        bias[80 + tid] = a.master[kC1 + tid];
+        bias[144 + tid] = __bfloat162float(a.f2b[tid]);
+    }
+    if (tid == 0) bias[208] = a.master[kC2];
+    if (tid < kFzNDesc) {
+        // the operand addresses are the same for every batch
+        uint64_t ad, bd;
+        const int i = tid;
+        const uint32_t s_o1 = sbase + kFzReg0, s_e2 = sbase + kFzReg1, s_o2 = s_e2 + 2 * kFzE2Plane;
+        const uint32_t s_e3 = sbase + kFzReg0, s_o3 = s_e3 + 4 * kFzE3Plane;
+        if (i < kFzD2) {  // conv1: tile t, K half k
+            const int t = i >> 1, k = i & 1, g0 = min(16 * t, kFzG1 - 16);
+            ad = tc::smem_desc(s_o1 + 512 * k + g0 * 128, kFzX1Plane, 128);
+            bd = tc::smem_desc(sbase + kFzW1 + 256 * k, 128, 512);
+        } else if (i < kFzD3) {  // conv2: tile tt (column half h, first group g0), tap
+            const int tt = (i - kFzD2) / 9, tap = (i - kFzD2) % 9, dy = tap / 3, dx = tap % 3;
+            const int h = tt >> 1, g0 = (tt & 1) ? kFzG2 - 16 : 0;
+            const uint32_t plane = dx == 1 ? s_e2 : s_o2;
+            const uint32_t rp = dx == 1 ? kFzE2Pitch : kFzO2Pitch;
+            const uint32_t cs = dx == 1 ? kFzE2Plane : kFzO2Plane;
+            ad = tc::smem_desc(plane + (2 * g0 + dy) * rp + (8 * h + (dx == 2 ? 1 : 0)) * 16, cs, 2 * rp);
+            bd = tc::smem_desc(sbase + kFzW2 + tap * 1024, 128, 256);
+        } else {  // conv3: tap, K half kk
+            const int j = i - kFzD3, tap = j >> 1, kk = j & 1, dy = tap / 3, dx = tap % 3;
+            const uint32_t plane = dx == 1 ? s_e3 : s_o3;
+            const uint32_t rp = dx == 1 ? kFzE3Pitch : kFzO3Pitch;
+            const uint32_t cs = dx == 1 ? kFzE3Plane : kFzO3Plane;
+            ad = tc::smem_desc(plane + 2 * kk * cs + dy * rp + (dx == 2 ? 16 : 0), cs, 2 * rp);
+            bd = tc::smem_desc(sbase + kFzW3 + tap * 2048 + kk * 256, 128, 512);
+        }
+        desc[2 * i] = ad;
+        desc[2 * i + 1] = bd;
+    }
+    for (int e = tid; e < kFzReg1Bytes / 16; e += kFzThreads)
+        reinterpret_cast<uint4*>(reg1)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int i = 0; i < kFzNBar; ++i) ptx::mbar_init(bar + i, 1);
+        ptx::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 256);
+    fz_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t tlane = static_cast<uint32_t>(32 * quad) << 16;
+    bool ok = true;
+
+    // phase-0 build task of this thread: pair p, input row iy, 32-column block hh
+    const int bp_ = tid / 72, biy = (tid >> 1) % 36, bhh = tid & 1;
+    const bool builder = tid < kFzPairs * 72;
+    const int64_t nbatch = (a.pairs + kFzPairs - 1) / kFzPairs;
+    auto pair_thumbs = [&](int64_t batch, int64_t& ip, int64_t& ic) {
+        int64_t b = batch * kFzPairs + bp_;
+        if (b >= a.pairs) b = a.pairs - 1;
+        ip = a.prev ? a.prev[b] : b;
+        ic = a.cur ? a.cur[b] : b + 1;
+    };
+    int64_t ip = 0, ic = 0;
+    if (builder && blockIdx.x < nbatch) pair_thumbs(blockIdx.x, ip, ic);
+    uint32_t it = 0;
+    for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x, ++it) {
+        const uint32_t par = it & 1u;
+        // ---- phase 0: layer-1 input planes; zero rows; zero rows of the first A1 plane that a3 overwrote
+        if (builder) {
+            const uint8_t* tp = a.thumbs + ip * 2304 + biy * 64 + 32 * bhh;
+            const uint8_t* tq = a.thumbs + ic * 2304 + biy * 64 + 32 * bhh;
+            const uint4 p0 = __ldg(reinterpret_cast<const uint4*>(tp));
+            const uint4 p1 = __ldg(reinterpret_cast<const uint4*>(tp + 16));
+            const uint4 q0 = __ldg(reinterpret_cast<const uint4*>(tq));
+            const uint4 q1 = __ldg(reinterpret_cast<const uint4*>(tq + 16));
+            const uint32_t before_p = bhh ? __ldg(tp - 1) : 0u, before_q = bhh ? __ldg(tq - 1) : 0u;
+            const uint32_t pw[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+            const uint32_t qw[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+            uint8_t* row = (biy & 1) ? O1 + (bp_ * kFzR1 + ((biy + 1) >> 1)) * 512 : E1 + (bp_ * kFzR1 + (biy >> 1)) * 512;
+            const float bpf = fmaf(static_cast<float>(before_p), 1.f / 64.f, -2.f);
+            const float bqf = fmaf(static_cast<float>(before_q), 1.f / 64.f, -2.f);
+            x1_entries(row + 16 * 16 * bhh, pw, qw, bhh ? bf16x2(bpf, bqf) : 0u);  // entries 16 hh ..
+        } else {
+            for (int z = tid - kFzPairs * 72; z < 6 * 32 + kFzPairs * 16; z += kFzThreads - kFzPairs * 72) {
+                uint8_t* dst;
+                if (z < 6 * 32) {  // zero rows: O1 {0, 19, 38}, E1 {18, 37, 38}
+                    const int which = z >> 5, ox = z & 31;
+                    const int zr = which == 0 ? 0 : which == 1 ? kFzR1 : which == 2 ? 2 * kFzR1
+                                 : which == 3 ? kFzR1 - 1 : which == 4 ? 2 * kFzR1 - 1 : 2 * kFzR1;
+                    dst = (which < 3 ? O1 : E1) + zr * 512 + ox * 16;
+                } else {
+                    const int y = z - 6 * 32;
+                    dst = E2 + ((y >> 4) * kFzR2) * kFzE2Pitch + (y & 15) * 16;
+                }
+                *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+            }
+        }
+        fz_sync();
+
+        // ---- phase 1: conv1, kFzT1 tiles of 128 x 16, issued by lane 0 of warp t % 8 (one
+        //      issuing thread is slower: each MMA waits for the tensor core to take it)
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 16);
+            for (int t = warp; t < kFzT1; t += kFzThreads / 32) {
+                tc::mma(tmem + 16 * t, desc[4 * t], desc[4 * t + 1], idesc, 0u);
+                tc::mma(tmem + 16 * t, desc[4 * t + 2], desc[4 * t + 3], idesc, 1u);
+                tc::commit(bar + t);
+            }
+        }
+        __syncwarp();
+        for (int t2 = half; t2 < kFzT1; t2 += 4) {
+            // tiles t2 and t2 + 2 of this warp's parity: both TMEM loads in flight at once
+            const bool two = t2 + 2 < kFzT1;
+            ok = fz_wait(bar + t2, par, ok, a.status);
+            if (two) ok = fz_wait(bar + t2 + 2, par, ok, a.status);
+            uint32_t accs[2][16];
+            tc::ld16(tmem + tlane + 16 * t2, accs[0]);
+            if (two) tc::ld16(tmem + tlane + 16 * (t2 + 2), accs[1]);
+            tc::wait_ld();
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !two) break;
+            const int t = t2 + 2 * u;
+            const uint32_t (&acc)[16] = accs[u];
+            const int g0 = min(16 * t, kFzG1 - 16);
+            const int g = g0 + (r >> 3);
+            const int p = g / (kFzR1 * 4), rem = g - p * (kFzR1 * 4), oy = rem >> 2;
+            if (g >= 16 * t && oy < 18) {
+                const int ox = 8 * (rem & 3) + (r & 7);
+                uint32_t o[8];
+#pragma unroll
+                for (int c = 0; c < 16; c += 2)
+                    o[c / 2] = pack_bf16(fmaxf(__uint_as_float(acc[c]) + bias[c], 0.f),
+                                         fmaxf(__uint_as_float(acc[c + 1]) + bias[c + 1], 0.f));
+                const int row = p * kFzR2 + oy + 1;
+                uint8_t* dst = (ox & 1) ? O2 + row * kFzO2Pitch + ((ox + 1) >> 1) * 16 : E2 + row * kFzE2Pitch + (ox >> 1) * 16;
+                const int cs = (ox & 1) ? kFzO2Plane : kFzE2Plane;
+                *reinterpret_cast<uint4*>(dst) = make_uint4(o[0], o[1], o[2], o[3]);
+                *reinterpret_cast<uint4*>(dst + cs) = make_uint4(o[4], o[5], o[6], o[7]);
+            }
+            }
+        }
+        fz_sync();
+
+        // ---- phase 2: conv2, 2 column halves x 2 tiles of 128 x 32; each tile accumulates
+        //      taps 0-4 and taps 5-8 in two TMEM blocks, issued by lane 0 of 8 warps (short
+        //      chains: each MMA waits for the tensor core to take it); zero padding of A2;
+        //      F1 transposed into region 0 for the head
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
+            const int tt = warp >> 1, k = warp & 1, t0 = 5 * k, t1 = k ? 9 : 5;
+            const uint64_t* d = desc + 2 * (kFzD2 + 9 * tt);
+            for (int tap = t0; tap < t1; ++tap)
+                tc::mma(tmem + 64 * tt + 32 * k, d[2 * tap], d[2 * tap + 1], idesc, tap > t0 ? 1u : 0u);
+            tc::commit(bar + kFzT1 + warp);
+        }
+        __syncwarp();
+        for (int e = tid; e < 3 * 4 * (8 + 9) + 2 * 9 * 4; e += kFzThreads) {
+            uint8_t* dst;
+            if (e < 3 * 4 * 17) {
+                const int rz = e / 68, c = (e / 17) & 3, k = e % 17;  // rows 0, 10, 20
+                dst = k < 8 ? E3 + c * kFzE3Plane + (rz * kFzR3) * kFzE3Pitch + k * 16
+                            : O3 + c * kFzO3Plane + (rz * kFzR3) * kFzO3Pitch + (k - 8) * 16;
+            } else {
+                const int z = e - 3 * 4 * 17, c = z & 3, rr = z >> 2, row = (rr / 9) * kFzR3 + 1 + rr % 9;
+                dst = O3 + c * kFzO3Plane + row * kFzO3Pitch;  // entry 0: column -1
+            }
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+        }
+        {
+            const int j = tid >> 2, c0 = (tid & 3) * 8;  // F1 row j, columns c0..c0+7
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.f1b + j * 32 + c0));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                f1t[(c0 + q) * 64 + j] = __uint_as_float((q & 1) ? (w[q >> 1] & 0xFFFF0000u) : (w[q >> 1] << 16));
+        }
+        for (int tt = half; tt < 4; tt += 2) {
+            ok = fz_wait(bar + kFzT1 + 2 * tt, par, ok, a.status);
+            ok = fz_wait(bar + kFzT1 + 2 * tt + 1, par, ok, a.status);
+            const int h = tt >> 1, first = (tt & 1) ? 16 : 0, g0 = (tt & 1) ? kFzG2 - 16 : 0;
+            const int g = g0 + (r >> 3), p = g / 10, oy = g - 10 * p;
+            const bool live = g >= first && oy < 9;
+            const int ox = 8 * h + (r & 7);
+            const int row = p * kFzR3 + oy + 1;
+            uint8_t* dst = (ox & 1) ? O3 + row * kFzO3Pitch + ((ox + 1) >> 1) * 16 : E3 + row * kFzE3Pitch + (ox >> 1) * 16;
+            const int cs = (ox & 1) ? kFzO3Plane : kFzE3Plane;
+#pragma unroll
+            for (int c0 = 0; c0 < 32; c0 += 16) {
+                uint32_t u0[16], u1[16];
+                tc::ld16(tmem + tlane + 64 * tt + c0, u0);
+                tc::ld16(tmem + tlane + 64 * tt + 32 + c0, u1);
+                tc::wait_ld();
+                if (live) {
+                    uint32_t o[8];
+#pragma unroll
+                    for (int c = 0; c < 16; c += 2)
+                        o[c / 2] = pack_bf16(
+                            fmaxf(__uint_as_float(u0[c]) + __uint_as_float(u1[c]) + bias[16 + c0 + c], 0.f),
+                            fmaxf(__uint_as_float(u0[c + 1]) + __uint_as_float(u1[c + 1]) + bias[16 + c0 + c + 1], 0.f));
+                    const int q = c0 / 8;
+                    *reinterpret_cast<uint4*>(dst + q * cs) = make_uint4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<uint4*>(dst + (q + 1) * cs) = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+            }
+        }
+        fz_sync();
+
+        // ---- phase 3: conv3, one tile of 128 x 32 (groups past kFzG3 are dropped); taps
+        //      0-2, 3-5, 6-8 accumulate in three TMEM blocks, issued by lane 0 of warps 0-2
+        if (lane == 0 && warp < 3) {
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
+            const uint64_t* d = desc + 2 * (kFzD3 + 6 * warp);
+#pragma unroll
+            for (int m = 0; m < 6; ++m) tc::mma(tmem + 32 * warp, d[2 * m], d[2 * m + 1], idesc, m > 0 ? 1u : 0u);
+            tc::commit(bar + kFzT1 + 8 + warp);
+        }
+        __syncwarp();
+        {
+            ok = fz_wait(bar + kFzT1 + 8, par, ok, a.status);
+            ok = fz_wait(bar + kFzT1 + 9, par, ok, a.status);
+            ok = fz_wait(bar + kFzT1 + 10, par, ok, a.status);
+            uint32_t acc[16];
+            {
+                uint32_t u0[16], u1[16], u2[16];
+                tc::ld16(tmem + tlane + 16 * half, u0);
+                tc::ld16(tmem + tlane + 32 + 16 * half, u1);
+                tc::ld16(tmem + tlane + 64 + 16 * half, u2);
+                tc::wait_ld();
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    acc[c] = __float_as_uint(__uint_as_float(u0[c]) + __uint_as_float(u1[c]) + __uint_as_float(u2[c]));
+            }
+            const int g = r >> 3;
+            if (g < kFzG3) {
+                const int p = g / 5, oy = g - 5 * p, pos = oy * 8 + (r & 7);
+                float* dst = a3 + (p * 40 + pos) * 32 + 16 * half;
+                const float* b3 = bias + 48 + 16 * half;
+#pragma unroll
+                for (int c = 0; c < 16; c += 4) {
+                    float4 v;
+                    v.x = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c]) + b3[c], 0.f)));
+                    v.y = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c + 1]) + b3[c + 1], 0.f)));
+                    v.z = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c + 2]) + b3[c + 2], 0.f)));
+                    v.w = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c + 3]) + b3[c + 3], 0.f)));
+                    *reinterpret_cast<float4*>(dst + c) = v;
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+
+        // ---- phase 4: pooling (thread per pair and channel), FC 32->64 (thread per pair and
+        //      unit), FC 64->1 (warp per pair); the next batch's pair indices are fetched meanwhile
+        if (tid < kFzPairs * 32) {
+            const float* src = a3 + (tid >> 5) * 40 * 32 + (tid & 31);
+            float s = 0.f;
+            for (int pos = 0; pos < 40; ++pos) s += src[pos * 32];
+            gs[tid] = s * (1.f / 40.f);
+        } else if (builder && batch + gridDim.x < nbatch) {
+            pair_thumbs(batch + gridDim.x, ip, ic);
+        }
+        __syncthreads();
+        if (tid < kFzPairs * 64) {
+            const int p = tid >> 6, j = tid & 63;
+            const float* g = gs + p * 32;
+            float v = bias[80 + j];
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c) v = fmaf(f1t[c * 64 + j], g[c], v);
+            vs[tid] = v;
+        }
+        if (tid < kFzPairs * 32 && builder && batch + gridDim.x < nbatch) pair_thumbs(batch + gridDim.x, ip, ic);
+        __syncthreads();
+        if (warp < kFzPairs) {
+            const int64_t b = batch * kFzPairs + warp;
+            if (b < a.pairs) {
+                const float* v = vs + warp * 64;
+                float zz = bias[144 + lane] * fmaxf(v[lane], 0.f) + bias[144 + lane + 32] * fmaxf(v[lane + 32], 0.f);
+                for (int o = 16; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
+                if (lane == 0) a.logits[b] = zz + bias[208];
+            }
+        }
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* prev, const int32_t* cur, int64_t pairs,
+                                float* logits, cudaStream_t st) {
+    static int attr_dev = -1;
+    int dev = 0;
+    SCN_CUDA_TRY(cudaGetDevice(&dev));
+    if (attr_dev != dev) {
+        SCN_CUDA_TRY(cudaFuncSetAttribute(cnn_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFzSmem));
+        SCN_CUDA_TRY(cudaFuncSetAttribute(cnn_forward_fused, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
+        attr_dev = dev;
+    }
+    FusedArgs a{};
+    a.thumbs = thumbs;
+    a.prev = prev;
+    a.cur = cur;
+    a.pairs = pairs;
+    a.w1b = n->w1b;
+    a.w2b = n->w2b;
+    a.w3b = n->w3b;
+    a.master = n->master;
+    a.f1b = n->f1b;
+    a.f2b = n->f2b;
+    a.logits = logits;
+    a.status = n->status;
+    const int64_t nbatch = (pairs + kFzPairs - 1) / kFzPairs;
+    int sms = device_sm_count();
+    if (sms <= 0) sms = 148;
+    const int grid = static_cast<int>(std::min<int64_t>(nbatch, static_cast<int64_t>(sms) * 2));
+    cnn_forward_fused<<<grid, kFzThreads, kFzSmem, st>>>(a);
+    SCN_CUDA_TRY(cudaGetLastError());
+    return SCN_OK;
+}
+
+// ---------------------------------------------------------------------------
 // training: head backward (warp per pair, register accumulation per warp)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ z, const float* __restrict__ y,
@@ -857,16 +1383,8 @@ scn_status scn_cnn_forward(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d
     if (!c || n < 0) return SCN_EINVAL;
     if (n == 0) return SCN_OK;
     if (!d_thumbs || !d_logits || (!d_prev) != (!d_cur)) return SCN_EINVAL;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    for (int64_t o = 0; o < n; o += c->net.max_batch) {
-        const int64_t m = std::min<int64_t>(c->net.max_batch, n - o);
-        // consecutive pairs (no index arrays): pair b of this chunk is (o + b, o + b + 1)
-        const uint8_t* th = d_prev ? d_thumbs : d_thumbs + o * 2304;
-        const scn_status s = forward_chunk(&c->net, th, d_prev ? d_prev + o : nullptr, d_cur ? d_cur + o : nullptr, m,
-                                           d_logits + o, false, st);
-        if (s != SCN_OK) return s;
-    }
-    return SCN_OK;
+    if (reinterpret_cast<uintptr_t>(d_thumbs) % 16) return SCN_EINVAL;  // rows are read as 16-byte vectors
+    return launch_forward_fused(&c->net, d_thumbs, d_prev, d_cur, n, d_logits, static_cast<cudaStream_t>(stream));
 }
 
 scn_status scn_cnn_gradients(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,

@@ -59,39 +59,68 @@ def oracle_x(th, prev, cur):
     return np.stack([ocnn.pair_input(th[a], th[b]) for a, b in zip(prev, cur)])
 
 
-@pytest.mark.parametrize("B", [1, 37, 300])
+@pytest.mark.parametrize("B", [1, 2, 3, 37, 300, 1501])
 def test_forward_matches_oracle(scn, B):
+    """Fused forward (one launch, activations on chip): odd counts leave a
+    half-filled last pair slot; 1501 pairs give most CTAs several iterations."""
     params = he_params(B)
     th, prev, cur = thumbs_and_pairs(B + 1, 64, B)
-    net = scn.scn_cnn_create(128)
+    net = scn.scn_cnn_create(8)  # the fused forward does not depend on max_batch
     try:
         scn.scn_cnn_set_params(net, params)
-        d_th = torch.from_numpy(th).cuda()
-        d_prev = torch.from_numpy(prev).cuda()
-        d_cur = torch.from_numpy(cur).cuda()
-        z = torch.full((B,), float("nan"), dtype=torch.float32, device="cuda")
-        scn.scn_cnn_forward(net, d_th, B, z, prev=d_prev, cur=d_cur)
+        z = torch.full((B + 1,), float("nan"), dtype=torch.float32, device="cuda")
+        scn.scn_cnn_forward(net, torch.from_numpy(th).cuda(), B, z,
+                            prev=torch.from_numpy(prev).cuda(), cur=torch.from_numpy(cur).cuda())
         assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
         t = ocnn.forward(rounded(params), oracle_x(th, prev, cur), rnd=ocnn.bf16_round)
         got = z.cpu().numpy().astype(np.float64)
-        assert np.all(np.isfinite(got))
+        assert np.all(np.isfinite(got[:B])) and np.isnan(got[B])  # nothing written past n
         scale = max(1.0, np.abs(t["z"]).max())
-        assert np.abs(got - t["z"]).max() <= 2e-2 * scale
-        # activations of the last chunk (pairs [B - m, B) with m = B - 128*floor((B-1)/128))
-        m = B - 128 * ((B - 1) // 128)
+        assert np.abs(got[:B] - t["z"]).max() <= 2e-2 * scale
+        # the bulk agrees far more closely than the bound (bf16 rounding flips are rare)
+        assert np.median(np.abs(got[:B] - t["z"])) <= 2e-3 * scale
+    finally:
+        scn.scn_cnn_destroy(net)
+
+
+@pytest.mark.parametrize("B", [1, 37, 300])
+def test_training_forward_activations_match_oracle(scn, B):
+    """The layered forward that training runs keeps a1, a2, a3 for the backward
+    pass; they match the oracle's bf16-rounded activations."""
+    params = he_params(B)
+    th, prev, cur = thumbs_and_pairs(B + 1, 64, B)
+    net = scn.scn_cnn_create(B)
+    try:
+        scn.scn_cnn_set_params(net, params)
+        y = torch.zeros(B, dtype=torch.float32, device="cuda")
+        scn.scn_cnn_gradients(net, torch.from_numpy(th).cuda(), y, B, 1.0,
+                              prev=torch.from_numpy(prev).cuda(), cur=torch.from_numpy(cur).cuda())
+        assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
+        t = ocnn.forward(rounded(params), oracle_x(th, prev, cur), rnd=ocnn.bf16_round)
         for layer, key, P, C in [(1, "a1", 576, 16), (2, "a2", 144, 32), (3, "a3", 40, 32)]:
             ptr = scn.scn_cnn_activation(net, layer)
-            nbytes = m * P * C * 2
+            nbytes = B * P * C * 2
             buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
             torch.cuda.synchronize()
             assert _cudart().cudaMemcpy(ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(ptr),
                                         ctypes.c_size_t(nbytes), 3) == 0  # device to device
-            a = buf.view(torch.bfloat16).float().cpu().numpy().reshape(m, P, C).astype(np.float64)
-            ref = t[key][B - m:].transpose(0, 2, 3, 1).reshape(m, P, C)
+            a = buf.view(torch.bfloat16).float().cpu().numpy().reshape(B, P, C).astype(np.float64)
+            ref = t[key].transpose(0, 2, 3, 1).reshape(B, P, C)
             err = np.abs(a - ref)
             tol = 2 ** -7 * np.abs(ref) + 1e-2 * max(1.0, np.abs(ref).max()) * 2 ** -7 * 8
             assert np.mean(err <= tol) > 0.999, (layer, err.max())
             assert err.max() <= 0.05 * max(1.0, np.abs(ref).max()), (layer, err.max())
+    finally:
+        scn.scn_cnn_destroy(net)
+
+
+def test_forward_rejects_misaligned_thumbnails(scn):
+    net = scn.scn_cnn_create(8)
+    try:
+        th = torch.zeros(3 * 2304 + 16, dtype=torch.uint8, device="cuda")
+        z = torch.empty(2, dtype=torch.float32, device="cuda")
+        with pytest.raises(scn.ScnError):
+            scn.scn_cnn_forward(net, th[1:], 2, z)
     finally:
         scn.scn_cnn_destroy(net)
 
