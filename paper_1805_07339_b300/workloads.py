@@ -69,3 +69,26 @@ def batched_spec(nvideos: int = 64, min_len: int = 200, max_len: int = 3000, see
         out.append(dict(video_id=1000 + v, width=W, height=H, num_frames=T, num_shots=max(1, T // 120),
                         sampling=kind, frames=idx.astype(np.int64)))
     return out
+
+
+# News-archive-shaped stream: many 640x360 videos of log-uniform length with
+# geometric shot lengths; each sampled at stride 24 plus a seeded 1% gather.
+STREAM = dict(width=640, height=360, nvideos=2000, min_len=1800, max_len=54000, stride=24, gather_percent=1)
+STREAM_SEED = 5
+STREAM_ID0 = 200000  # video ids of the stream (disjoint from every other workload)
+
+
+def stream_spec(nvideos: int = STREAM["nvideos"], seed: int = STREAM_SEED, min_len: int = STREAM["min_len"],
+                max_len: int = STREAM["max_len"], id0: int = STREAM_ID0) -> list[dict]:
+    """Per video: id, size, length (log-uniform in [min_len, max_len]), shot_mode 1
+    (geometric shot lengths), the stride-24 frames and a sorted seeded 1% gather."""
+    rng = np.random.default_rng(seed)
+    W, H, step = STREAM["width"], STREAM["height"], STREAM["stride"]
+    out = []
+    for v in range(nvideos):
+        T = int(round(float(np.exp(rng.uniform(np.log(min_len), np.log(max_len))))))
+        m = max(1, (T * STREAM["gather_percent"] + 50) // 100)
+        gather = np.sort(rng.choice(T, size=m, replace=False)).astype(np.int64)
+        out.append(dict(video_id=id0 + v, width=W, height=H, num_frames=T, shot_mode=1,
+                        stride=np.arange(0, T, step, dtype=np.int64), gather=gather))
+    return out
