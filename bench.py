@@ -333,6 +333,12 @@ def main():
                         "included; hist_*: device time of the batched hist+score plans"}
         del res
         torch.cuda.empty_cache()
+        if not args.no_proposal:
+            from paper_1805_07339_b300 import proposal as prop_mod
+            sp = prop_mod.run_stream_proposal(torch)
+            news["proposal"] = {"model": "trained on stride-24 pairs of 160 stream-shaped videos, tau on 40 more",
+                                **sp}
+            torch.cuda.empty_cache()
 
     prop = None
     if not args.no_proposal:

@@ -231,3 +231,81 @@ def run(torch, steps: int = 6000, batch: int = 256, lr: float = 1e-3, seed: int 
             scn.scn_cnn_destroy(fwd)
     finally:
         src.close()
+
+
+# ---------------------------------------------------------------------------
+# The news-archive stream: a second model for stride-24 pairs of 640x360 videos
+# ---------------------------------------------------------------------------
+# Pairs 24 frames apart see a drifted ramp and, with geometric shots of mean
+# length ~65, cross a boundary about a third of the time: a different input
+# distribution from consecutive 1080p frames, so the stream gets its own model,
+# trained and thresholded on stream-shaped videos with ids disjoint from the stream.
+STREAM_TRAIN = dict(nvideos=160, seed=21, id0=400000)
+STREAM_VAL = dict(nvideos=40, seed=22, id0=410000)
+
+
+def stream_pairs(torch, spec: list[dict], res):
+    """Concatenated thumbnails of every video's stride sequence and the (prev, cur,
+    label) of its consecutive stride pairs (label = exact flag of the later frame)."""
+    ths, prev, cur, lab = [], [], [], []
+    off = 0
+    for i in range(len(spec)):
+        th = res.thumbs[i]
+        n = th.shape[0]
+        ths.append(th)
+        k = torch.arange(1, n, device="cuda", dtype=torch.int32) + off
+        prev.append(k - 1)
+        cur.append(k)
+        lab.append(torch.from_numpy(res.stride[i][1][1:].astype(np.float32)))
+        off += n
+    return torch.cat(ths), torch.cat(prev), torch.cat(cur), torch.cat(lab).cuda()
+
+
+def run_stream_proposal(torch, eval_spec=None, steps: int = 3000, batch: int = 256, lr: float = 1e-3,
+                        seed: int = 0) -> dict:
+    """Train on stride-24 pairs of stream-shaped videos, pick tau on held-out ones, then
+    score every stride-24 pair of the stream and compare with the exact flags."""
+    from . import stream
+    from .workloads import stream_spec
+    tr_spec, va_spec = stream_spec(**STREAM_TRAIN), stream_spec(**STREAM_VAL)
+    ev_spec = eval_spec if eval_spec is not None else stream_spec()
+    net = scn.scn_cnn_create(batch)
+    fwd = scn.scn_cnn_create(8)
+    try:
+        tr = stream.run_stream(torch, tr_spec, thumbs=True)
+        th, pv, cu, lab = stream_pairs(torch, tr_spec, tr)
+        del tr
+        scn.scn_cnn_set_params(net, he_uniform(seed))
+        trn = train(torch, net, th, pv, cu, lab, steps=steps, batch=batch, lr=lr, seed=seed, log_every=0)
+        scn.scn_cnn_set_params(fwd, scn.scn_cnn_get_params(net))
+        n_train, pos_train = int(lab.numel()), int(lab.sum().item())
+        del th, pv, cu, lab
+        va = stream.run_stream(torch, va_spec, thumbs=True)
+        vth, vp, vc, vl = stream_pairs(torch, va_spec, va)
+        del va
+        tau = choose_tau(logits(torch, fwd, vth, vp, vc).cpu().numpy(), vl.cpu().numpy())
+        del vth, vp, vc, vl
+        ev = stream.run_stream(torch, ev_spec, thumbs=True)
+        eth, ep, ec, el = stream_pairs(torch, ev_spec, ev)
+        del ev
+        z = torch.empty(ep.numel(), dtype=torch.float32, device="cuda")
+        scn.scn_cnn_forward(fwd, eth, ep.numel(), z, prev=ep, cur=ec)  # warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        scn.scn_cnn_forward(fwd, eth, ep.numel(), z, prev=ep, cur=ec)
+        e1.record()
+        torch.cuda.synchronize()
+        if scn.scn_cnn_sync_status(fwd) != scn.SCN_OK:
+            raise RuntimeError("device status error in the proposal network")
+        p = (z.cpu().numpy() > tau)
+        y = el.cpu().numpy() > 0.5
+        tp = int((p & y).sum())
+        return {"pairs": int(y.size), "positives": int(y.sum()), "proposed": int(p.sum()),
+                "recall": tp / max(int(y.sum()), 1), "precision": tp / max(int(p.sum()), 1),
+                "proposed_fraction": float(p.mean()), "tau": tau, "forward_ms": e0.elapsed_time(e1),
+                "forward_pairs_per_s": y.size / (e0.elapsed_time(e1) / 1000),
+                "train_pairs": n_train, "train_positives": pos_train, "train_steps": trn["steps"],
+                "train_seconds": trn["seconds"]}
+    finally:
+        scn.scn_cnn_destroy(net)
+        scn.scn_cnn_destroy(fwd)

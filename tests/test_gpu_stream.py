@@ -75,3 +75,12 @@ def test_full_news_stream(scn, orc):
     # geometric shots (mean ~65 frames): about a third of the stride-24 pairs cross a boundary
     frac = np.mean(np.concatenate([res.stride[i][1][1:] for i in range(len(spec))]))
     assert 0.2 < frac < 0.45, frac
+
+
+def test_stream_proposal_model(scn):
+    """A model trained on stride-24 pairs of stream-shaped videos (disjoint ids)
+    finds the boundaries between sampled frames of the stream's first 100 videos."""
+    from paper_1805_07339_b300 import proposal
+    r = proposal.run_stream_proposal(torch, eval_spec=stream_spec(nvideos=100))
+    assert r["pairs"] > 50000 and 0.2 < r["positives"] / r["pairs"] < 0.45
+    assert r["recall"] >= 0.99 and r["precision"] >= 0.95, r
