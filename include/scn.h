@@ -299,6 +299,57 @@ scn_status scn_cnn_activation(const scn_cnn* c, int32_t layer, const void** d_pt
 scn_status scn_cnn_sync_status(scn_cnn* c, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Spacing and slicing (Sec. 3.2) and the per-shot montage (Sec. 5.2)       */
+/* ------------------------------------------------------------------------ */
+typedef enum {
+    SCN_FILL_VALUE = 0,    /* frames no element samples get the fill element */
+    SCN_FILL_REPEAT = 1    /* ... the output of the nearest earlier sampled frame (fill before the first) */
+} scn_fill_mode;
+
+/* Spacing, the inverse of the sampling op that made s (Sec. 3.2, "Sampling/
+ * spacing operations": fill elements align sequences sampled at different
+ * rates).  d_in: n = length(s) elements of elem_bytes bytes (1..1024), device,
+ * element k being the result for sampled frame k of s.  d_out: num_frames
+ * elements of the table (device): element t = the input element whose sampled
+ * frame is t (the last such element when s samples t more than once); frames
+ * that no element samples get h_fill (elem_bytes bytes, host; NULL = zero
+ * bytes) or, with SCN_FILL_REPEAT, the element of the nearest earlier sampled
+ * frame.  The first call on a sequence builds its sorted frame list on the
+ * device (synchronous); later calls are asynchronous on stream.  Errors:
+ * SCN_EINVAL (bad size or mode, NULL buffers), SCN_ERANGE (more than 2^31-1
+ * frames), SCN_ECUDA. */
+scn_status scn_space(scn_seq* s, const void* d_in, int32_t elem_bytes, int32_t fill_mode, const void* h_fill,
+                     void* d_out, void* stream);
+
+/* Slicing at boundaries (Sec. 3.2, "Slicing/unslicing operations": e.g. at
+ * shot boundaries, so that stencils and state do not cross shots): element k
+ * of an n-element sequence starts a slice when k == 0 or d_flag[k] != 0 (for
+ * instance the shot flags of scn_hist_scores).  d_start (device int32,
+ * capacity n) receives the first element of every slice in ascending order,
+ * d_count (device int64) the number of slices.  n = 0 writes count 0.
+ * Errors: SCN_EINVAL, SCN_ERANGE (n > 2^31-1). */
+scn_status scn_slice(const uint8_t* d_flag, int64_t n, int32_t* d_start, int64_t* d_count, void* stream);
+/* One representative element per slice (the film summaries of Sec. 5.2 show
+ * one frame per shot): d_mid[i] = (start[i] + end[i] - 1) / 2, end[i] =
+ * start[i+1] or n, for i < *d_count (read on the device). */
+scn_status scn_slice_middles(const int32_t* d_start, const int64_t* d_count, int64_t n, int32_t* d_mid, void* stream);
+/* Shot scores whose two-element stencil stops at slice boundaries: score[k]
+ * = 0 where a slice starts (k == 0 or d_boundary[k] != 0, device uint8 [n]),
+ * else as scn_shot_scores. */
+scn_status scn_shot_scores_sliced(const uint32_t* d_hist, int64_t n, int64_t pixel_count, const uint8_t* d_boundary,
+                                  uint32_t* d_score, uint8_t* d_flag, void* stream);
+/* Montage of sequence elements (Sec. 5.2, film summaries: one frame from each
+ * shot): tile i (row-major, `cols` tiles per row) shows element d_elem[i]
+ * (device int32, m entries) of s, nearest-neighbour downsampled to tile_w x
+ * tile_h (1..4096): tile pixel (x, y) = BT.601 fixed-point RGB (as scn_hist)
+ * of source pixel (floor((2x+1) W / (2 tile_w)), floor((2y+1) H / (2 tile_h))).
+ * d_out: uint8 [rows*tile_h][cols*tile_w][3], rows = ceil(m / cols), device;
+ * tiles past m, and tiles whose element is outside s, are black.  m = 0 writes
+ * nothing.  Errors: SCN_EINVAL, SCN_ERANGE (more than 2^34 output pixels). */
+scn_status scn_montage(const scn_seq* s, const int32_t* d_elem, int64_t m, int32_t cols, int32_t tile_w,
+                       int32_t tile_h, uint8_t* d_out, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Gated exact path: a gate proposes boundary candidates, only the frames of */
 /* proposed pairs go through the exact kernel, which remains the judge.      */
 /* ------------------------------------------------------------------------ */

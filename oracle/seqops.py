@@ -1,0 +1,87 @@
+"""Sequence operations of the oracle: spacing, slicing, slice representatives,
+sliced shot scores, montage.  TEST INFRASTRUCTURE ONLY (same rules as the
+package: only tests/, the smoke check and the bench's CPU legs use it).
+
+Definitions (Scanner, Poms et al. 2018):
+  * spacing inverts sampling: the sampled results go back to their frames and
+    the other frames receive "fill" elements (Sec. 3.2, sampling/spacing); the
+    fill is a given element, or (the repeat reading) the nearest earlier
+    sampled frame's result;
+  * slicing partitions a sequence at boundaries so that stencils and state do
+    not cross them (Sec. 3.2, slicing/unslicing); a boundary element starts a
+    slice, and so does element 0;
+  * a film summary shows one frame per shot (Sec. 5.2, montage); here the
+    middle element of each slice, nearest-neighbour downsampled into a tile.
+Pins: tests/test_oracle_seqops.py.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import scores as _scores
+from . import yuv_to_rgb_array
+
+
+def space(values: np.ndarray, frames, num_frames: int, repeat: bool = False, fill=None) -> np.ndarray:
+    """values: [n, ...] results of the sampled elements; frames: the frame each element sampled."""
+    values = np.asarray(values)
+    elem = values.shape[1:]
+    fill_v = np.zeros(elem, dtype=values.dtype) if fill is None else np.asarray(fill, dtype=values.dtype)
+    have = [None] * num_frames
+    for k, f in enumerate(frames):  # a later element sampling the same frame replaces an earlier one
+        have[int(f)] = k
+    out = np.empty((num_frames,) + elem, dtype=values.dtype)
+    last = None
+    for t in range(num_frames):
+        if have[t] is not None:
+            last = values[have[t]]
+            out[t] = last
+        elif repeat and last is not None:
+            out[t] = last
+        else:
+            out[t] = fill_v
+    return out
+
+
+def slice_starts(flags) -> np.ndarray:
+    """First element of every slice: k == 0 or flags[k] != 0, ascending."""
+    flags = np.asarray(flags)
+    return np.array([k for k in range(len(flags)) if k == 0 or flags[k] != 0], dtype=np.int64)
+
+
+def slice_middles(starts, n: int) -> np.ndarray:
+    ends = list(starts[1:]) + [n]
+    return np.array([(s + e - 1) // 2 for s, e in zip(starts, ends)], dtype=np.int64)
+
+
+def sliced_scores(hist: np.ndarray, boundary, pixel_count: int):
+    """Shot scores whose stencil stops at slice starts (score 0 there)."""
+    s, f = _scores(hist, pixel_count)
+    s = s.copy()
+    f = f.copy()
+    for k in range(len(s)):
+        if k == 0 or boundary[k] != 0:
+            s[k] = 0
+            f[k] = 0
+    return s, f
+
+
+def montage(frames: list, W: int, H: int, cols: int, tile_w: int, tile_h: int) -> np.ndarray:
+    """frames: NV12 frames of the tiles in order (None = a black tile)."""
+    m = len(frames)
+    rows = (m + cols - 1) // cols
+    out = np.zeros((rows * tile_h, cols * tile_w, 3), dtype=np.uint8)
+    xs = [((2 * x + 1) * W) // (2 * tile_w) for x in range(tile_w)]
+    ys = [((2 * y + 1) * H) // (2 * tile_h) for y in range(tile_h)]
+    for i, fr in enumerate(frames):
+        if fr is None:
+            continue
+        fr = np.asarray(fr, dtype=np.uint8)
+        yuv = np.empty((tile_h, tile_w, 3), dtype=np.uint8)
+        for ty, sy in enumerate(ys):
+            for tx, sx in enumerate(xs):
+                uv = W * H + (sy // 2) * W + (sx // 2) * 2
+                yuv[ty, tx] = (fr[sy * W + sx], fr[uv], fr[uv + 1])
+        r0, c0 = (i // cols) * tile_h, (i % cols) * tile_w
+        out[r0:r0 + tile_h, c0:c0 + tile_w] = yuv_to_rgb_array(yuv.reshape(-1, 3)).reshape(tile_h, tile_w, 3)
+    return out

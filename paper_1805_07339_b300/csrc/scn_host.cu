@@ -387,6 +387,7 @@ scn_status scn_seq_length(const scn_seq* s, int64_t* n) {
 scn_status scn_seq_destroy(scn_seq* s) {
     if (!s) return SCN_EINVAL;
     free_gate_workspace(s);
+    free_space_workspace(s);
     if (s->d_block) cudaFree(s->d_block);
     delete s;
     return SCN_OK;

@@ -74,6 +74,7 @@ struct scn_seq {
     int* d_status = nullptr;         // device status word
     uint32_t* d_queue = nullptr;     // work-queue counters (2 words, left zero)
     void* gate_ws = nullptr;         // gated-path workspace, made on first use
+    void* space_ws = nullptr;        // spacing workspace (sorted sampled frames), made on first use
     scn_tune tune{0, 0, 0};          // 0 fields: chosen per call
 };
 
@@ -148,4 +149,5 @@ Launch single_launch(const scn_table* t, int64_t n, const int32_t* slot, const H
 int device_sm_count();
 // Release a sequence's gated-path workspace (scn_proposal.cu).
 void free_gate_workspace(scn_seq* s);
+void free_space_workspace(scn_seq* s);
 }  // namespace scn

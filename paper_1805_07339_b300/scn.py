@@ -17,6 +17,7 @@ c_i32, c_i64, c_u64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, cty
 SCN_OK, SCN_EINVAL, SCN_ERANGE, SCN_ENOMEM, SCN_ECUDA, SCN_ETIMEOUT, SCN_EUNSUPPORTED = range(7)
 SCN_STRIDE, SCN_RANGE, SCN_GATHER, SCN_KEYFRAME = range(4)
 SCN_F32, SCN_BF16 = 0, 1
+SCN_FILL_VALUE, SCN_FILL_REPEAT = 0, 1
 
 
 class ScnError(RuntimeError):
@@ -104,6 +105,11 @@ SIGNATURES = [
     ("scn_thumb_diff", c_i32, [c_vp, c_i64, c_vp, c_vp]),
     ("scn_resize_norm", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_i32, c_vp, c_vp]),
     ("scn_thumbs", c_i32, [c_vp, c_vp, c_vp]),
+    ("scn_space", c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp]),
+    ("scn_slice", c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
+    ("scn_slice_middles", c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    ("scn_shot_scores_sliced", c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
+    ("scn_montage", c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_vp, c_vp]),
 ]
 
 
@@ -436,3 +442,32 @@ def scn_resize_norm(s: int, oh: int, ow: int, mean, std, dtype: int, out, stream
 
 def scn_thumbs(s: int, thumb, stream=None) -> None:
     _check(_lib.scn_thumbs(s, _ptr(thumb), _stream(stream)), "scn_thumbs")
+
+
+def scn_space(s: int, values, elem_bytes: int, out, fill_mode: int = SCN_FILL_VALUE, fill: bytes | None = None,
+              stream=None) -> None:
+    """values: CUDA tensor holding length(s) elements of elem_bytes bytes; out: CUDA tensor
+    holding num_frames elements of the table."""
+    buf = None
+    if fill is not None:
+        if len(fill) != elem_bytes:
+            raise ValueError("fill must be elem_bytes long")
+        buf = ctypes.create_string_buffer(bytes(fill), elem_bytes)
+    _check(_lib.scn_space(s, _ptr(values), elem_bytes, fill_mode, buf, _ptr(out), _stream(stream)), "scn_space")
+
+
+def scn_slice(flags, n: int, starts, count, stream=None) -> None:
+    _check(_lib.scn_slice(_ptr(flags), n, _ptr(starts), _ptr(count), _stream(stream)), "scn_slice")
+
+
+def scn_slice_middles(starts, count, n: int, mids, stream=None) -> None:
+    _check(_lib.scn_slice_middles(_ptr(starts), _ptr(count), n, _ptr(mids), _stream(stream)), "scn_slice_middles")
+
+
+def scn_shot_scores_sliced(hist, n: int, pixel_count: int, boundary, score, flag, stream=None) -> None:
+    _check(_lib.scn_shot_scores_sliced(_ptr(hist), n, pixel_count, _ptr(boundary), _ptr(score), _ptr(flag),
+                                       _stream(stream)), "scn_shot_scores_sliced")
+
+
+def scn_montage(s: int, elems, m: int, cols: int, tile_w: int, tile_h: int, out, stream=None) -> None:
+    _check(_lib.scn_montage(s, _ptr(elems), m, cols, tile_w, tile_h, _ptr(out), _stream(stream)), "scn_montage")

@@ -1,0 +1,157 @@
+"""Spacing, slicing, sliced scores and the per-shot montage on the GPU against
+the oracle's definitions (bit-exact)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import seqops  # noqa: E402
+from paper_1805_07339_b300.workloads import MASTER_SEED, TINY  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def scn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_07339_b300 import scn as s
+    return s
+
+
+@pytest.fixture(scope="module")
+def tiny(scn, orc):
+    W, H, T, S = TINY["width"], TINY["height"], TINY["num_frames"], TINY["num_shots"]
+    fb = W * H * 3 // 2
+    v = scn.scn_video_create(MASTER_SEED, 0, W, H, T, S)
+    buf = torch.empty(T * fb, dtype=torch.uint8, device="cuda")
+    scn.scn_generate(v, buf, 0, T, fb)
+    t = scn.scn_table_create(buf, W, H, T)
+    frames = orc.Video(MASTER_SEED, 0, W, H, T, S).frames(range(T), nthreads=8)
+    yield dict(scn=scn, buf=buf, table=t, W=W, H=H, T=T, frames=frames)
+    scn.scn_table_destroy(t)
+    scn.scn_video_destroy(v)
+
+
+def _hs(scn, seq, n):
+    h = torch.empty((n, 48), dtype=torch.int32, device="cuda")
+    s = torch.empty(n, dtype=torch.int32, device="cuda")
+    f = torch.empty(n, dtype=torch.uint8, device="cuda")
+    scn.scn_hist_scores(seq, h, s, f)
+    return h, s, f
+
+
+@pytest.mark.parametrize("kind", ["stride", "gather"])
+def test_space_matches_oracle(tiny, kind):
+    scn, T = tiny["scn"], tiny["T"]
+    if kind == "stride":
+        idx = np.arange(3, T, 24)
+        seq = scn.scn_sample(tiny["table"], scn.SCN_STRIDE, 3, T, 24)
+    else:  # unsorted, with repeats
+        rng = np.random.default_rng(7)
+        idx = rng.integers(0, T, 57)
+        seq = scn.scn_sample(tiny["table"], scn.SCN_GATHER, indices=idx.tolist())
+    try:
+        n = len(idx)
+        h, s, f = _hs(scn, seq, n)
+        for vals, eb, fill in ((h, 192, bytes(range(192))), (s, 4, b"\xff\xff\xff\x7f"), (f, 1, b"\x07")):
+            for mode in (scn.SCN_FILL_VALUE, scn.SCN_FILL_REPEAT):
+                out = torch.empty((T,) + tuple(vals.shape[1:]), dtype=vals.dtype, device="cuda")
+                scn.scn_space(seq, vals, eb, out, fill_mode=mode, fill=fill)
+                fill_v = np.frombuffer(fill, dtype=vals.cpu().numpy().dtype).reshape(vals.shape[1:])
+                ref = seqops.space(vals.cpu().numpy(), idx, T, repeat=mode == scn.SCN_FILL_REPEAT, fill=fill_v)
+                assert np.array_equal(out.cpu().numpy(), ref), (eb, mode)
+        # no fill given: zero bytes
+        out = torch.full((T,), -1, dtype=torch.int32, device="cuda")
+        scn.scn_space(seq, s, 4, out)
+        assert np.array_equal(out.cpu().numpy(), seqops.space(s.cpu().numpy(), idx, T))
+    finally:
+        scn.scn_seq_destroy(seq)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 1000, 8193, 1_300_000])
+def test_slice_matches_oracle(scn, n):
+    rng = np.random.default_rng(n)
+    flags = (rng.random(n) < 0.01).astype(np.uint8)
+    d_flags = torch.from_numpy(flags).cuda()
+    starts = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
+    count = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    scn.scn_slice(d_flags, n, starts, count)
+    m = int(count.item())
+    ref = np.flatnonzero(np.concatenate([[1], flags[1:]])) if n else np.zeros(0, np.int64)
+    if n <= 8193:
+        assert np.array_equal(ref, seqops.slice_starts(flags))
+    assert m == len(ref) and np.array_equal(starts.cpu().numpy()[:m], ref)
+    if n:
+        mids = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        scn.scn_slice_middles(starts, count, n, mids)
+        assert np.array_equal(mids.cpu().numpy()[:m], seqops.slice_middles(ref, n))
+        assert np.all(mids.cpu().numpy()[m:] == -1)  # nothing written past the slices
+
+
+def test_sliced_scores_match_oracle(scn):
+    rng = np.random.default_rng(9)
+    n, px = 3001, 320 * 180
+    hist = rng.integers(0, 4000, (n, 48)).astype(np.uint32)
+    b = (rng.random(n) < 0.05).astype(np.uint8)
+    s = torch.empty(n, dtype=torch.int32, device="cuda")
+    f = torch.empty(n, dtype=torch.uint8, device="cuda")
+    scn.scn_shot_scores_sliced(torch.from_numpy(hist.view(np.int32)).cuda(), n, px, torch.from_numpy(b).cuda(), s, f)
+    rs, rf = seqops.sliced_scores(hist, b, px)
+    assert np.array_equal(s.cpu().numpy().view(np.uint32), rs) and np.array_equal(f.cpu().numpy(), rf)
+
+
+def test_shot_montage_pipeline(tiny, orc):
+    """Detect shots, slice at them, take each slice's middle frame, lay the frames out as a montage."""
+    scn, W, H, T = tiny["scn"], tiny["W"], tiny["H"], tiny["T"]
+    seq = scn.scn_sample(tiny["table"], scn.SCN_STRIDE, 0, T, 1)
+    try:
+        _, _, f = _hs(scn, seq, T)
+        starts = torch.empty(T, dtype=torch.int32, device="cuda")
+        count = torch.empty(1, dtype=torch.int64, device="cuda")
+        scn.scn_slice(f, T, starts, count)
+        mids = torch.empty(T, dtype=torch.int32, device="cuda")
+        scn.scn_slice_middles(starts, count, T, mids)
+        m = int(count.item())
+        cols, tw, th = 4, 80, 45
+        rows = (m + cols - 1) // cols
+        out = torch.empty((rows * th, cols * tw, 3), dtype=torch.uint8, device="cuda")
+        scn.scn_montage(seq, mids, m, cols, tw, th, out)
+        # oracle pipeline on the oracle's own frames
+        h = orc.hist_batch(tiny["frames"], W, H, nthreads=8)
+        _, rf = orc.scores(h, W * H)
+        rst = seqops.slice_starts(rf)
+        rmid = seqops.slice_middles(rst, T)
+        assert m == len(rst) and m >= 4
+        ref = seqops.montage([tiny["frames"][k] for k in rmid], W, H, cols, tw, th)
+        assert np.array_equal(out.cpu().numpy(), ref)
+        # tiles whose element lies outside the sequence are black
+        bad = torch.tensor([0, T, -1], dtype=torch.int32, device="cuda")
+        out2 = torch.full((th, 3 * tw, 3), 9, dtype=torch.uint8, device="cuda")
+        scn.scn_montage(seq, bad, 3, 3, tw, th, out2)
+        o2 = out2.cpu().numpy()
+        assert np.array_equal(o2[:, :tw], seqops.montage([tiny["frames"][0]], W, H, 1, tw, th))
+        assert np.all(o2[:, tw:] == 0)
+    finally:
+        scn.scn_seq_destroy(seq)
+
+
+def test_montage_random_bytes_and_odd_tiles(scn, orc):
+    """Uniformly random NV12 (every clamp), tile sizes that do not divide the frame."""
+    from paper_1805_07339_b300.workloads import random_nv12
+    W, H = 64, 36
+    fr = random_nv12(31, 5, W, H)
+    buf = torch.from_numpy(fr.reshape(-1)).cuda()
+    t = scn.scn_table_create(buf, W, H, 5)
+    seq = scn.scn_sample(t, scn.SCN_STRIDE, 0, 5, 1)
+    try:
+        for tw, th, cols in ((64, 36, 2), (13, 7, 3), (100, 50, 5)):
+            el = torch.tensor([4, 0, 2, 1, 3], dtype=torch.int32, device="cuda")
+            rows = (5 + cols - 1) // cols
+            out = torch.empty((rows * th, cols * tw, 3), dtype=torch.uint8, device="cuda")
+            scn.scn_montage(seq, el, 5, cols, tw, th, out)
+            ref = seqops.montage([fr[k] for k in (4, 0, 2, 1, 3)], W, H, cols, tw, th)
+            assert np.array_equal(out.cpu().numpy(), ref), (tw, th)
+    finally:
+        scn.scn_seq_destroy(seq)
+        scn.scn_table_destroy(t)
