@@ -79,6 +79,7 @@ struct Net {
     __nv_bfloat16* w3t;     // [288][32]
     __nv_bfloat16* f1b;     // [64][32]
     __nv_bfloat16* f2b;     // [64]
+    float* f1t;             // [32][64]  F1 as used by the forward (BF16 values), transposed
     // activations of the last batch (device)
     __nv_bfloat16 *a1, *a2, *a3;   // NHWC
     float *g, *v, *z;              // head
@@ -277,7 +278,8 @@ __global__ void __launch_bounds__(256) head_fwd(const __nv_bfloat16* __restrict_
 // fp32 master -> BF16 operand layouts
 // ---------------------------------------------------------------------------
 __global__ void prep_weights(const float* m, __nv_bfloat16* w1b, __nv_bfloat16* w2b, __nv_bfloat16* w3b,
-                             __nv_bfloat16* w2t, __nv_bfloat16* w3t, __nv_bfloat16* f1b, __nv_bfloat16* f2b) {
+                             __nv_bfloat16* w2t, __nv_bfloat16* w3t, __nv_bfloat16* f1b, __nv_bfloat16* f2b,
+                             float* f1t) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     // conv weights W[co][ci][di][dj] -> [co][tap*CIN + ci]
     if (i < 16 * 32) {
@@ -300,6 +302,7 @@ __global__ void prep_weights(const float* m, __nv_bfloat16* w1b, __nv_bfloat16* 
     }
     if (i < 64 * 32) f1b[i] = __float2bfloat16_rn(m[kF1 + i]);
     if (i < 64) f2b[i] = __float2bfloat16_rn(m[kF2 + i]);
+    if (i < 64 * 32) f1t[(i % 32) * 64 + i / 32] = __bfloat162float(__float2bfloat16_rn(m[kF1 + i]));
 }
 
 template <int L>
@@ -403,9 +406,9 @@ constexpr int kFzE3Pitch = 8 * 16, kFzO3Pitch = 9 * 16;
 constexpr int kFzE3Plane = kFzA2Rows * kFzE3Pitch, kFzO3Plane = kFzA2Rows * kFzO3Pitch;
 constexpr int kFzA2Bytes = 4 * (kFzE3Plane + kFzO3Plane);
 constexpr int kFzG3 = kFzPairs * 5;
-// head scratch in region 0 after a2 (phases 2-4): F1 transposed (fp32 [32][64]), pooled g, hidden v
-constexpr int kFzF1T = 24576;
-constexpr int kFzGs = kFzF1T + 32 * 64 * 4;
+// head scratch in region 0 after a2 (phases 2-4): pooled g, hidden v
+constexpr int kFzF1T = 24576;  // end of what layer-3 reads of region 0
+constexpr int kFzGs = kFzF1T;
 constexpr int kFzVs = kFzGs + kFzPairs * 32 * 4;
 // MMA descriptor table: conv1 2 per tile, conv2 9 per tile, conv3 18
 constexpr int kFzD1 = 0, kFzD2 = kFzD1 + 2 * kFzT1, kFzD3 = kFzD2 + 4 * 9, kFzNDesc = kFzD3 + 18;
@@ -422,9 +425,10 @@ constexpr int kFzReg0Bytes = 2 * kFzX1Plane;
 constexpr int kFzReg1 = kFzReg0 + kFzReg0Bytes;    // A1, later a3 (fp32) over its first plane
 constexpr int kFzReg1Bytes = 2 * kFzE2Plane + 2 * kFzO2Plane;
 constexpr int kFzSmem = kFzReg1 + kFzReg1Bytes;
-constexpr int kFzG3Bytes = kFzPairs * 40 * 32 * 4;
+constexpr int kFzA3Pitch = 41;  // a3 as [pair][channel][position], odd pitch: conflict-free pooling
+constexpr int kFzG3Bytes = kFzPairs * 32 * kFzA3Pitch * 4;
 static_assert(kFzNBar * 8 + 4 <= 256, "barrier area");
-static_assert(kFzG3Bytes <= kFzE2Plane - kFzE2Pitch, "a3 overlays the first a1 plane except its last row");
+static_assert(kFzG3Bytes <= kFzE2Plane, "a3 overlays the first a1 plane");
 static_assert(kFzSmem <= 115712, "two CTAs per SM");
 static_assert(kFzG1 >= 16 && kFzG2 >= 16, "every layer-1/2 tile lies inside the buffers");
 // every row the MMAs read lies inside its plane (layers 1, 2) or inside region 0 (layer 3)
@@ -444,6 +448,7 @@ struct FusedArgs {
     const float* master;       // fp32 parameters (biases)
     const __nv_bfloat16* f1b;
     const __nv_bfloat16* f2b;
+    const float* f1t;          // [32][64] fp32 (BF16 values), transposed F1
     float* logits;
     int* status;
 };
@@ -460,36 +465,6 @@ __device__ __forceinline__ float thumb_at(const uint32_t (&w)[8]) {
 __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-// entry i of a 32-column block: [prev, cur] at block columns 2i-1, 2i, 2i+1, zeros
-template <int I>
-__device__ __forceinline__ void x1_entry(uint8_t* row, const uint32_t (&p)[8], const uint32_t (&q)[8], uint32_t w0) {
-    if constexpr (I > 0) w0 = bf16x2(thumb_at<2 * I - 1>(p), thumb_at<2 * I - 1>(q));
-    const uint32_t w1 = bf16x2(thumb_at<2 * I>(p), thumb_at<2 * I>(q));
-    const uint32_t w2 = bf16x2(thumb_at<2 * I + 1>(p), thumb_at<2 * I + 1>(q));
-    *reinterpret_cast<uint4*>(row + I * 16) = make_uint4(w0, w1, w2, 0u);
-}
-
-// 16 layer-1 input entries of one input row (32 columns from column 32 hh) of one
-// pair; w0 = the entry-0 word for column 32 hh - 1 (zero padding when hh = 0)
-__device__ __forceinline__ void x1_entries(uint8_t* row, const uint32_t (&p)[8], const uint32_t (&q)[8], uint32_t w0) {
-    x1_entry<0>(row, p, q, w0);
-    x1_entry<1>(row, p, q, 0);
-    x1_entry<2>(row, p, q, 0);
-    x1_entry<3>(row, p, q, 0);
-    x1_entry<4>(row, p, q, 0);
-    x1_entry<5>(row, p, q, 0);
-    x1_entry<6>(row, p, q, 0);
-    x1_entry<7>(row, p, q, 0);
-    x1_entry<8>(row, p, q, 0);
-    x1_entry<9>(row, p, q, 0);
-    x1_entry<10>(row, p, q, 0);
-    x1_entry<11>(row, p, q, 0);
-    x1_entry<12>(row, p, q, 0);
-    x1_entry<13>(row, p, q, 0);
-    x1_entry<14>(row, p, q, 0);
-    x1_entry<15>(row, p, q, 0);
 }
 
 __device__ __forceinline__ bool fz_wait(uint64_t* bar, uint32_t par, bool ok, int* status) {
@@ -524,7 +499,6 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
     uint8_t* E1 = reg0 + kFzX1Plane;
     uint8_t* E3 = reg0;
     uint8_t* O3 = reg0 + 4 * kFzE3Plane;
-    float* f1t = reinterpret_cast<float*>(reg0 + kFzF1T);
     float* gs = reinterpret_cast<float*>(reg0 + kFzGs);
     float* vs = reinterpret_cast<float*>(reg0 + kFzVs);
     uint8_t* E2 = reg1;
@@ -609,52 +583,69 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
     const uint32_t tlane = static_cast<uint32_t>(32 * quad) << 16;
     bool ok = true;
 
-    // phase-0 build task of this thread: pair p, input row iy, 32-column block hh
-    const int bp_ = tid / 72, biy = (tid >> 1) % 36, bhh = tid & 1;
-    const bool builder = tid < kFzPairs * 72;
+    // thumbnail indices of the batch's two pairs (every thread keeps them; fetched a batch ahead)
     const int64_t nbatch = (a.pairs + kFzPairs - 1) / kFzPairs;
-    auto pair_thumbs = [&](int64_t batch, int64_t& ip, int64_t& ic) {
-        int64_t b = batch * kFzPairs + bp_;
+    auto pair_thumbs = [&](int64_t batch, int p, int64_t& ip, int64_t& ic) {
+        int64_t b = batch * kFzPairs + p;
         if (b >= a.pairs) b = a.pairs - 1;
         ip = a.prev ? a.prev[b] : b;
         ic = a.cur ? a.cur[b] : b + 1;
     };
-    int64_t ip = 0, ic = 0;
-    if (builder && blockIdx.x < nbatch) pair_thumbs(blockIdx.x, ip, ic);
+    int64_t ip0 = 0, ic0 = 0, ip1 = 0, ic1 = 0;
+    if (blockIdx.x < nbatch) {
+        pair_thumbs(blockIdx.x, 0, ip0, ic0);
+        pair_thumbs(blockIdx.x, 1, ip1, ic1);
+    }
     uint32_t it = 0;
     for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x, ++it) {
         const uint32_t par = it & 1u;
-        // ---- phase 0: layer-1 input planes; zero rows; zero rows of the first A1 plane that a3 overwrote
-        if (builder) {
-            const uint8_t* tp = a.thumbs + ip * 2304 + biy * 64 + 32 * bhh;
-            const uint8_t* tq = a.thumbs + ic * 2304 + biy * 64 + 32 * bhh;
-            const uint4 p0 = __ldg(reinterpret_cast<const uint4*>(tp));
-            const uint4 p1 = __ldg(reinterpret_cast<const uint4*>(tp + 16));
-            const uint4 q0 = __ldg(reinterpret_cast<const uint4*>(tq));
-            const uint4 q1 = __ldg(reinterpret_cast<const uint4*>(tq + 16));
-            const uint32_t before_p = bhh ? __ldg(tp - 1) : 0u, before_q = bhh ? __ldg(tq - 1) : 0u;
-            const uint32_t pw[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-            const uint32_t qw[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-            uint8_t* row = (biy & 1) ? O1 + (bp_ * kFzR1 + ((biy + 1) >> 1)) * 512 : E1 + (bp_ * kFzR1 + (biy >> 1)) * 512;
-            const float bpf = fmaf(static_cast<float>(before_p), 1.f / 64.f, -2.f);
-            const float bqf = fmaf(static_cast<float>(before_q), 1.f / 64.f, -2.f);
-            x1_entries(row + 16 * 16 * bhh, pw, qw, bhh ? bf16x2(bpf, bqf) : 0u);  // entries 16 hh ..
-        } else {
-            for (int z = tid - kFzPairs * 72; z < 6 * 32 + kFzPairs * 16; z += kFzThreads - kFzPairs * 72) {
-                uint8_t* dst;
-                if (z < 6 * 32) {  // zero rows: O1 {0, 19, 38}, E1 {18, 37, 38}
-                    const int which = z >> 5, ox = z & 31;
-                    const int zr = which == 0 ? 0 : which == 1 ? kFzR1 : which == 2 ? 2 * kFzR1
-                                 : which == 3 ? kFzR1 - 1 : which == 4 ? 2 * kFzR1 - 1 : 2 * kFzR1;
-                    dst = (which < 3 ? O1 : E1) + zr * 512 + ox * 16;
-                } else {
-                    const int y = z - 6 * 32;
-                    dst = E2 + ((y >> 4) * kFzR2) * kFzE2Pitch + (y & 15) * 16;
-                }
-                *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+        // ---- phase 0: layer-1 input planes, one warp per input row of a pair (lane = output
+        //      column, so each store writes one contiguous 512-byte plane row); zero rows;
+        //      zero rows of the first A1 plane that a3 overwrote
+        constexpr int kRowsPerWarp = kFzPairs * 36 / (kFzThreads / 32);
+        static_assert(kRowsPerWarp * (kFzThreads / 32) == kFzPairs * 36, "rows split evenly over warps");
+        uint32_t vps[kRowsPerWarp], vqs[kRowsPerWarp];
+#pragma unroll
+        for (int q = 0; q < kRowsPerWarp; ++q) {  // every load in flight before the first store
+            const int task = warp + q * (kFzThreads / 32), p = task / 36, iy = task - 36 * p;
+            const int64_t ip = p ? ip1 : ip0, ic = p ? ic1 : ic0;
+            // bytes 2 lane, 2 lane + 1 of the row; column 2 lane - 1 comes from the lane below
+            vps[q] = __ldg(reinterpret_cast<const uint16_t*>(a.thumbs + ip * 2304 + iy * 64) + lane);
+            vqs[q] = __ldg(reinterpret_cast<const uint16_t*>(a.thumbs + ic * 2304 + iy * 64) + lane);
+        }
+#pragma unroll
+        for (int q = 0; q < kRowsPerWarp; ++q) {
+            const int task = warp + q * (kFzThreads / 32), p = task / 36, iy = task - 36 * p;
+            const uint32_t vp = vps[q], vq = vqs[q];
+            const uint32_t up = __shfl_up_sync(0xffffffffu, vp, 1), uq = __shfl_up_sync(0xffffffffu, vq, 1);
+            const uint32_t w[8] = {vp, vq, up, uq, 0, 0, 0, 0};
+            // w as bytes: 0,1 = prev cols 2l, 2l+1; 4,5 = cur; 9 = prev col 2l-1; 13 = cur col 2l-1
+            const uint32_t w0 = lane ? bf16x2(thumb_at<9>(w), thumb_at<13>(w)) : 0u;  // column -1 is padding
+            const uint32_t w1 = bf16x2(thumb_at<0>(w), thumb_at<4>(w));
+            const uint32_t w2 = bf16x2(thumb_at<1>(w), thumb_at<5>(w));
+            uint8_t* row = (iy & 1) ? O1 + (p * kFzR1 + ((iy + 1) >> 1)) * 512 : E1 + (p * kFzR1 + (iy >> 1)) * 512;
+            *reinterpret_cast<uint4*>(row + lane * 16) = make_uint4(w0, w1, w2, 0u);
+        }
+        for (int z = tid; z < 6 * 32 + kFzPairs * 16; z += kFzThreads) {
+            uint8_t* dst;
+            if (z < 6 * 32) {  // zero rows: O1 {0, 19, 38}, E1 {18, 37, 38}
+                const int which = z >> 5, ox = z & 31;
+                const int zr = which == 0 ? 0 : which == 1 ? kFzR1 : which == 2 ? 2 * kFzR1
+                             : which == 3 ? kFzR1 - 1 : which == 4 ? 2 * kFzR1 - 1 : 2 * kFzR1;
+                dst = (which < 3 ? O1 : E1) + zr * 512 + ox * 16;
+            } else {
+                const int y = z - 6 * 32;
+                dst = E2 + ((y >> 4) * kFzR2) * kFzE2Pitch + (y & 15) * 16;
             }
+            *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
         }
         fz_sync();
+
+        // the next batch's thumbnail indices: loads in flight through phases 1-4
+        if (batch + gridDim.x < nbatch) {
+            pair_thumbs(batch + gridDim.x, 0, ip0, ic0);
+            pair_thumbs(batch + gridDim.x, 1, ip1, ic1);
+        }
 
         // ---- phase 1: conv1, kFzT1 tiles of 128 x 16, issued by lane 0 of warp t % 8 (one
         //      issuing thread is slower: each MMA waits for the tensor core to take it)
@@ -667,18 +658,19 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
             }
         }
         __syncwarp();
-        for (int t2 = half; t2 < kFzT1; t2 += 4) {
-            // tiles t2 and t2 + 2 of this warp's parity: both TMEM loads in flight at once
-            const bool two = t2 + 2 < kFzT1;
-            ok = fz_wait(bar + t2, par, ok, a.status);
-            if (two) ok = fz_wait(bar + t2 + 2, par, ok, a.status);
-            uint32_t accs[2][16];
+        for (int t2 = half; t2 < kFzT1; t2 += 6) {
+            // up to three tiles of this warp's parity per TMEM round trip (each tcgen05.ld
+            // round trip costs hundreds of cycles; loads in flight together share it)
+            const int nt = min(3, (kFzT1 - t2 + 1) / 2);
+            for (int u = 0; u < nt; ++u) ok = fz_wait(bar + t2 + 2 * u, par, ok, a.status);
+            uint32_t accs[3][16];
             tc::ld16(tmem + tlane + 16 * t2, accs[0]);
-            if (two) tc::ld16(tmem + tlane + 16 * (t2 + 2), accs[1]);
+            if (nt > 1) tc::ld16(tmem + tlane + 16 * (t2 + 2), accs[1]);
+            if (nt > 2) tc::ld16(tmem + tlane + 16 * (t2 + 4), accs[2]);
             tc::wait_ld();
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-            if (u == 1 && !two) break;
+            for (int u = 0; u < 3; ++u) {
+            if (u >= nt) break;
             const int t = t2 + 2 * u;
             const uint32_t (&acc)[16] = accs[u];
             const int g0 = min(16 * t, kFzG1 - 16);
@@ -703,8 +695,7 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
 
         // ---- phase 2: conv2, 2 column halves x 2 tiles of 128 x 32; each tile accumulates
         //      taps 0-4 and taps 5-8 in two TMEM blocks, issued by lane 0 of 8 warps (short
-        //      chains: each MMA waits for the tensor core to take it); zero padding of A2;
-        //      F1 transposed into region 0 for the head
+        //      chains: each MMA waits for the tensor core to take it); zero padding of A2
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
             const int tt = warp >> 1, k = warp & 1, t0 = 5 * k, t1 = k ? 9 : 5;
@@ -726,14 +717,6 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
             }
             *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
         }
-        {
-            const int j = tid >> 2, c0 = (tid & 3) * 8;  // F1 row j, columns c0..c0+7
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.f1b + j * 32 + c0));
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                f1t[(c0 + q) * 64 + j] = __uint_as_float((q & 1) ? (w[q >> 1] & 0xFFFF0000u) : (w[q >> 1] << 16));
-        }
         for (int tt = half; tt < 4; tt += 2) {
             ok = fz_wait(bar + kFzT1 + 2 * tt, par, ok, a.status);
             ok = fz_wait(bar + kFzT1 + 2 * tt + 1, par, ok, a.status);
@@ -744,12 +727,17 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
             const int row = p * kFzR3 + oy + 1;
             uint8_t* dst = (ox & 1) ? O3 + row * kFzO3Pitch + ((ox + 1) >> 1) * 16 : E3 + row * kFzE3Pitch + (ox >> 1) * 16;
             const int cs = (ox & 1) ? kFzO3Plane : kFzE3Plane;
+            // the tile's 64 accumulator columns (two tap ranges x 32 channels) in one round trip
+            uint32_t us[4][16];
+            tc::ld16(tmem + tlane + 64 * tt, us[0]);
+            tc::ld16(tmem + tlane + 64 * tt + 32, us[1]);
+            tc::ld16(tmem + tlane + 64 * tt + 16, us[2]);
+            tc::ld16(tmem + tlane + 64 * tt + 48, us[3]);
+            tc::wait_ld();
 #pragma unroll
             for (int c0 = 0; c0 < 32; c0 += 16) {
-                uint32_t u0[16], u1[16];
-                tc::ld16(tmem + tlane + 64 * tt + c0, u0);
-                tc::ld16(tmem + tlane + 64 * tt + 32 + c0, u1);
-                tc::wait_ld();
+                const uint32_t (&u0)[16] = us[c0 / 8];
+                const uint32_t (&u1)[16] = us[c0 / 8 + 1];
                 if (live) {
                     uint32_t o[8];
 #pragma unroll
@@ -792,18 +780,14 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
             }
             const int g = r >> 3;
             if (g < kFzG3) {
+                // [pair][channel][position]: the lanes of one store write consecutive positions
                 const int p = g / 5, oy = g - 5 * p, pos = oy * 8 + (r & 7);
-                float* dst = a3 + (p * 40 + pos) * 32 + 16 * half;
+                float* dst = a3 + (p * 32 + 16 * half) * kFzA3Pitch + pos;
                 const float* b3 = bias + 48 + 16 * half;
 #pragma unroll
-                for (int c = 0; c < 16; c += 4) {
-                    float4 v;
-                    v.x = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c]) + b3[c], 0.f)));
-                    v.y = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c + 1]) + b3[c + 1], 0.f)));
-                    v.z = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c + 2]) + b3[c + 2], 0.f)));
-                    v.w = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c + 3]) + b3[c + 3], 0.f)));
-                    *reinterpret_cast<float4*>(dst + c) = v;
-                }
+                for (int c = 0; c < 16; ++c)
+                    dst[c * kFzA3Pitch] =
+                        __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c]) + b3[c], 0.f)));
             }
         }
         tc::fence_before_sync();
@@ -813,12 +797,10 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
         // ---- phase 4: pooling (thread per pair and channel), FC 32->64 (thread per pair and
         //      unit), FC 64->1 (warp per pair); the next batch's pair indices are fetched meanwhile
         if (tid < kFzPairs * 32) {
-            const float* src = a3 + (tid >> 5) * 40 * 32 + (tid & 31);
+            const float* src = a3 + tid * kFzA3Pitch;  // pair tid / 32, channel tid % 32
             float s = 0.f;
-            for (int pos = 0; pos < 40; ++pos) s += src[pos * 32];
+            for (int pos = 0; pos < 40; ++pos) s += src[pos];
             gs[tid] = s * (1.f / 40.f);
-        } else if (builder && batch + gridDim.x < nbatch) {
-            pair_thumbs(batch + gridDim.x, ip, ic);
         }
         __syncthreads();
         if (tid < kFzPairs * 64) {
@@ -826,10 +808,9 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
             const float* g = gs + p * 32;
             float v = bias[80 + j];
 #pragma unroll 8
-            for (int c = 0; c < 32; ++c) v = fmaf(f1t[c * 64 + j], g[c], v);
+            for (int c = 0; c < 32; ++c) v = fmaf(__ldg(a.f1t + c * 64 + j), g[c], v);
             vs[tid] = v;
         }
-        if (tid < kFzPairs * 32 && builder && batch + gridDim.x < nbatch) pair_thumbs(batch + gridDim.x, ip, ic);
         __syncthreads();
         if (warp < kFzPairs) {
             const int64_t b = batch * kFzPairs + warp;
@@ -870,6 +851,7 @@ scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* pr
     a.master = n->master;
     a.f1b = n->f1b;
     a.f2b = n->f2b;
+    a.f1t = n->f1t;
     a.logits = logits;
     a.status = n->status;
     const int64_t nbatch = (pairs + kFzPairs - 1) / kFzPairs;
@@ -1285,7 +1267,7 @@ scn_status gradients(Net* n, const uint8_t* thumbs, const int32_t* prev, const i
 
 scn_status prep(Net* n, cudaStream_t st) {
     prep_weights<<<(32 * 288 + 255) / 256, 256, 0, st>>>(n->master, n->w1b, n->w2b, n->w3b, n->w2t, n->w3t, n->f1b,
-                                                         n->f2b);
+                                                         n->f2b, n->f1t);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }
@@ -1321,7 +1303,7 @@ scn_status scn_cnn_create(int64_t max_batch, scn_cnn** out) {
         {reinterpret_cast<void**>(&n.w1b), 16 * 32 * 2},    {reinterpret_cast<void**>(&n.w2b), 32 * 144 * 2},
         {reinterpret_cast<void**>(&n.w3b), 32 * 288 * 2},   {reinterpret_cast<void**>(&n.w2t), 144 * 32 * 2},
         {reinterpret_cast<void**>(&n.w3t), 288 * 32 * 2},   {reinterpret_cast<void**>(&n.f1b), 64 * 32 * 2},
-        {reinterpret_cast<void**>(&n.f2b), 64 * 2},
+        {reinterpret_cast<void**>(&n.f2b), 64 * 2},    {reinterpret_cast<void**>(&n.f1t), 32 * 64 * 4},
         {reinterpret_cast<void**>(&n.a1), size_t(B) * 576 * 16 * 2},
         {reinterpret_cast<void**>(&n.a2), size_t(B) * 144 * 32 * 2},
         {reinterpret_cast<void**>(&n.a3), size_t(B) * 40 * 32 * 2},
