@@ -405,6 +405,11 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
     const uint32_t stages = ptx::smem_u32(s.stages);
     uint32_t it = 0;
     int rot = 0;
+    // geometry of the current job, kept in registers: reloaded only when a chunk
+    // belongs to another job (global loads at every chunk start stall all warps)
+    int cur_job = -1, W = 0, wv = 1, sc = 0, crows = 0;
+    uint32_t dY = 0, dU = 0;
+    float inv_wv = 1.f;
     for (;; ++it) {
         const uint32_t st = it % kStages;
         // Every consumer reaches the same chunk before any of them gives up, so
@@ -417,15 +422,24 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
         const ChunkMeta m = s.meta[st];
         if (m.job < 0) break;
         const Job& J = job_of(L, m.job);
-        const int W = J.W, wv = J.wv, sc = J.sc;
+        if (m.job != cur_job) {
+            cur_job = m.job;
+            W = J.W;
+            wv = J.wv;
+            sc = J.sc;
+            crows = J.chunk_rows;
+            dY = J.dY;
+            dU = J.dU;
+            inv_wv = J.inv_wv;
+        }
         const uint32_t ybase = stages + st * L.stage_bytes;
         const int units = (m.rows / 2) * wv;
         int u = ctid - rot;
         if (u < 0) u += kNT;
-        const int p0 = static_cast<int>((static_cast<float>(u) + 0.5f) * J.inv_wv);
+        const int p0 = static_cast<int>((static_cast<float>(u) + 0.5f) * inv_wv);
         int c = u - p0 * wv;
         uint32_t ya = ybase + p0 * 2 * W + c * 16;
-        uint32_t ua = ybase + J.chunk_rows * W + p0 * W + c * 16;
+        uint32_t ua = ybase + crows * W + p0 * W + c * 16;
         for (; u < units; u += kNT) {
             const uint4 y0 = lds128(ya);
             const uint4 y1 = lds128(ya + W);
@@ -433,8 +447,8 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
             count_unit(lanereg, inc, cR, cG, cB, y0, y1, uv);
             // next unit: kNT units on; a column wrap adds one more row pair and
             // removes a row of columns (luma +2W-W, chroma +W-W)
-            ya += J.dY;
-            ua += J.dU;
+            ya += dY;
+            ua += dU;
             c += sc;
             if (c >= wv) {
                 c -= wv;
