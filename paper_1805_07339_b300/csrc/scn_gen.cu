@@ -14,12 +14,49 @@
 namespace scn {
 namespace {
 
-__device__ __forceinline__ uint64_t sm64(uint64_t s, uint64_t i) {
-    uint64_t v = s + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+// SplitMix64 finaliser of a counter value c = s + (i+1) * kGolden
+__device__ __forceinline__ uint64_t sm_mix(uint64_t v) {
     v = (v ^ (v >> 30)) * 0xBF58476D1CE4E5B9ull;
     v = (v ^ (v >> 27)) * 0x94D049BB133111EBull;
     return v ^ (v >> 31);
 }
+
+// noise of the sample whose first counter value is c (= s_pix + (2q+1) kGolden; the
+// second draw's counter is c + kGolden)
+__device__ __forceinline__ int noise_from_counter(uint64_t c) {
+    const uint64_t w0 = sm_mix(c);
+    const uint64_t w1 = sm_mix(c + kGolden);
+    unsigned sum = __dp4a(static_cast<unsigned>(w0), 0x01010101u, 0u);
+    sum = __dp4a(static_cast<unsigned>(w0 >> 32), 0x01010101u, sum);
+    sum = __dp4a(static_cast<unsigned>(w1), 0x01010101u, sum);
+    return (static_cast<int>(sum) - 1514) >> 5;  // arithmetic shift = floor division by 32
+}
+
+// floor(n / W) kept as quotient and remainder while n steps by d (W > 0)
+struct FloorStep {
+    int q, r;
+    __device__ __forceinline__ void init(int n, int W) {
+        q = n / W;
+        r = n - q * W;
+        if (r < 0) {
+            r += W;
+            --q;
+        }
+    }
+    __device__ __forceinline__ void step(int d, int W) {
+        r += d;
+        while (r >= W) {
+            r -= W;
+            ++q;
+        }
+        while (r < 0) {
+            r += W;
+            --q;
+        }
+    }
+};
 
 __device__ __forceinline__ int floordiv_pos(int a, int b) {
     // b > 0
@@ -27,14 +64,6 @@ __device__ __forceinline__ int floordiv_pos(int a, int b) {
     return (a % b != 0 && a < 0) ? q - 1 : q;
 }
 
-__device__ __forceinline__ int noise_at(uint64_t s_pix, uint64_t q) {
-    const uint64_t w0 = sm64(s_pix, 2 * q);
-    const uint64_t w1 = sm64(s_pix, 2 * q + 1);
-    unsigned sum = __dp4a(static_cast<unsigned>(w0), 0x01010101u, 0u);
-    sum = __dp4a(static_cast<unsigned>(w0 >> 32), 0x01010101u, sum);
-    sum = __dp4a(static_cast<unsigned>(w1), 0x01010101u, sum);
-    return (static_cast<int>(sum) - 1514) >> 5;  // arithmetic shift = floor division by 32
-}
 
 struct GenArgs {
     const scn_shot* shots;
@@ -72,29 +101,47 @@ __global__ void __launch_bounds__(256) gen_kernel(GenArgs a) {
         const scn_shot* sh = shot_of(a.shots, a.nshots, f);
         const int dt = static_cast<int>(f - sh->start);
         uint8_t b[16];
+        // Along a row the sample index q steps by 1, so the counter s_pix + (2q+1) kGolden
+        // steps by 2 kGolden, and floor(gx (x - dt) / W) is kept as quotient and remainder.
         if (row < a.H) {
             const int y = row;
-            const int ramp_y = floordiv_pos(sh->gy[0] * y, a.H);
-            const uint64_t qrow = (static_cast<uint64_t>(f) * 3 * a.H + y) * a.W;
+            const int x0 = vec * 16;
+            const int base = sh->base[0] + floordiv_pos(sh->gy[0] * y, a.H);
+            const uint64_t q0 = (static_cast<uint64_t>(f) * 3 * a.H + y) * a.W + x0;
+            uint64_t c = a.s_pix + (2 * q0 + 1) * kGolden;
+            FloorStep rx;
+            rx.init(sh->gx[0] * (x0 - dt), a.W);
+            const int gx = sh->gx[0];
 #pragma unroll 4
             for (int i = 0; i < 16; ++i) {
-                const int x = vec * 16 + i;
-                int v = sh->base[0] + floordiv_pos(sh->gx[0] * (x - dt), a.W) + ramp_y +
-                        noise_at(a.s_pix, qrow + x);
+                const int v = base + rx.q + noise_from_counter(c);
                 b[i] = static_cast<uint8_t>(min(max(v, 16), 235));
+                c += 2 * kGolden;
+                rx.step(gx, a.W);
             }
         } else {
             const int cy = row - a.H;
             const int Wc = a.W / 2, Hc = a.H / 2;
+            const int cx0 = vec * 8;
+            uint64_t c[2];
+            FloorStep rx[2];
+            int base[2], gx2[2];
+#pragma unroll
+            for (int pl = 1; pl <= 2; ++pl) {
+                const uint64_t q0 = ((static_cast<uint64_t>(f) * 3 + pl) * Hc + cy) * Wc + cx0;
+                c[pl - 1] = a.s_pix + (2 * q0 + 1) * kGolden;
+                rx[pl - 1].init(sh->gx[pl] * (2 * cx0 - dt), a.W);
+                base[pl - 1] = sh->base[pl] + floordiv_pos(sh->gy[pl] * (2 * cy), a.H);
+                gx2[pl - 1] = 2 * sh->gx[pl];
+            }
 #pragma unroll 2
             for (int j = 0; j < 8; ++j) {
-                const int cx = vec * 8 + j;
 #pragma unroll
-                for (int pl = 1; pl <= 2; ++pl) {
-                    const uint64_t q = ((static_cast<uint64_t>(f) * 3 + pl) * Hc + cy) * Wc + cx;
-                    int v = sh->base[pl] + floordiv_pos(sh->gx[pl] * (2 * cx - dt), a.W) +
-                            floordiv_pos(sh->gy[pl] * (2 * cy), a.H) + noise_at(a.s_pix, q);
-                    b[2 * j + pl - 1] = static_cast<uint8_t>(min(max(v, 16), 240));
+                for (int pl = 0; pl < 2; ++pl) {
+                    const int v = base[pl] + rx[pl].q + noise_from_counter(c[pl]);
+                    b[2 * j + pl] = static_cast<uint8_t>(min(max(v, 16), 240));
+                    c[pl] += 2 * kGolden;
+                    rx[pl].step(gx2[pl], a.W);
                 }
             }
         }
