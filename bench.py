@@ -165,6 +165,35 @@ class OracleSample:
         return self.nframes * reps / tot, reps, tot
 
 
+def host_info() -> dict:
+    """CPU model, logical cores and RAM of the machine the CPU legs run on."""
+    model, mem = "unknown", None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemTotal"):
+                    mem = round(int(ln.split()[1]) / 1024 / 1024, 1)
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "logical_cores": os.cpu_count(), "ram_GiB": mem}
+
+
+# The paper's own HIST throughput (Sec. 5.1.2-5.1.3), for context only: it includes H.264 decode of
+# a 202,525-frame 1080p film and unstated bins, on other hardware; frames/s = 202,525 / time.
+PAPER_CONTEXT = [
+    {"what": "HIST, one machine", "frames_per_s": 785, "hardware": "GCE, 32 vCPUs", "includes": "H.264 decode"},
+    {"what": "HIST, one GPU", "frames_per_s": 225, "hardware": "1x NVIDIA K80 (GCE)", "includes": "H.264 decode"},
+    {"what": "HIST, scaled out", "frames_per_s": 10100, "hardware": "2,400 cores (GCE)", "includes": "H.264 decode"},
+    {"what": "HIST, scaled out", "frames_per_s": 6530, "hardware": "75x K80 (GCE)", "includes": "H.264 decode"},
+]
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -184,7 +213,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": "1080p NV12 video, 7200 frames, 60 shots; hist+score (CPU oracle sample)",
                    "frames_per_step": nframes},
-        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": ncores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": ncores, "kind": "oracle", "sample": sample,
+                         "host": host_info()},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -360,8 +390,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ncores = os.cpu_count() or 1
         fps, reps, secs = OracleSample(32, ncores).rate(budget_s=10.0)
+        fps1, reps1, secs1 = OracleSample(4, 1).rate(budget_s=4.0)
         cpu = {"value": fps, "unit": "frames/s", "cores": ncores, "kind": "oracle",
-               "sample": f"hist+score of 32 1080p frames of the workload, {reps} passes, {secs:.1f} s"}
+               "sample": f"hist+score of 32 1080p frames of the workload, {reps} passes, {secs:.1f} s",
+               "single_thread": {"value": fps1, "unit": "frames/s",
+                                 "sample": f"4 frames, {reps1} passes, {secs1:.1f} s"},
+               "host": host_info()}
 
     for m in seqs:
         if scn.scn_seq_sync_status(seqs[m]) != scn.SCN_OK:
@@ -378,7 +412,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_GB_per_s": frames_per_step * ALG_BYTES_PER_FRAME / (ms_step / 1000) / 1e9,
             "kernels": kern, "roofline": roofline, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
-            "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "stream": news, "proposal": prop,
+            "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "stream": news, "proposal": prop, "paper_context": PAPER_CONTEXT,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
