@@ -377,6 +377,12 @@ typedef enum { SCN_F32 = 0, SCN_BF16 = 1 } scn_dtype;
  * in dtype.  mean/std are host arrays of 3. */
 scn_status scn_resize_norm(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean, const float* h_std,
                            int32_t dtype, void* d_out, void* stream);
+/* The same resize and normalisation written once as FP32 (d_out_f32) and once
+ * as BF16 (d_out_bf16, the RNE of each FP32 value), from one pass over the
+ * source rows: the two layouts of the two scn_resize_norm calls, for half the
+ * reads.  Both outputs [n][3][oh][ow], device, 4- and 2-byte aligned. */
+scn_status scn_resize_norm_both(scn_seq* s, int32_t out_h, int32_t out_w, const float* h_mean, const float* h_std,
+                                float* d_out_f32, void* d_out_bf16, void* stream);
 /* Luma thumbnails: d_thumb[k][r][c] = Y[s*r][s*c], s = W/64 = H/36
  * (requires W == 64*s and H == 36*s); output uint8 [n][36][64]. */
 scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream);

@@ -27,8 +27,8 @@ struct ResizeArgs {
     float scale[3], bias[3];  // out = v * scale + bias, scale = 1/(255 std), bias = -mean/std
     float inv255;
     float mean[3], istd[3];
-    void* out;
-    int bf16;
+    float* out32;            // [n][3][oh][ow] FP32, or null
+    __nv_bfloat16* out16;    // [n][3][oh][ow] BF16 (RNE of the FP32 value), or null
 };
 
 __device__ __forceinline__ void src_coord(int o, int S, int O, int& i0, int& i1, float& l) {
@@ -76,11 +76,8 @@ __global__ void __launch_bounds__(256) resize_kernel(ResizeArgs a) {
             const float v = (1.f - ly) * top + ly * bot;
             const float o = (v * a.inv255 - a.mean[c]) * a.istd[c];
             const int64_t idx = (static_cast<int64_t>(k) * 3 + c) * npix + i;
-            if (a.bf16) {
-                reinterpret_cast<__nv_bfloat16*>(a.out)[idx] = __float2bfloat16_rn(o);
-            } else {
-                reinterpret_cast<float*>(a.out)[idx] = o;
-            }
+            if (a.out32) a.out32[idx] = o;
+            if (a.out16) a.out16[idx] = __float2bfloat16_rn(o);
         }
     }
 }
@@ -98,20 +95,18 @@ __global__ void __launch_bounds__(256) thumbs_kernel(const uint8_t* nv12, int64_
 }  // namespace
 }  // namespace scn
 
-extern "C" {
 
-scn_status scn_resize_norm(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean, const float* h_std, int32_t dtype,
-                           void* d_out, void* stream) {
-    if (!s || !h_mean || !h_std || !d_out || oh < 1 || ow < 1) return SCN_EINVAL;
-    if (dtype != SCN_F32 && dtype != SCN_BF16) return SCN_EINVAL;
-    const uintptr_t al = dtype == SCN_F32 ? 3u : 1u;
-    if (reinterpret_cast<uintptr_t>(d_out) & al) return SCN_EINVAL;
+
+namespace scn {
+namespace {
+scn_status launch_resize(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean, const float* h_std, float* out32,
+                         __nv_bfloat16* out16, void* stream) {
     if (oh > 16384 || ow > 16384) return SCN_ERANGE;  // keeps (2o+1)*S in int32
     for (int c = 0; c < 3; ++c)
         if (!(h_std[c] != 0.f)) return SCN_EINVAL;
     if (s->n == 0) return SCN_OK;
     if (s->n > 65535) return SCN_ERANGE;  // one grid row per element
-    scn::ResizeArgs a;
+    ResizeArgs a;
     a.nv12 = s->table->d_nv12;
     a.stride = s->table->frame_stride;
     a.W = s->table->W;
@@ -124,14 +119,36 @@ scn_status scn_resize_norm(scn_seq* s, int32_t oh, int32_t ow, const float* h_me
         a.mean[c] = h_mean[c];
         a.istd[c] = 1.f / h_std[c];
     }
-    a.out = d_out;
-    a.bf16 = dtype == SCN_BF16;
+    a.out32 = out32;
+    a.out16 = out16;
     const int npix = oh * ow;
     const int bx = std::min((npix + 255) / 256, 1024);
     dim3 grid(bx, static_cast<unsigned>(s->n));
-    scn::resize_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    resize_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(a);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
+}
+}  // namespace
+}  // namespace scn
+
+extern "C" {
+
+scn_status scn_resize_norm(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean, const float* h_std, int32_t dtype,
+                           void* d_out, void* stream) {
+    if (!s || !h_mean || !h_std || !d_out || oh < 1 || ow < 1) return SCN_EINVAL;
+    if (dtype != SCN_F32 && dtype != SCN_BF16) return SCN_EINVAL;
+    const uintptr_t al = dtype == SCN_F32 ? 3u : 1u;
+    if (reinterpret_cast<uintptr_t>(d_out) & al) return SCN_EINVAL;
+    return scn::launch_resize(s, oh, ow, h_mean, h_std, dtype == SCN_F32 ? static_cast<float*>(d_out) : nullptr,
+                              dtype == SCN_BF16 ? static_cast<__nv_bfloat16*>(d_out) : nullptr, stream);
+}
+
+scn_status scn_resize_norm_both(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean, const float* h_std,
+                                float* d_out_f32, void* d_out_bf16, void* stream) {
+    if (!s || !h_mean || !h_std || !d_out_f32 || !d_out_bf16 || oh < 1 || ow < 1) return SCN_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_out_f32) & 3u) || (reinterpret_cast<uintptr_t>(d_out_bf16) & 1u))
+        return SCN_EINVAL;
+    return scn::launch_resize(s, oh, ow, h_mean, h_std, d_out_f32, static_cast<__nv_bfloat16*>(d_out_bf16), stream);
 }
 
 scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream) {

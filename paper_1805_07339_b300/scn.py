@@ -105,6 +105,7 @@ SIGNATURES = [
     ("scn_thumb_diff", c_i32, [c_vp, c_i64, c_vp, c_vp]),
     ("scn_resize_norm", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_i32, c_vp, c_vp]),
     ("scn_thumbs", c_i32, [c_vp, c_vp, c_vp]),
+    ("scn_resize_norm_both", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_vp, c_vp, c_vp]),
     ("scn_space", c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp]),
     ("scn_slice", c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
     ("scn_slice_middles", c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
@@ -438,6 +439,13 @@ def scn_resize_norm(s: int, oh: int, ow: int, mean, std, dtype: int, out, stream
     m = (ctypes.c_float * 3)(*[float(x) for x in mean])
     sd = (ctypes.c_float * 3)(*[float(x) for x in std])
     _check(_lib.scn_resize_norm(s, oh, ow, m, sd, dtype, _ptr(out), _stream(stream)), "scn_resize_norm")
+
+
+def scn_resize_norm_both(s: int, oh: int, ow: int, mean, std, out_f32, out_bf16, stream=None) -> None:
+    m = (ctypes.c_float * 3)(*[float(x) for x in mean])
+    sd = (ctypes.c_float * 3)(*[float(x) for x in std])
+    _check(_lib.scn_resize_norm_both(s, oh, ow, m, sd, _ptr(out_f32), _ptr(out_bf16), _stream(stream)),
+           "scn_resize_norm_both")
 
 
 def scn_thumbs(s: int, thumb, stream=None) -> None:

@@ -315,6 +315,33 @@ def test_resize_norm_parity(scn, orc, W, H, oh, ow, n):
         dev.close()
 
 
+@pytest.mark.parametrize("W,H,oh,ow,n", [(320, 180, 224, 224, 3), (1920, 1080, 224, 224, 2), (64, 36, 7, 300, 2)])
+def test_resize_norm_both_equals_single_calls(scn, orc, W, H, oh, ow, n):
+    """One pass writing FP32 and BF16 gives exactly the two single-precision calls, and the FP32
+    values stay within tolerance of the fp64 oracle."""
+    frames = random_nv12(W + 7 * oh, n, W, H)
+    dev = Dev(scn, torch.from_numpy(frames.reshape(-1)).cuda(), W, H, n)
+    try:
+        seq = dev.seq(scn.SCN_GATHER, indices=list(range(n))[::-1])
+        a32 = torch.empty((n, 3, oh, ow), dtype=torch.float32, device="cuda")
+        a16 = torch.empty((n, 3, oh, ow), dtype=torch.bfloat16, device="cuda")
+        b32 = torch.full((n, 3, oh, ow), float("nan"), dtype=torch.float32, device="cuda")
+        b16 = torch.full((n, 3, oh, ow), float("nan"), dtype=torch.bfloat16, device="cuda")
+        scn.scn_resize_norm(seq, oh, ow, MEAN, STD, scn.SCN_F32, a32)
+        scn.scn_resize_norm(seq, oh, ow, MEAN, STD, scn.SCN_BF16, a16)
+        scn.scn_resize_norm_both(seq, oh, ow, MEAN, STD, b32, b16)
+        assert torch.equal(a32, b32) and torch.equal(a16.view(torch.int16), b16.view(torch.int16))
+        ref = orc.resize_norm_frame(frames[n - 1], W, H, oh, ow, MEAN, STD)
+        assert np.abs(b32[0].cpu().numpy() - ref).max() <= RESIZE_TOL
+        # a BF16 output one byte off its alignment is rejected before any launch
+        odd = torch.empty(b16.numel() * 2 + 2, dtype=torch.uint8, device="cuda")[1:]
+        with pytest.raises(scn.ScnError):
+            scn.scn_resize_norm_both(seq, oh, ow, MEAN, STD, b32, odd)
+        scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+
+
 def test_resize_generator_frames_tiny(scn, orc):
     W, H, T = TINY["width"], TINY["height"], TINY["num_frames"]
     v = _video(scn, TINY)
