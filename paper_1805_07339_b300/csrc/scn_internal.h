@@ -28,16 +28,16 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 constexpr int kStatusTimeout = 1;
 
 // Histogram kernel geometry (fixed at compile time).
-constexpr int kConsumerWarps = 16;                        // warps that convert + count
-constexpr int kHistThreads = (kConsumerWarps + 1) * 32;  // + one producer warp (bulk copies)
-constexpr int kStages = 2;                                // staged chunks in flight (2 x ~30 KB measured best)
+constexpr int kConsumerWarps = 20;                        // warps that load, convert + count
+constexpr int kHistThreads = (kConsumerWarps + 1) * 32;  // + one producer warp (work descriptors)
+constexpr int kStages = 2;                                // chunk descriptors in flight
 constexpr int kGroupWarps = 4;                            // warps sharing one table region
 constexpr int kRegions = kConsumerWarps / kGroupWarps;
 constexpr int kTabRowsPerRegion = 136;                    // 45 (R) + 39 (G) + 52 (B) extended bins
 constexpr int kTabBytes = kRegions * kTabRowsPerRegion * 256;
 constexpr int kSmemLimit = 232448;                        // 227 KB opt-in per CTA
 constexpr int kSmemMisc = 1024;                           // accumulators + barriers + flags
-constexpr int kStageBudget = (kSmemLimit - kTabBytes - kSmemMisc) / kStages;
+static_assert(kTabBytes + kSmemMisc <= kSmemLimit, "tables fit in shared memory");
 constexpr int kConsumerThreads = kConsumerWarps * 32;
 // Pixels of one work item at most: the table is flushed after every item, and
 // this keeps every 16-bit lane counter below 2^16 (each of the 512 consumer
@@ -115,12 +115,11 @@ struct Launch {
     int64_t rp_per_cta;    // > 0: no queue; CTA b takes row pairs [b*rp_per_cta, (b+1)*rp_per_cta) of job0
     uint32_t* queue;       // [0..1] next item (64-bit), [2] CTAs done with the queue; left zero
     int* status;           // device status word
-    int stage_bytes;       // bytes per stage (>= chunk_rows * W * 3/2 of every job)
     int grid;
 };
 
-// Luma rows per chunk for width W (largest even count that fits a stage), or
-// the requested count when it is smaller.
+// Luma rows per work descriptor: the requested even count, or (0) the whole
+// frame, so that a descriptor covers a whole item or segment.
 int chunk_rows_for(int W, int H, int requested);
 // Fill the derived consumer constants of a job (wv, sp, sc, dY, dU, inv_wv).
 void fill_job_consts(Job& j);
@@ -134,12 +133,11 @@ scn_status prepare_hist();
 
 // Launch shape resolved for a sequence.
 struct HistShape {
-    int chunk_rows;      // luma rows per staged chunk (even)
+    int chunk_rows;      // luma rows per work descriptor (even)
     int grid;            // CTAs
     int item_rp;         // row pairs per work item
     int items_per_frame;
     int64_t rp_per_cta;  // > 0: contiguous row-pair range per CTA instead of the queue
-    int stage_bytes;     // bytes per stage buffer
     size_t smem;
 };
 HistShape resolve_hist_shape(const scn_seq* s);

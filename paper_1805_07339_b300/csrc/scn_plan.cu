@@ -25,7 +25,6 @@ struct scn_plan {
     scn_tune tune{0, 0, 0};
     std::vector<scn::Job> jobs;     // host copy of the device job array
     int64_t n_items = 0;
-    int stage_bytes = 0;
     int grid = 0;
     void* d_block = nullptr;        // status + queue
     scn::Job* d_jobs = nullptr;
@@ -49,7 +48,6 @@ scn_status build_items(scn_plan* p) {
     for (scn_seq* s : p->seqs) total_frames += s->n;
     // too few items for the CTAs: split frames further
     int64_t px_target = item_px;
-    int max_stage = 0;
     for (size_t j = 0; j < p->seqs.size(); ++j) {
         const scn_seq* s = p->seqs[j];
         Job& J = p->jobs[j];
@@ -67,7 +65,6 @@ scn_status build_items(scn_plan* p) {
         J.H = s->table->H;
         J.chunk_rows = chunk_rows_for(J.W, J.H, p->tune.chunk_rows);
         fill_job_consts(J);
-        max_stage = std::max(max_stage, ((J.chunk_rows * J.W * 3 / 2) + 127) & ~127);
     }
     for (int pass = 0; pass < 8; ++pass) {
         int64_t items = 0;
@@ -102,7 +99,6 @@ scn_status build_items(scn_plan* p) {
             }
         }
     }
-    p->stage_bytes = max_stage;
     p->grid = static_cast<int>(std::min<int64_t>(grid_req, std::max<int64_t>(p->n_items, 1)));
     // device copies (synchronous: plans are built once, then run many times)
     if (p->items_cap < p->n_items) {
@@ -129,7 +125,6 @@ Launch plan_launch(const scn_plan* p) {
     L.n_items = p->n_items;
     L.queue = reinterpret_cast<uint32_t*>(static_cast<char*>(p->d_block) + 64);
     L.status = static_cast<int*>(p->d_block);
-    L.stage_bytes = p->stage_bytes;
     L.grid = p->grid;
     return L;
 }
