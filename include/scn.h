@@ -356,9 +356,11 @@ scn_status scn_montage(const scn_seq* s, const int32_t* d_elem, int64_t m, int32
 /* d_gate[k] (device float, k >= 1) scores pair (k-1, k) of the sequence; pair
  * k is proposed when d_gate[k] > tau (d_gate[0] is ignored).  Writes
  * d_proposed[k] (0/1); d_score / d_flag get the exact score and flag of every
- * proposed pair and 0 elsewhere.  Synchronises the stream once (the number of
- * proposals is read back; *h_nproposed receives it when not NULL).  The
- * sequence's gated workspace is allocated on the first call. */
+ * proposed pair and 0 elsewhere.  The number of proposals stays on the device
+ * (every launch reads it there), so with h_nproposed NULL the call is fully
+ * asynchronous on stream; when h_nproposed is not NULL the call waits for the
+ * stream at its end and writes the number there.  The sequence's gated
+ * workspace is allocated on the first call (synchronous). */
 scn_status scn_gated_hist_scores(scn_seq* s, const float* d_gate, float tau, uint8_t* d_proposed, uint32_t* d_score,
                                  uint8_t* d_flag, int64_t* h_nproposed, void* stream);
 /* The learned proposal path: thumbnails of the sequence into d_thumbs

@@ -101,6 +101,11 @@ static_assert(kStages * sizeof(ChunkMeta) + 64 * 4 + 2 * kStages * 8 + 16 <= kSm
 
 __device__ __forceinline__ const Job& job_of(const Launch& L, int j) { return L.jobs ? L.jobs[j] : L.job0; }
 
+// elements of job0 when its count lives on the device
+__device__ __forceinline__ int64_t device_elems(const Launch& L) {
+    return L.d_count ? static_cast<int64_t>(L.count_mul) * static_cast<int64_t>(*L.d_count) : L.job0.n;
+}
+
 __device__ __forceinline__ void fail(const Launch& L, const Smem& s) {
     *reinterpret_cast<volatile int*>(s.abort_flag) = 1;
     atomicOr(L.status, kStatusTimeout);
@@ -151,13 +156,15 @@ __device__ __forceinline__ bool stage_chunk(const Launch& L, const Smem& s, uint
 
 __device__ void produce(const Launch& L, const Smem& s) {
     uint32_t it = 0;
-    if (L.rp_per_cta > 0) {
+    if (L.rp_per_cta != 0) {
         // Contiguous split of job0's row pairs: every CTA does the same work and
         // flushes only at frame edges or every item_rp row pairs (16-bit bound).
         const Job& J = L.job0;
         const int hp = J.H / 2, crp = J.chunk_rows / 2, srp = J.item_rp;
-        int64_t g = blockIdx.x * L.rp_per_cta;
-        const int64_t g_end = min(g + L.rp_per_cta, J.n * hp);
+        const int64_t total_rp = device_elems(L) * hp;
+        const int64_t rpc = L.rp_per_cta > 0 ? L.rp_per_cta : (total_rp + gridDim.x - 1) / gridDim.x;
+        int64_t g = blockIdx.x * rpc;
+        const int64_t g_end = min(g + rpc, total_rp);
         int64_t k = g / hp;
         int rp = static_cast<int>(g - k * hp);
         int seg = 0;
@@ -178,9 +185,10 @@ __device__ void produce(const Launch& L, const Smem& s) {
             }
         }
     } else {
+        const int64_t n_items = L.d_count ? device_elems(L) * L.job0.items_per_frame : L.n_items;
         while (!aborted(s)) {
             const uint64_t i = atomicAdd(reinterpret_cast<unsigned long long*>(L.queue), 1ull);
-            if (i >= static_cast<uint64_t>(L.n_items)) break;
+            if (i >= static_cast<uint64_t>(n_items)) break;
             const Item item = item_at(L, static_cast<int64_t>(i));
             const Job& J = job_of(L, item.job);
             const int r_end = 2 * (item.rp0 + item.nrp);
@@ -317,7 +325,7 @@ __device__ __forceinline__ void write_score(const Job& J, int64_t k, uint32_t h0
 
 // One warp, after the flush: publish an item's counts of element k (seg_rp
 // row pairs), complete the frame and the scores it unblocks.
-__device__ void publish(const Job& J, int64_t k, int seg_rp, uint32_t* acc, int lane) {
+__device__ void publish(const Job& J, int64_t n, int64_t k, int seg_rp, uint32_t* acc, int lane) {
     uint32_t h0 = acc[lane];
     uint32_t h1 = lane < 16 ? acc[32 + lane] : 0u;
     acc[lane] = 0;
@@ -361,7 +369,7 @@ __device__ void publish(const Job& J, int64_t k, int seg_rp, uint32_t* acc, int 
             if (lane == 0) J.pair[k] = 0;
         }
     }
-    if (k + 1 < J.n) {
+    if (k + 1 < n) {
         uint32_t old = 0;
         if (lane == 0) old = atomicAdd(&J.pair[k + 1], 1u);
         old = __shfl_sync(0xffffffffu, old, 0);
@@ -378,6 +386,7 @@ __device__ __forceinline__ uint4 ldg128(const uint8_t* p) { return __ldg(reinter
 
 __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
     const int ctid = warp * 32 + lane;
+    const int64_t n_dev = device_elems(L);
     const int region = warp / kGroupWarps;
     const uint32_t lanereg = static_cast<uint32_t>(lane * 4 + (warp & 1) * 128);
     const uint32_t inc = (warp & 2) ? 65536u : 1u;
@@ -460,7 +469,7 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
             ptx::named_bar_sync(1, kNT);  // every consumer has counted the item
             flush_table(s.tab, s.acc, ctid);
             ptx::named_bar_sync(1, kNT);  // table zeroed, acc complete
-            if (warp == 0) publish(J, m.k, m.seg_rp, s.acc, lane);
+            if (warp == 0) publish(J, L.d_count ? n_dev : J.n, m.k, m.seg_rp, s.acc, lane);
         }
     }
 }

@@ -112,10 +112,16 @@ struct Launch {
     const Job* jobs;       // device array of jobs (batched plans), null: job0 only
     const Item* items;     // device array of items (batched plans), null: implicit items of job0
     int64_t n_items;
-    int64_t rp_per_cta;    // > 0: no queue; CTA b takes row pairs [b*rp_per_cta, (b+1)*rp_per_cta) of job0
+    int64_t rp_per_cta;    // > 0: no queue; CTA b takes row pairs [b*rp_per_cta, (b+1)*rp_per_cta) of job0;
+                           // < 0: the same split, computed on the device from d_count over gridDim.x CTAs
     uint32_t* queue;       // [0..1] next item (64-bit), [2] CTAs done with the queue; left zero
     int* status;           // device status word
     int grid;
+    // optional device-side element count of job0 (single-sequence launches):
+    // when set, job0 has count_mul * (*d_count) elements and n_items is only an
+    // upper bound; the count is read by the kernel, so the host need not wait for it
+    const int32_t* d_count = nullptr;
+    int32_t count_mul = 0;
 };
 
 // Luma rows per work descriptor: the requested even count, or (0) the whole

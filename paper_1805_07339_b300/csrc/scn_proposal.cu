@@ -46,18 +46,20 @@ __global__ void propose_kernel(const float* gate, int64_t n, float tau, uint8_t*
     }
 }
 
-__global__ void pair_slots(const int32_t* list, int64_t m, const int32_t* slot, int32_t* slots2) {
+// the proposal count m is read on the device (*count), so no host round trip sits
+// between the gate and the exact pass
+__global__ void pair_slots(const int32_t* list, const int* count, const int32_t* slot, int32_t* slots2) {
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= m) return;
+    if (i >= *count) return;
     const int32_t k = list[i];
     slots2[2 * i] = slot[k - 1];
     slots2[2 * i + 1] = slot[k];
 }
 
-__global__ void scatter_scores(const int32_t* list, int64_t m, const uint32_t* score2, const uint8_t* flag2,
+__global__ void scatter_scores(const int32_t* list, const int* count, const uint32_t* score2, const uint8_t* flag2,
                                uint32_t* score, uint8_t* flag) {
     const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= m) return;
+    if (i >= *count) return;
     const int32_t k = list[i];
     score[k] = score2[2 * i + 1];
     flag[k] = flag2[2 * i + 1];
@@ -166,20 +168,28 @@ scn_status scn_gated_hist_scores(scn_seq* s, const float* d_gate, float tau, uin
     propose_kernel<<<static_cast<unsigned>(blocks), 256, 0, cs>>>(d_gate, s->n, tau, d_proposed, ws->list, ws->count,
                                                                   d_score, d_flag);
     SCN_CUDA_TRY(cudaGetLastError());
-    int m = 0;
-    SCN_CUDA_TRY(cudaMemcpyAsync(&m, ws->count, sizeof(int), cudaMemcpyDeviceToHost, cs));
-    SCN_CUDA_TRY(cudaStreamSynchronize(cs));
-    if (h_nproposed) *h_nproposed = m;
-    if (m == 0) return SCN_OK;
-    pair_slots<<<(m + 255) / 256, 256, 0, cs>>>(ws->list, m, s->d_slot, ws->slots2);
+    // m = *ws->count stays on the device: every later launch is sized for the
+    // largest m (n - 1 pairs) and reads m itself
+    const int64_t cap = s->n;
+    const unsigned pblocks = static_cast<unsigned>((cap + 255) / 256);
+    pair_slots<<<pblocks, 256, 0, cs>>>(ws->list, ws->count, s->d_slot, ws->slots2);
     SCN_CUDA_TRY(cudaGetLastError());
-    // the exact kernel over the 2m frames of the proposed pairs
+    // the exact kernel over the 2m frames of the proposed pairs: one contiguous
+    // range of row pairs per CTA, each CTA computing its range from m on the device
     scn_seq q;
     q.table = s->table;
-    q.n = 2 * static_cast<int64_t>(m);
+    q.n = 2 * cap;
     q.tune = s->tune;
-    const HistShape sh = resolve_hist_shape(&q);
+    HistShape sh = resolve_hist_shape(&q);
+    const int W = s->table->W, H = s->table->H;
+    int sms = device_sm_count();
+    if (sms <= 0) sms = 148;
+    sh.grid = s->tune.grid > 0 ? s->tune.grid : sms;
+    sh.rp_per_cta = -1;
+    sh.item_rp = static_cast<int>(std::min<int64_t>(H / 2, std::max<int64_t>(1, kItemPixelsMax / (2LL * W))));
     Launch L = single_launch(s->table, q.n, ws->slots2, sh);
+    L.d_count = ws->count;
+    L.count_mul = 2;
     L.job0.hist = ws->hist2;
     L.job0.score = ws->score2;
     L.job0.flag = ws->flag2;
@@ -190,8 +200,14 @@ scn_status scn_gated_hist_scores(scn_seq* s, const float* d_gate, float tau, uin
     L.status = s->d_status;
     st = launch_hist(L, cs);
     if (st != SCN_OK) return st;
-    scatter_scores<<<(m + 255) / 256, 256, 0, cs>>>(ws->list, m, ws->score2, ws->flag2, d_score, d_flag);
+    scatter_scores<<<pblocks, 256, 0, cs>>>(ws->list, ws->count, ws->score2, ws->flag2, d_score, d_flag);
     SCN_CUDA_TRY(cudaGetLastError());
+    if (h_nproposed) {  // the only host wait, at the end and only when asked for
+        int m = 0;
+        SCN_CUDA_TRY(cudaMemcpyAsync(&m, ws->count, sizeof(int), cudaMemcpyDeviceToHost, cs));
+        SCN_CUDA_TRY(cudaStreamSynchronize(cs));
+        *h_nproposed = m;
+    }
     return SCN_OK;
 }
 

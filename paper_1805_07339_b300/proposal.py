@@ -175,11 +175,11 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
             a.record()
             for _ in range(reps):
                 if gate == "learned":
-                    scn.scn_proposal_hist_scores(src.seq, net, tau, thumbs, zl, prop, sc, fl)
+                    scn.scn_proposal_hist_scores(src.seq, net, tau, thumbs, zl, prop, sc, fl, count=False)
                 else:
                     src.thumbs(thumbs)
                     scn.scn_thumb_diff(thumbs, T, diff)
-                    scn.scn_gated_hist_scores(src.seq, diff, tau_diff, prop, sc, fl)
+                    scn.scn_gated_hist_scores(src.seq, diff, tau_diff, prop, sc, fl, count=False)
             b.record()
             torch.cuda.synchronize()
             tot["t_" + gate] += a.elapsed_time(b) / reps

@@ -417,18 +417,23 @@ def scn_cnn_sync_status(c: int, stream=None) -> int:
     return int(_lib.scn_cnn_sync_status(c, _stream(stream)))
 
 
-def scn_gated_hist_scores(s: int, gate, tau: float, proposed, score, flag, stream=None) -> int:
+def scn_gated_hist_scores(s: int, gate, tau: float, proposed, score, flag, stream=None, count: bool = True):
+    """Returns the number of proposals (the call then waits for the stream), or None with count=False
+    (fully asynchronous)."""
     m = c_i64()
-    _check(_lib.scn_gated_hist_scores(s, _ptr(gate), tau, _ptr(proposed), _ptr(score), _ptr(flag), ctypes.byref(m),
-                                      _stream(stream)), "scn_gated_hist_scores")
-    return m.value
+    _check(_lib.scn_gated_hist_scores(s, _ptr(gate), tau, _ptr(proposed), _ptr(score), _ptr(flag),
+                                      ctypes.byref(m) if count else None, _stream(stream)), "scn_gated_hist_scores")
+    return m.value if count else None
 
 
-def scn_proposal_hist_scores(s: int, net: int, tau: float, thumbs, logits, proposed, score, flag, stream=None) -> int:
+def scn_proposal_hist_scores(s: int, net: int, tau: float, thumbs, logits, proposed, score, flag, stream=None,
+                             count: bool = True):
+    """As scn_gated_hist_scores, gated by the network's logits."""
     m = c_i64()
     _check(_lib.scn_proposal_hist_scores(s, net, tau, _ptr(thumbs), _ptr(logits), _ptr(proposed), _ptr(score),
-                                         _ptr(flag), ctypes.byref(m), _stream(stream)), "scn_proposal_hist_scores")
-    return m.value
+                                         _ptr(flag), ctypes.byref(m) if count else None, _stream(stream)),
+           "scn_proposal_hist_scores")
+    return m.value if count else None
 
 
 def scn_thumb_diff(thumbs, n: int, diff, stream=None) -> None:

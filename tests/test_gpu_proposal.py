@@ -70,6 +70,23 @@ def test_gate_all_and_random(scn, tiny):
         assert m == int(p.sum()) == int((g[1:] > tau).sum())
 
 
+def test_gate_async_calls_in_a_row(scn, tiny):
+    """Without the count the calls never wait for the GPU; back-to-back calls on one sequence (none,
+    all, some proposed) each stay exact, so every device counter is left clean for the next."""
+    T = tiny["T"]
+    rng = np.random.default_rng(2)
+    g_host = rng.random(T).astype(np.float32)
+    g = torch.from_numpy(g_host).cuda()
+    taus = (2.0, -1.0, 0.9, 0.3)
+    outs = [_outs(T) for _ in taus]
+    for (prop, sc, fl), tau in zip(outs, taus):
+        assert scn.scn_gated_hist_scores(tiny["seq"], g, tau, prop, sc, fl, count=False) is None
+    torch.cuda.synchronize()
+    for (prop, sc, fl), tau in zip(outs, taus):
+        p = _check(prop, sc, fl, tiny["exact"])
+        assert int(p.sum()) == int((g_host[1:] > tau).sum())
+
+
 def test_thumb_diff(scn, orc, tiny):
     T = tiny["T"]
     th = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
