@@ -72,6 +72,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step_per_rank: float, world: int, ms_step: float) -> float:
+    """Units all ranks processed per second (replicas: every rank does the same work)."""
+    return units_per_step_per_rank * world / (ms_step / 1000.0)
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -304,14 +320,9 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end), world)
     ms_step = ms_total / args.steps
-    value = frames_per_step * world / (ms_step / 1000)
+    value = whole_job_rate(frames_per_step, world, ms_step)
 
     # dominant kernel: the fused hist+score launch over the 7200-frame stride-1 sequence
     kern = {}
