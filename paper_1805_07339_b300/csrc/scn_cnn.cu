@@ -119,6 +119,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return static_cast<uint32_t>(__bfloat16_as_ushort(a)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b)) << 16);
 }
 
+// BF16 pair (lo, hi) of relu(lo), relu(hi): one paired conversion, then the ReLU on
+// the packed pair; rounding keeps the sign, so this equals rounding relu(x)
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    v = __hmax2(v, __float2bfloat162_rn(0.f));
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
 // 8 consecutive im2col values (columns 8j..8j+7) of output row (pair b, position pos)
 template <int L>
 __device__ __forceinline__ uint4 im2col_chunk(const ConvFwdArgs& a, int64_t b, int pos, int j) {
@@ -681,8 +689,7 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
                 uint32_t o[8];
 #pragma unroll
                 for (int c = 0; c < 16; c += 2)
-                    o[c / 2] = pack_bf16(fmaxf(__uint_as_float(acc[c]) + bias[c], 0.f),
-                                         fmaxf(__uint_as_float(acc[c + 1]) + bias[c + 1], 0.f));
+                    o[c / 2] = relu_bf16x2(__uint_as_float(acc[c]) + bias[c], __uint_as_float(acc[c + 1]) + bias[c + 1]);
                 const int row = p * kFzR2 + oy + 1;
                 uint8_t* dst = (ox & 1) ? O2 + row * kFzO2Pitch + ((ox + 1) >> 1) * 16 : E2 + row * kFzE2Pitch + (ox >> 1) * 16;
                 const int cs = (ox & 1) ? kFzO2Plane : kFzE2Plane;
@@ -742,9 +749,9 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
                     uint32_t o[8];
 #pragma unroll
                     for (int c = 0; c < 16; c += 2)
-                        o[c / 2] = pack_bf16(
-                            fmaxf(__uint_as_float(u0[c]) + __uint_as_float(u1[c]) + bias[16 + c0 + c], 0.f),
-                            fmaxf(__uint_as_float(u0[c + 1]) + __uint_as_float(u1[c + 1]) + bias[16 + c0 + c + 1], 0.f));
+                        o[c / 2] = relu_bf16x2(__uint_as_float(u0[c]) + __uint_as_float(u1[c]) + bias[16 + c0 + c],
+                                               __uint_as_float(u0[c + 1]) + __uint_as_float(u1[c + 1]) +
+                                                   bias[16 + c0 + c + 1]);
                     const int q = c0 / 8;
                     *reinterpret_cast<uint4*>(dst + q * cs) = make_uint4(o[0], o[1], o[2], o[3]);
                     *reinterpret_cast<uint4*>(dst + (q + 1) * cs) = make_uint4(o[4], o[5], o[6], o[7]);
