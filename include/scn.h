@@ -338,6 +338,25 @@ scn_status scn_slice_middles(const int32_t* d_start, const int64_t* d_count, int
  * else as scn_shot_scores. */
 scn_status scn_shot_scores_sliced(const uint32_t* d_hist, int64_t n, int64_t pixel_count, const uint8_t* d_boundary,
                                   uint32_t* d_score, uint8_t* d_flag, void* stream);
+/* Stencil S[a, b] over a histogram sequence (Sec. 3.2, "Stencil operations":
+ * an op may read a window of elements around each one), the windowed shot
+ * score: with P = -a frames before element k and F = b + 1 frames from it
+ * (-64 <= a < 0 <= b < 64),
+ *   score[k] = sum over the 48 bins |F * sum_{j=a}^{-1} h[k+j] - P * sum_{j=0}^{b} h[k+j]|
+ *   flag[k]  = 2 * score[k] > P * F * pixel_count
+ * (the L1 distance of the two windows' mean histograms, scaled by P*F to stay
+ * integer; a = -1, b = 0 is scn_shot_scores).  k whose window leaves [0, n), or
+ * holds a slice start after its first frame (d_boundary != 0 at k+a+1 .. k+b;
+ * d_boundary may be NULL), gets 0.  Only a slice of the sequence need be
+ * resident: d_hist (device uint32 [hist_count][48]) and d_boundary hold
+ * elements [hist_first, hist_first + hist_count); the outputs are elements
+ * [k0, k1), written to d_score[k - k0] (device uint64) and d_flag[k - k0].  The
+ * outputs' dependency range (Sec. 4.2), [max(0, k0 + a), min(n, k1 + b)), must
+ * lie inside the resident slice, else SCN_ERANGE: a sequence can be split into
+ * shards that each carry their -a / b element halo.  Errors: SCN_EINVAL. */
+scn_status scn_window_scores(const uint32_t* d_hist, int64_t hist_first, int64_t hist_count, int64_t n, int32_t a,
+                             int32_t b, int64_t pixel_count, const uint8_t* d_boundary, int64_t k0, int64_t k1,
+                             uint64_t* d_score, uint8_t* d_flag, void* stream);
 /* Montage of sequence elements (Sec. 5.2, film summaries: one frame from each
  * shot): tile i (row-major, `cols` tiles per row) shows element d_elem[i]
  * (device int32, m entries) of s, nearest-neighbour downsampled to tile_w x

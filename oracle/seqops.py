@@ -85,3 +85,36 @@ def montage(frames: list, W: int, H: int, cols: int, tile_w: int, tile_h: int) -
         r0, c0 = (i // cols) * tile_h, (i % cols) * tile_w
         out[r0:r0 + tile_h, c0:c0 + tile_w] = yuv_to_rgb_array(yuv.reshape(-1, 3)).reshape(tile_h, tile_w, 3)
     return out
+
+
+def window_scores(hist: np.ndarray, a: int, b: int, pixel_count: int, boundary=None):
+    """Stencil S[a, b] shot score (Sec. 3.2 stencils; a < 0 <= b): for element k,
+    with P = -a frames before it and F = b + 1 frames from it,
+      score[k] = sum over bins | F * sum_{j=a}^{-1} h[k+j] - P * sum_{j=0}^{b} h[k+j] |,
+      flag[k] = 2 * score[k] > P * F * pixel_count,
+    i.e. the L1 distance of the two windows' mean histograms, scaled by P * F to stay
+    in integers.  An element whose window reaches outside the sequence, or contains a
+    slice start after its first element (boundary[s] != 0 for k+a < s <= k+b), gets
+    score 0 and flag 0.  a = -1, b = 0 is the plain two-frame shot score."""
+    h = np.asarray(hist, dtype=np.int64).reshape(len(hist), -1)
+    n = h.shape[0]
+    P, F = -a, b + 1
+    score = np.zeros(n, dtype=np.uint64)
+    flag = np.zeros(n, dtype=np.uint8)
+    for k in range(n):
+        if k + a < 0 or k + b >= n:
+            continue
+        if boundary is not None and any(boundary[s] for s in range(k + a + 1, k + b + 1)):
+            continue
+        before = h[k + a:k].sum(axis=0)
+        after = h[k:k + b + 1].sum(axis=0)
+        sc = int(np.abs(F * before - P * after).sum())
+        score[k] = sc
+        flag[k] = 1 if 2 * sc > P * F * pixel_count else 0
+    return score, flag
+
+
+def stencil_inputs(k0: int, k1: int, a: int, b: int, n: int) -> tuple[int, int]:
+    """Per-element dependency analysis of S[a, b] (Sec. 4.2): the input elements the
+    outputs [k0, k1) read, clipped to the sequence."""
+    return max(0, k0 + a), min(n, k1 + b)

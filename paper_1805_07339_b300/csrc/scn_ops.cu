@@ -169,6 +169,44 @@ __global__ void sliced_scores_kernel(const uint32_t* hist, int64_t n, int64_t pi
     }
 }
 
+// Stencil S[a, b] shot score, one warp per output element k (global index): with
+// P = -a frames before k and F = b + 1 frames from k, score = sum over the 48 bins
+// of |F * sum_{j=a..-1} h[k+j] - P * sum_{j=0..b} h[k+j]|, flag = 2 score > P F px.
+// Elements whose window leaves [0, n) or holds a slice start after its first
+// frame score 0.  hist/boundary hold elements [first, first + count) only.
+constexpr int kMaxWindow = 64;
+
+__global__ void window_scores_kernel(const uint32_t* hist, const uint8_t* boundary, int64_t first, int64_t n, int a,
+                                     int b, int64_t pixel_count, int64_t k0, int64_t k1, uint64_t* score,
+                                     uint8_t* flag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = k0 + blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
+    if (k >= k1) return;
+    const int64_t P = -a, F = b + 1;
+    bool zero = k + a < 0 || k + b >= n;
+    if (!zero && boundary) {
+        bool hit = false;
+        for (int j = a + 1 + lane; j <= b; j += 32) hit |= boundary[k + j - first] != 0;
+        zero = __any_sync(0xffffffffu, hit);
+    }
+    uint64_t d = 0;
+    if (!zero) {
+        for (int bin = lane; bin < 48; bin += 32) {
+            int64_t before = 0, after = 0;
+            for (int j = a; j < 0; ++j) before += hist[(k + j - first) * 48 + bin];
+            for (int j = 0; j <= b; ++j) after += hist[(k + j - first) * 48 + bin];
+            const int64_t v = F * before - P * after;
+            d += static_cast<uint64_t>(v < 0 ? -v : v);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) {
+        score[k - k0] = d;
+        flag[k - k0] = (2ull * d > static_cast<uint64_t>(P * F) * static_cast<uint64_t>(pixel_count)) ? 1 : 0;
+    }
+}
+
 // Montage: tile i (row-major over `cols` tiles) shows sequence element elem[i],
 // nearest-neighbour downsampled: output pixel (x, y) of a tw x th tile takes
 // source pixel (floor((2x+1) W / (2 tw)), floor((2y+1) H / (2 th))) of the
@@ -288,6 +326,25 @@ scn_status scn_shot_scores_sliced(const uint32_t* d_hist, int64_t n, int64_t pix
     if (blocks > 0x7fffffff) return SCN_ERANGE;
     sliced_scores_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         d_hist, n, pixel_count, d_boundary, d_score, d_flag);
+    SCN_CUDA_TRY(cudaGetLastError());
+    return SCN_OK;
+}
+
+scn_status scn_window_scores(const uint32_t* d_hist, int64_t hist_first, int64_t hist_count, int64_t n, int32_t a,
+                             int32_t b, int64_t pixel_count, const uint8_t* d_boundary, int64_t k0, int64_t k1,
+                             uint64_t* d_score, uint8_t* d_flag, void* stream) {
+    if (a >= 0 || b < 0 || -a > kMaxWindow || b + 1 > kMaxWindow || pixel_count < 0 || n < 0) return SCN_EINVAL;
+    if (k0 < 0 || k1 < k0 || k1 > n || hist_first < 0 || hist_count < 0) return SCN_ERANGE;
+    if (k1 == k0) return SCN_OK;
+    if (!d_hist || !d_score || !d_flag) return SCN_EINVAL;
+    // dependency analysis: the outputs [k0, k1) read elements [k0 + a, k1 + b) within [0, n)
+    const int64_t need0 = std::max<int64_t>(0, k0 + a), need1 = std::min<int64_t>(n, k1 + b);
+    if (need0 < hist_first || need1 > hist_first + hist_count) return SCN_ERANGE;
+    if (pixel_count > (int64_t(1) << 40)) return SCN_ERANGE;
+    const int64_t blocks = (k1 - k0 + 7) / 8;
+    if (blocks > 0x7fffffff) return SCN_ERANGE;
+    window_scores_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        d_hist, d_boundary, hist_first, n, a, b, pixel_count, k0, k1, d_score, d_flag);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }

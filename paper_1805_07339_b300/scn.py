@@ -111,6 +111,7 @@ SIGNATURES = [
     ("scn_slice_middles", c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
     ("scn_shot_scores_sliced", c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
     ("scn_montage", c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_vp, c_vp]),
+    ("scn_window_scores", c_i32, [c_vp, c_i64, c_i64, c_i64, c_i32, c_i32, c_i64, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
 ]
 
 
@@ -484,3 +485,10 @@ def scn_shot_scores_sliced(hist, n: int, pixel_count: int, boundary, score, flag
 
 def scn_montage(s: int, elems, m: int, cols: int, tile_w: int, tile_h: int, out, stream=None) -> None:
     _check(_lib.scn_montage(s, _ptr(elems), m, cols, tile_w, tile_h, _ptr(out), _stream(stream)), "scn_montage")
+
+
+def scn_window_scores(hist, hist_first: int, hist_count: int, n: int, a: int, b: int, pixel_count: int, k0: int,
+                      k1: int, score, flag, boundary=None, stream=None) -> None:
+    """hist: CUDA tensor holding elements [hist_first, hist_first + hist_count) of the sequence."""
+    _check(_lib.scn_window_scores(_ptr(hist), hist_first, hist_count, n, a, b, pixel_count, _ptr(boundary), k0, k1,
+                                  _ptr(score), _ptr(flag), _stream(stream)), "scn_window_scores")

@@ -155,3 +155,59 @@ def test_montage_random_bytes_and_odd_tiles(scn, orc):
     finally:
         scn.scn_seq_destroy(seq)
         scn.scn_table_destroy(t)
+
+
+@pytest.mark.parametrize("a,b", [(-1, 0), (-2, 1), (-8, 3), (-64, 63)])
+def test_window_scores_match_oracle(scn, a, b):
+    rng = np.random.default_rng(-a * 100 + b)
+    n, px = 1501, 320 * 180
+    hist = rng.integers(0, 4000, (n, 48)).astype(np.uint32)
+    bnd = (rng.random(n) < 0.03).astype(np.uint8)
+    d_hist = torch.from_numpy(hist.view(np.int32)).cuda()
+    for boundary in (None, bnd):
+        s = torch.empty(n, dtype=torch.int64, device="cuda")
+        f = torch.empty(n, dtype=torch.uint8, device="cuda")
+        scn.scn_window_scores(d_hist, 0, n, n, a, b, px, 0, n, s, f,
+                              boundary=None if boundary is None else torch.from_numpy(boundary).cuda())
+        rs, rf = seqops.window_scores(hist, a, b, px, boundary=boundary)
+        assert np.array_equal(s.cpu().numpy().view(np.uint64), rs) and np.array_equal(f.cpu().numpy(), rf)
+
+
+def test_window_scores_plain_window_equals_shot_scores(tiny):
+    scn, T, W, H = tiny["scn"], tiny["T"], tiny["W"], tiny["H"]
+    seq = scn.scn_sample(tiny["table"], scn.SCN_STRIDE, 0, T, 1)
+    try:
+        h, s, f = _hs(scn, seq, T)
+        ws = torch.empty(T, dtype=torch.int64, device="cuda")
+        wf = torch.empty(T, dtype=torch.uint8, device="cuda")
+        scn.scn_window_scores(h, 0, T, T, -1, 0, W * H, 0, T, ws, wf)
+        assert np.array_equal(ws.cpu().numpy(), s.cpu().numpy().astype(np.int64))
+        assert np.array_equal(wf.cpu().numpy(), f.cpu().numpy())
+    finally:
+        scn.scn_seq_destroy(seq)
+
+
+def test_window_scores_sharded_with_halos(scn):
+    """Shards that hold only their dependency range (outputs plus a -a / b element halo)
+    give the unsharded result; a slice missing part of the range is refused."""
+    from paper_1805_07339_b300 import stencil
+    rng = np.random.default_rng(21)
+    n, px, a, b = 2000, 640 * 360, -5, 3
+    d_hist = torch.from_numpy(rng.integers(0, 9000, (n, 48)).astype(np.int32)).cuda()
+    d_bnd = torch.from_numpy((rng.random(n) < 0.02).astype(np.uint8)).cuda()
+    full_s = torch.empty(n, dtype=torch.int64, device="cuda")
+    full_f = torch.empty(n, dtype=torch.uint8, device="cuda")
+    scn.scn_window_scores(d_hist, 0, n, n, a, b, px, 0, n, full_s, full_f, boundary=d_bnd)
+    for parts in (1, 3, 7, 64):
+        s, f = stencil.window_scores_sharded(torch, d_hist, n, a, b, px, parts, boundary=d_bnd)
+        assert torch.equal(s, full_s) and torch.equal(f, full_f), parts
+    # outputs [100, 200) need elements [95, 203): a slice starting at 96 is one short
+    s = torch.empty(100, dtype=torch.int64, device="cuda")
+    f = torch.empty(100, dtype=torch.uint8, device="cuda")
+    with pytest.raises(scn.ScnError):
+        scn.scn_window_scores(d_hist[96:203].clone(), 96, 107, n, a, b, px, 100, 200, s, f)
+    scn.scn_window_scores(d_hist[95:203].clone(), 95, 108, n, a, b, px, 100, 200, s, f,
+                          boundary=d_bnd[95:203].clone())
+    assert torch.equal(s, full_s[100:200]) and torch.equal(f, full_f[100:200])
+    with pytest.raises(scn.ScnError):  # window wider than 64
+        scn.scn_window_scores(d_hist, 0, n, n, -65, 0, px, 0, n, full_s, full_f)

@@ -86,3 +86,58 @@ def test_montage_layout_and_constant_frames():
     assert m.shape == (6, 10, 3)
     assert np.all(m[:3, :5] == 128) and np.all(m[:3, 5:] == 0) and np.all(m[3:, :5] == 128) and np.all(m[3:, 5:] == 0)
     assert oracle.yuv_to_rgb(126, 128, 128) == (128, 128, 128)
+
+
+def test_window_scores_reduce_to_the_plain_score():
+    rng = np.random.default_rng(10)
+    hist = rng.integers(0, 900, (40, 48)).astype(np.uint32)
+    s0, f0 = oracle.scores(hist, 7000)
+    s, f = seqops.window_scores(hist, -1, 0, 7000)
+    assert np.array_equal(s.astype(np.uint64), s0.astype(np.uint64)) and np.array_equal(f, f0)
+
+
+def test_window_scores_hand_cases():
+    # one bin, pixel_count 10: a cut between frames 3 and 4, and a one-frame flash at 8
+    h = np.zeros((12, 1), np.int64)
+    h[:4, 0] = 10
+    h[4:, 0] = 0
+    h[8, 0] = 10
+    s, f = seqops.window_scores(h, -2, 1, 10)  # P = 2 before, F = 2 from k
+    # k = 4: before = frames 2, 3 (20), after = frames 4, 5 (0): |2*20 - 2*0| = 40 > 2*2*10/2
+    assert s[4] == 40 and f[4] == 1
+    # k = 8 (the flash): before = 6, 7 (0), after = 8, 9 (10): |0 - 20| = 20, 2*20 = 40 = P*F*10: no flag
+    assert s[8] == 20 and f[8] == 0
+    # the plain score flags the flash twice (into it and out of it)
+    _, fp = seqops.window_scores(h, -1, 0, 10)
+    assert fp[8] == 1 and fp[9] == 1
+    # windows outside the sequence: the first 2 and the last 1 elements
+    assert s[0] == s[1] == s[11] == 0
+    # a slice start inside the window (after its first element) zeroes the score: the windows of
+    # k = 4, 5, 6 contain frame 5 after their first frame; k = 7's window starts at frame 5
+    bnd = np.zeros(12, np.uint8)
+    bnd[5] = 1
+    sb, _ = seqops.window_scores(h, -2, 1, 10, boundary=bnd)
+    assert sb[4] == 0 and sb[5] == 0 and sb[6] == 0
+    assert sb[3] == s[3] and sb[7] == s[7] and sb[8] == s[8]
+
+
+def test_window_scores_brute_force_and_dependency_ranges():
+    rng = np.random.default_rng(11)
+    for a, b in [(-1, 0), (-3, 0), (-2, 2), (-5, 4)]:
+        hist = rng.integers(0, 50, (30, 4)).astype(np.int64)
+        s, f = seqops.window_scores(hist, a, b, 100)
+        for k in range(30):
+            if k + a < 0 or k + b >= 30:
+                assert s[k] == 0
+                continue
+            P, F = -a, b + 1
+            mb = hist[k + a:k].sum(0) / P
+            ma = hist[k:k + b + 1].sum(0) / F
+            assert abs(s[k] - P * F * np.abs(mb - ma).sum()) < 1e-6
+        # outputs [k0, k1) computed from only their dependency range give the same values
+        for k0, k1 in [(0, 7), (7, 19), (19, 30)]:
+            i0, i1 = seqops.stencil_inputs(k0, k1, a, b, 30)
+            part = np.zeros_like(hist)
+            part[i0:i1] = hist[i0:i1]  # everything outside the range erased
+            sp, _ = seqops.window_scores(part, a, b, 100)
+            assert np.array_equal(sp[k0:k1], s[k0:k1])
