@@ -251,7 +251,7 @@ scn_status scn_plan_autotune(scn_plan* p, int32_t reps, void* stream, scn_tune* 
 /* Learned boundary proposal: a tiny BF16 CNN (FP32 accumulation, tcgen05    */
 /* tensor cores for the convolutions) over pairs of 36x64 luma thumbnails.    */
 /* The paper runs DNNs on sampled frames (Sec. 3.1, Sec. 5.1.2) but fixes no   */
-/* proposal network; this one is the build's:                               */
+/* proposal network; this library's is:                                     */
 /*   x = [(Yprev-128)/64, (Ycur-128)/64] (2x36x64) -> conv3x3/s2/p1 2->16 ->  */
 /*   16->32 -> 32->32 (each + bias + ReLU) -> mean over 5x8 -> FC 32->64 +    */
 /*   ReLU -> FC 64->1 = logit.  16369 parameters, flat fp32 in that order    */
@@ -370,7 +370,7 @@ scn_status scn_montage(const scn_seq* s, const int32_t* d_elem, int64_t m, int32
 
 /* ------------------------------------------------------------------------ */
 /* Gated exact path: a gate proposes boundary candidates, only the frames of */
-/* proposed pairs go through the exact kernel, which remains the judge.      */
+/* proposed pairs go through the exact kernel, which keeps the final say.  */
 /* ------------------------------------------------------------------------ */
 /* d_gate[k] (device float, k >= 1) scores pair (k-1, k) of the sequence; pair
  * k is proposed when d_gate[k] > tau (d_gate[0] is ignored).  Writes

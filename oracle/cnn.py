@@ -2,7 +2,7 @@
 
 The paper's pipelines run a DNN on sampled frames (Sec. 3.1 face detection,
 Sec. 5.1.2 DNN) but fix no network for shot proposals.  This is the network
-the build specifies:
+used here:
   input  x: 2 x 36 x 64, channel 0 = (Y_prev - 128) / 64, channel 1 = (Y_cur - 128) / 64,
             Y = luma thumbnail (every s-th row and column of the frame);
   a1 = relu(conv3x3/s2/p1(x;  W1: 16 x 2,  b1))     -> 16 x 18 x 32

@@ -1,7 +1,7 @@
 // Gated exact path: a cheap gate (the proposal network's logits, or any score)
 // proposes candidate boundaries between consecutive sampled frames, and only
 // the frames of proposed pairs go through the exact convert + histogram +
-// score kernel, which stays the judge: an unproposed pair gets score 0 and
+// score kernel, which keeps the final say: an unproposed pair gets score 0 and
 // flag 0, a proposed pair gets its exact score and flag.
 //
 // Steps: proposals -> compacted list of proposed elements k (pair k-1, k) ->

@@ -4,7 +4,7 @@ Every number crunched here runs in libscn's kernels (generator, thumbnails,
 exact histogram/score path, the network's forward/backward/Adam, the gated exact
 path); this module only sequences the calls and counts.
 
-Data (the build's reading of the proposal workload): 1080p synthetic videos of
+Data (this library's reading of the proposal workload): 1080p synthetic videos of
 7200 frames and 60 shots; a training pair is two consecutive frames (k-1, k)
 labelled by the exact detector's flag of frame k.  Training, threshold and
 evaluation videos use disjoint video ids.

@@ -1,5 +1,5 @@
 """Gated exact path and the learned proposal pipeline on the GPU: the exact
-kernel stays the judge on every proposed pair, unproposed pairs get 0."""
+kernel has the final say on every proposed pair, unproposed pairs get 0."""
 import numpy as np
 import pytest
 
