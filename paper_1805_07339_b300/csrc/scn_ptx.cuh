@@ -1,5 +1,5 @@
-// Thin inline-PTX wrappers used by the kernels (mbarrier, bulk async copy,
-// byte dot products, byte permute, bounded waits).
+// Thin inline-PTX wrappers used by the kernels (mbarrier, byte dot products,
+// byte permute, bounded waits).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -18,11 +18,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -56,15 +51,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 255u) == 0 && globaltimer() - t0 > limit_ns) return false;
     }
-}
-
-// 1-D bulk copy global -> shared (TMA engine), completion counted on bar.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
 }
 
 // d = c + a.h0 * b.byte0 + a.h1 * b.byte1   (unsigned a, unsigned b)
