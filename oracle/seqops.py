@@ -11,7 +11,13 @@ Definitions (Scanner, Poms et al. 2018):
     not cross them (Sec. 3.2, slicing/unslicing); a boundary element starts a
     slice, and so does element 0;
   * a film summary shows one frame per shot (Sec. 5.2, montage); here the
-    middle element of each slice, nearest-neighbour downsampled into a tile.
+    middle element of each slice, nearest-neighbour downsampled into a tile;
+  * a stencil S[a, b] reads a window of elements around each output (Sec. 3.2);
+  * a bounded-state op carries state from element to element, and before it
+    produces element i it has processed at least the W elements before i (the
+    warmup, Sec. 3.2); a run of outputs therefore starts W elements early and
+    drops those outputs; dependency analysis treats the op as a stencil over
+    (i - W .. i) (Sec. 4.2).
 Pins: tests/test_oracle_seqops.py.
 """
 from __future__ import annotations
@@ -118,3 +124,72 @@ def stencil_inputs(k0: int, k1: int, a: int, b: int, n: int) -> tuple[int, int]:
     """Per-element dependency analysis of S[a, b] (Sec. 4.2): the input elements the
     outputs [k0, k1) read, clipped to the sequence."""
     return max(0, k0 + a), min(n, k1 + b)
+
+
+def bounded_state_run(hist: np.ndarray, pixel_count: int, shift: int, j0: int, k0: int, k1: int, boundary=None):
+    """One run of the bounded-state shot score: process elements j0 .. k1-1 in order,
+    return the outputs of [k0, k1) as (score list, flag list).
+
+    The state is a reference histogram m.  The first processed element, and an
+    element where a slice starts (boundary != 0), set m to its own histogram and
+    output (0, 0).  Every other element j outputs d = sum over bins |h[j] - m| and
+    f = (2 d > pixel_count), then updates m to h[j] when f is set (a cut restarts
+    the reference), else m + floor((h[j] - m) / 2**shift) (an exponential average
+    of the shot so far).  shift = 0 makes m the previous histogram, i.e. the plain
+    two-frame score."""
+    h = np.asarray(hist, dtype=np.int64).reshape(len(hist), -1)
+    m = None
+    scores, flags = [], []
+    for j in range(j0, k1):
+        if m is None or (boundary is not None and boundary[j] != 0):
+            m = h[j].copy()
+            d, f = 0, 0
+        else:
+            d = int(np.abs(h[j] - m).sum())
+            f = 1 if 2 * d > pixel_count else 0
+            if f:
+                m = h[j].copy()
+            else:
+                m = m + np.floor_divide(h[j] - m, 2 ** shift)
+        if j >= k0:
+            scores.append(d)
+            flags.append(f)
+    return scores, flags
+
+
+def bounded_state_runs(first: int, length: int, stride: int, count: int, n: int) -> list[tuple[int, int]]:
+    """Output runs of the pattern: run r covers [first + r*stride, first + r*stride + length)
+    clipped to [0, n) (possibly empty)."""
+    out = []
+    for r in range(count):
+        k0 = first + r * stride
+        out.append((min(k0, n), min(k0 + length, n)))
+    return out
+
+
+def bounded_state_scores(hist: np.ndarray, pixel_count: int, shift: int, warmup: int, first: int, length: int,
+                         stride: int, count: int, boundary=None):
+    """Bounded-state shot scores over runs of outputs, each run processed on its own
+    from W = warmup elements before its first output (clipped at element 0); output
+    slot r*length + (k - run start) holds element k of run r.  Slots of elements
+    past the sequence's end hold -1."""
+    n = len(hist)
+    score = np.full(count * length, -1, dtype=np.int64)
+    flag = np.full(count * length, -1, dtype=np.int64)
+    for r, (k0, k1) in enumerate(bounded_state_runs(first, length, stride, count, n)):
+        if k1 <= k0:
+            continue
+        s, f = bounded_state_run(hist, pixel_count, shift, max(0, k0 - warmup), k0, k1, boundary)
+        score[r * length:r * length + (k1 - k0)] = s
+        flag[r * length:r * length + (k1 - k0)] = f
+    return score, flag
+
+
+def bounded_state_inputs(first: int, length: int, stride: int, count: int, warmup: int, n: int) -> list[int]:
+    """The exact set of input elements the runs read (Sec. 4.2: a warmup of W is a
+    stencil footprint i - W .. i), ascending."""
+    need = set()
+    for k0, k1 in bounded_state_runs(first, length, stride, count, n):
+        if k1 > k0:
+            need.update(range(max(0, k0 - warmup), k1))
+    return sorted(need)

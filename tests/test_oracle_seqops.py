@@ -141,3 +141,68 @@ def test_window_scores_brute_force_and_dependency_ranges():
             part[i0:i1] = hist[i0:i1]  # everything outside the range erased
             sp, _ = seqops.window_scores(part, a, b, 100)
             assert np.array_equal(sp[k0:k1], s[k0:k1])
+
+
+def test_bounded_state_hand_example():
+    # two bins, pixel_count 100, shift 1 (the reference moves half way to each frame, floor)
+    h = np.zeros((5, 2), np.int64)
+    h[:] = [[10, 0], [6, 4], [9, 1], [0, 60], [0, 61]]
+    # serial: m = (10, 0); k=1: |6-10|+|4-0| = 8, m = (10-2, 0+2) = (8, 2);
+    # k=2: |9-8|+|1-2| = 2, m = (8 + floor(1/2), 2 + floor(-1/2)) = (8, 1);
+    # k=3: |0-8|+|60-1| = 67, 134 > 100: cut, m = (0, 60); k=4: |0|+|61-60| = 1
+    s, f = seqops.bounded_state_scores(h, 100, 1, 0, 0, 5, 5, 1)
+    assert s.tolist() == [0, 8, 2, 67, 1] and f.tolist() == [0, 0, 0, 1, 0]
+    # runs of two outputs, warmup 1: run [2, 4) starts at 1 with m = (6, 4):
+    # k=2: |9-6|+|1-4| = 6, m = (6 + floor(3/2), 4 + floor(-3/2)) = (7, 2); k=3: |0-7|+|60-2| = 65, a cut;
+    # the ragged run [4, 5) starts at 3 with m = (0, 60): k=4 scores 1; slot 5 is past the end
+    s, f = seqops.bounded_state_scores(h, 100, 1, 1, 0, 2, 2, 3)
+    assert s.tolist() == [0, 8, 6, 65, 1, -1] and f.tolist() == [0, 0, 0, 1, 0, -1]
+    # warmup 0: every run starts from its own first output, which scores 0; run [2, 4) has m = (9, 1)
+    # at k=3: |0-9|+|60-1| = 68
+    s, _ = seqops.bounded_state_scores(h, 100, 1, 0, 0, 2, 2, 3)
+    assert s.tolist() == [0, 8, 0, 68, 0, -1]
+    # a slice start at 2 restarts the state as a run start does: m = (9, 1), k=3: |0-9|+|60-1| = 68, a cut
+    bnd = np.array([0, 0, 1, 0, 0], np.uint8)
+    s, f = seqops.bounded_state_scores(h, 100, 1, 0, 0, 5, 5, 1, boundary=bnd)
+    assert s.tolist() == [0, 8, 0, 68, 1] and f.tolist() == [0, 0, 0, 1, 0]
+    # sparse outputs (every other element, warmup 2) read exactly the elements within 2 before each
+    assert seqops.bounded_state_inputs(1, 1, 2, 2, 2, 5) == [0, 1, 2, 3]
+    assert seqops.bounded_state_inputs(4, 1, 9, 3, 1, 5) == [3, 4]
+
+
+def test_bounded_state_shift_zero_is_the_plain_score():
+    rng = np.random.default_rng(12)
+    hist = rng.integers(0, 900, (60, 48)).astype(np.uint32)
+    s0, f0 = oracle.scores(hist, 20000)
+    for warmup, length in [(1, 60), (1, 7), (3, 1), (60, 13)]:
+        count = -(-60 // length)
+        s, f = seqops.bounded_state_scores(hist, 20000, 0, warmup, 0, length, length, count)
+        assert np.array_equal(s[:60], s0.astype(np.int64)) and np.array_equal(f[:60], f0.astype(np.int64))
+    bnd = (rng.random(60) < 0.1).astype(np.uint8)
+    sb, fb = seqops.sliced_scores(hist, bnd, 20000)
+    s, f = seqops.bounded_state_scores(hist, 20000, 0, 1, 0, 60, 60, 1, boundary=bnd)
+    assert np.array_equal(s, sb.astype(np.int64)) and np.array_equal(f, fb.astype(np.int64))
+
+
+def test_bounded_state_runs_agree_with_serial_where_the_state_restarts():
+    # Shot-like histograms: the state of a run equals the serial state from a slice start
+    # on, so a run whose warmup reaches back to a slice start (or to element 0) gives the
+    # serial outputs; with shift > 0 and no restart in reach they may differ.
+    rng = np.random.default_rng(13)
+    n = 90
+    base = rng.integers(0, 400, (6, 48))
+    shot = np.repeat(np.arange(6), 15)
+    hist = (base[shot] + rng.integers(0, 60, (n, 48))).astype(np.int64)
+    bnd = np.zeros(n, np.uint8)
+    bnd[::15] = 1
+    serial, sflag = seqops.bounded_state_scores(hist, 30000, 2, 0, 0, n, n, 1, boundary=bnd)
+    for length, warmup in [(5, 15), (10, 14), (7, 20), (1, 15)]:
+        count = -(-n // length)
+        s, f = seqops.bounded_state_scores(hist, 30000, 2, warmup, 0, length, length, count, boundary=bnd)
+        assert np.array_equal(s[:n], serial) and np.array_equal(f[:n], sflag)
+    # no slice starts: warmup that reaches element 0 reproduces the serial run
+    serial, _ = seqops.bounded_state_scores(hist, 30000, 2, 0, 0, n, n, 1)
+    s, _ = seqops.bounded_state_scores(hist, 30000, 2, n, 0, 10, 10, 9)
+    assert np.array_equal(s, serial)
+    short, _ = seqops.bounded_state_scores(hist, 30000, 2, 1, 0, 10, 10, 9)
+    assert not np.array_equal(short, serial)
