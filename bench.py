@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-proposal", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--no-state", action="store_true")
     return ap.parse_args()
 
 
@@ -345,6 +346,11 @@ def main():
                 "kernel": "hist_kernel (scn_hist_scores, stride-1, 7200 frames)",
                 "alg_bytes_per_launch": dom["frames"] * ALG_BYTES_PER_FRAME}
 
+    # ---- the bounded-state shot score over the stride-1 histograms: serial vs shards with warmup
+    state = None
+    if not args.no_state:
+        state = run_bounded_state(scn, torch, outs["stride1"][0], W * H, stream)
+
     # ---- end-to-end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -428,12 +434,51 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_GB_per_s": frames_per_step * ALG_BYTES_PER_FRAME / (ms_step / 1000) / 1e9,
             "kernels": kern, "roofline": roofline, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
-            "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "stream": news, "proposal": prop, "paper_context": PAPER_CONTEXT,
+            "e2e": e2e, "cpu_baseline": cpu, "batched": batched, "stream": news, "proposal": prop,
+            "bounded_state": state, "paper_context": PAPER_CONTEXT,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_bounded_state(scn, torch, hist, px, stream, shift=3, warmup=24, reps=20):
+    """The bounded-state shot score (reference histogram, exponential average with
+    shift 3, restarted at cuts) over the 7200 stride-1 histograms: one serial run,
+    1184 shards (8 per SM) each after a warmup of 24 elements, and every 24th output
+    alone after the same warmup or after 8 elements (a third of the inputs read).  Device time per call (CUDA events, mean of reps)
+    and how often the sharded flags equal the serial ones."""
+    from paper_1805_07339_b300 import stencil
+    n = hist.shape[0]
+    pats = {"serial": (0, n, n, 1), "shards_1184": stencil.state_shards(n, 1184),
+            "every_24th": stencil.state_sparse(n, 24), "every_24th_w8": stencil.state_sparse(n, 24)}
+    res, flags = {}, {}
+    for name, pat in pats.items():
+        first, length, stride, runs = pat
+        sc = torch.empty(runs * length, dtype=torch.int32, device="cuda")
+        fl = torch.empty(runs * length, dtype=torch.uint8, device="cuda")
+        w = 0 if name == "serial" else (8 if name.endswith("_w8") else warmup)
+
+        def call():
+            scn.scn_bounded_state_scores(hist, 0, n, n, px, shift, w, first, length, stride, runs, sc, fl,
+                                         stream=stream)
+        call()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        flags[name] = fl.cpu()
+        res[name] = {"ms": e0.elapsed_time(e1) / reps, "runs": runs, "warmup": w,
+                     "inputs_read": stencil.state_input_fraction(*pat, w, n)}
+    serial = flags["serial"][:n]
+    res["shards_1184"]["flags_equal_serial"] = float((flags["shards_1184"][:n] == serial).float().mean())
+    for name in ("every_24th", "every_24th_w8"):
+        res[name]["flags_equal_serial"] = float((flags[name] == serial[::24]).float().mean())
+    res["serial"]["cuts"] = int(serial.sum())
+    return {"workload": f"{n} stride-1 1080p histograms, shift {shift}", **res}
 
 
 def run_batched(args, scn, torch, stream):

@@ -357,6 +357,34 @@ scn_status scn_shot_scores_sliced(const uint32_t* d_hist, int64_t n, int64_t pix
 scn_status scn_window_scores(const uint32_t* d_hist, int64_t hist_first, int64_t hist_count, int64_t n, int32_t a,
                              int32_t b, int64_t pixel_count, const uint8_t* d_boundary, int64_t k0, int64_t k1,
                              uint64_t* d_score, uint8_t* d_flag, void* stream);
+/* Bounded-state shot score (Sec. 3.2, "Bounded state operations": an op may
+ * carry state from element to element, and before it produces element i it
+ * has processed at least the `warmup` elements before i).  The state is a
+ * reference histogram m.  The first element a run processes, and an element
+ * where a slice starts (d_boundary != 0; d_boundary may be NULL), set m to its
+ * histogram h and output score 0, flag 0.  Every other element outputs
+ *   score = sum over the 48 bins |h - m|,  flag = 2 * score > pixel_count,
+ * then sets m = h if flag (a cut restarts the reference) else
+ * m += floor((h - m) / 2^shift) (an exponential average of the shot so far);
+ * shift = 0 gives the plain two-frame score.
+ * Runs: run r (0 <= r < runs) has outputs [k0, k1) = [run_first + r*run_stride,
+ * + run_len) clipped to [0, n), processed on its own from max(0, k0 - warmup);
+ * element k of run r goes to d_score[r*run_len + k - k0] (device uint32) and
+ * d_flag[...]; slots of elements past n are not written.  One run of n
+ * outputs is the serial op; run_len == run_stride splits it into shards;
+ * run_len 1 produces sparse outputs, each after `warmup` elements.  Results
+ * depend on the runs chosen (as the paper allows for bounded state), and equal
+ * the serial op's where a run's warmup reaches back to a slice start or to 0.
+ * d_hist (device uint32 [hist_count][48], as scn_hist writes it: each channel
+ * sums to pixel_count) and d_boundary hold elements [hist_first, hist_first +
+ * hist_count), which must cover [max(0, run_first - warmup), end of the last
+ * run) (Sec. 4.2: warmup W is the footprint i - W .. i), else SCN_ERANGE.
+ * Errors: SCN_EINVAL (shift outside 0..30, warmup < 0, run_len < 1,
+ * run_stride < run_len, ...), SCN_ERANGE (pixel_count > 715827882). */
+scn_status scn_bounded_state_scores(const uint32_t* d_hist, int64_t hist_first, int64_t hist_count, int64_t n,
+                                   int64_t pixel_count, int32_t shift, int64_t warmup, int64_t run_first,
+                                   int64_t run_len, int64_t run_stride, int64_t runs, const uint8_t* d_boundary,
+                                   uint32_t* d_score, uint8_t* d_flag, void* stream);
 /* Montage of sequence elements (Sec. 5.2, film summaries: one frame from each
  * shot): tile i (row-major, `cols` tiles per row) shows element d_elem[i]
  * (device int32, m entries) of s, nearest-neighbour downsampled to tile_w x

@@ -207,6 +207,89 @@ __global__ void window_scores_kernel(const uint32_t* hist, const uint8_t* bounda
     }
 }
 
+// Bounded-state shot score, one warp per run of outputs.  Run r has outputs
+// [k0, k1) = [first + r*stride, first + r*stride + len) clipped to n, and
+// processes elements max(0, k0 - warmup) .. k1 - 1 in order (the warmup).  The
+// state is a reference histogram m (lane: bins lane and 32 + lane).  The first
+// processed element, and a slice start, set m = h and output (0, 0); every
+// other element outputs d = sum |h - m| and f = 2d > px, then sets m = h when f
+// (a cut) else m += (h - m) >> shift (floor).  Histograms are read a block of
+// kStateBlock elements ahead of the dependent chain.
+constexpr int kStateBlock = 4;
+constexpr int64_t kMaxStatePixels = 715827882;  // 6 * pixel_count < 2^32
+
+__device__ __forceinline__ void state_load(const uint32_t* hist, const uint8_t* boundary, int64_t hfirst, int64_t j,
+                                           int64_t k1, int lane, uint32_t (&h0)[kStateBlock],
+                                           uint32_t (&h1)[kStateBlock], uint32_t (&bd)[kStateBlock]) {
+#pragma unroll
+    for (int u = 0; u < kStateBlock; ++u) {
+        const int64_t e = j + u;
+        h0[u] = 0;
+        h1[u] = 0;
+        bd[u] = 0;
+        if (e < k1) {
+            const uint32_t* row = hist + (e - hfirst) * 48;
+            h0[u] = __ldg(row + lane);
+            if (lane < 16) h1[u] = __ldg(row + 32 + lane);
+            if (boundary) bd[u] = __ldg(boundary + (e - hfirst));
+        }
+    }
+}
+
+__global__ void bounded_state_kernel(const uint32_t* hist, const uint8_t* boundary, int64_t hfirst, int64_t n,
+                                     int64_t pixel_count, int shift, int64_t warmup, int64_t first, int64_t len,
+                                     int64_t stride, int64_t runs, uint32_t* score, uint8_t* flag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
+    if (r >= runs) return;
+    const int64_t k0 = first + r * stride;
+    if (k0 >= n) return;
+    const int64_t k1 = k0 + min(len, n - k0);
+    const int64_t j0 = max(static_cast<int64_t>(0), k0 - warmup);
+    const uint64_t px = static_cast<uint64_t>(pixel_count);
+    uint32_t* out_s = score + r * len;  // element k goes to slot r*len + (k - k0)
+    uint8_t* out_f = flag + r * len;
+    int32_t m0 = 0, m1 = 0;
+    uint32_t c0[kStateBlock], c1[kStateBlock], cb[kStateBlock];
+    state_load(hist, boundary, hfirst, j0, k1, lane, c0, c1, cb);
+    for (int64_t j = j0; j < k1; j += kStateBlock) {
+        uint32_t n0[kStateBlock], n1[kStateBlock], nb[kStateBlock];
+        state_load(hist, boundary, hfirst, j + kStateBlock, k1, lane, n0, n1, nb);
+#pragma unroll
+        for (int u = 0; u < kStateBlock; ++u) {
+            const int64_t e = j + u;
+            if (e >= k1) break;
+            const int32_t h0 = static_cast<int32_t>(c0[u]), h1 = static_cast<int32_t>(c1[u]);
+            uint32_t d = 0, f = 0;
+            if (e == j0 || cb[u] != 0) {
+                m0 = h0;
+                m1 = h1;
+            } else {
+                const int32_t x0 = h0 - m0, x1 = h1 - m1;  // x1 = 0 on lanes >= 16
+                d = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(abs(x0) + abs(x1)));
+                f = 2ull * d > px ? 1u : 0u;
+                if (f) {
+                    m0 = h0;
+                    m1 = h1;
+                } else {
+                    m0 += x0 >> shift;
+                    m1 += x1 >> shift;
+                }
+            }
+            if (lane == 0 && e >= k0) {
+                out_s[e - k0] = d;
+                out_f[e - k0] = static_cast<uint8_t>(f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kStateBlock; ++u) {
+            c0[u] = n0[u];
+            c1[u] = n1[u];
+            cb[u] = nb[u];
+        }
+    }
+}
+
 // Montage: tile i (row-major over `cols` tiles) shows sequence element elem[i],
 // nearest-neighbour downsampled: output pixel (x, y) of a tw x th tile takes
 // source pixel (floor((2x+1) W / (2 tw)), floor((2y+1) H / (2 th))) of the
@@ -345,6 +428,32 @@ scn_status scn_window_scores(const uint32_t* d_hist, int64_t hist_first, int64_t
     if (blocks > 0x7fffffff) return SCN_ERANGE;
     window_scores_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         d_hist, d_boundary, hist_first, n, a, b, pixel_count, k0, k1, d_score, d_flag);
+    SCN_CUDA_TRY(cudaGetLastError());
+    return SCN_OK;
+}
+
+scn_status scn_bounded_state_scores(const uint32_t* d_hist, int64_t hist_first, int64_t hist_count, int64_t n,
+                                   int64_t pixel_count, int32_t shift, int64_t warmup, int64_t run_first,
+                                   int64_t run_len, int64_t run_stride, int64_t runs, const uint8_t* d_boundary,
+                                   uint32_t* d_score, uint8_t* d_flag, void* stream) {
+    if (n < 0 || pixel_count < 0 || shift < 0 || shift > 30 || warmup < 0 || run_first < 0 || run_len < 1 ||
+        run_stride < run_len || runs < 0 || hist_first < 0 || hist_count < 0)
+        return SCN_EINVAL;
+    if (pixel_count > kMaxStatePixels) return SCN_ERANGE;
+    if (runs == 0 || run_first >= n) return SCN_OK;
+    if (!d_hist || !d_score || !d_flag) return SCN_EINVAL;
+    // the last run with outputs, and the dependency range of all runs (Sec. 4.2:
+    // a warmup of W is the footprint i - W .. i)
+    const int64_t r_last = std::min(runs - 1, (n - 1 - run_first) / run_stride);
+    const int64_t need0 = std::max<int64_t>(0, run_first - warmup);
+    const int64_t k_last = run_first + r_last * run_stride;  // < n
+    const int64_t need1 = k_last + std::min(run_len, n - k_last);
+    if (need0 < hist_first || need1 > hist_first + hist_count) return SCN_ERANGE;
+    const int64_t blocks = (r_last + 1 + 7) / 8;
+    if (blocks > 0x7fffffff) return SCN_ERANGE;
+    bounded_state_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        d_hist, d_boundary, hist_first, n, pixel_count, shift, warmup, run_first, run_len, run_stride, r_last + 1,
+        d_score, d_flag);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }

@@ -112,6 +112,8 @@ SIGNATURES = [
     ("scn_shot_scores_sliced", c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
     ("scn_montage", c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_vp, c_vp]),
     ("scn_window_scores", c_i32, [c_vp, c_i64, c_i64, c_i64, c_i32, c_i32, c_i64, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
+    ("scn_bounded_state_scores", c_i32, [c_vp, c_i64, c_i64, c_i64, c_i64, c_i32, c_i64, c_i64, c_i64, c_i64, c_i64,
+                                         c_vp, c_vp, c_vp, c_vp]),
 ]
 
 
@@ -492,3 +494,13 @@ def scn_window_scores(hist, hist_first: int, hist_count: int, n: int, a: int, b:
     """hist: CUDA tensor holding elements [hist_first, hist_first + hist_count) of the sequence."""
     _check(_lib.scn_window_scores(_ptr(hist), hist_first, hist_count, n, a, b, pixel_count, _ptr(boundary), k0, k1,
                                   _ptr(score), _ptr(flag), _stream(stream)), "scn_window_scores")
+
+
+def scn_bounded_state_scores(hist, hist_first: int, hist_count: int, n: int, pixel_count: int, shift: int,
+                             warmup: int, run_first: int, run_len: int, run_stride: int, runs: int, score, flag,
+                             boundary=None, stream=None) -> None:
+    """hist: CUDA tensor holding elements [hist_first, hist_first + hist_count); score/flag: one slot per
+    output of each run (run r, element k -> r*run_len + k - run start)."""
+    _check(_lib.scn_bounded_state_scores(_ptr(hist), hist_first, hist_count, n, pixel_count, shift, warmup,
+                                         run_first, run_len, run_stride, runs, _ptr(boundary), _ptr(score),
+                                         _ptr(flag), _stream(stream)), "scn_bounded_state_scores")

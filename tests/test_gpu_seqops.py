@@ -211,3 +211,127 @@ def test_window_scores_sharded_with_halos(scn):
     assert torch.equal(s, full_s[100:200]) and torch.equal(f, full_f[100:200])
     with pytest.raises(scn.ScnError):  # window wider than 64
         scn.scn_window_scores(d_hist, 0, n, n, -65, 0, px, 0, n, full_s, full_f)
+
+
+def _shot_hists(rng, n, px):
+    """Histograms with shot structure: per shot a random 16-bin distribution per channel,
+    per frame a multinomial draw of px pixels from it (each channel sums to px)."""
+    hist = np.empty((n, 48), np.int64)
+    k = 0
+    while k < n:
+        L = min(n - k, int(rng.integers(3, 90)))
+        for c in range(3):
+            p = rng.dirichlet(np.full(16, 0.6))
+            q = p * rng.uniform(0.85, 1.15, (L, 16))
+            q /= q.sum(1, keepdims=True)
+            hist[k:k + L, 16 * c:16 * c + 16] = [rng.multinomial(px, qq) for qq in q]
+        k += L
+    return hist
+
+
+def _state_run(scn, d_hist, n, px, shift, warmup, pat, d_bnd=None, hist_first=0, hist_count=None):
+    first, length, stride, runs = pat
+    slots = runs * length
+    s = torch.full((max(slots, 1),), -1, dtype=torch.int32, device="cuda")
+    f = torch.full((max(slots, 1),), 255, dtype=torch.uint8, device="cuda")
+    scn.scn_bounded_state_scores(d_hist, hist_first, n if hist_count is None else hist_count, n, px, shift, warmup,
+                                 first, length, stride, runs, s, f, boundary=d_bnd)
+    return s.cpu().numpy()[:slots].astype(np.int64) & 0xFFFFFFFF, f.cpu().numpy()[:slots]
+
+
+@pytest.mark.parametrize("shift,warmup,pat", [
+    (3, 0, (0, 1501, 1501, 1)),       # serial
+    (3, 24, (0, 94, 94, 16)),         # shards, the last one ragged
+    (2, 10, (0, 2, 2, 751)),          # 751 two-element shards
+    (2, 24, (0, 1, 24, 63)),          # sparse: every 24th output
+    (4, 3, (5, 7, 10, 150)),          # gaps between runs
+    (0, 1, (0, 50, 50, 31)),          # shift 0: the plain score
+    (30, 50, (11, 13, 13, 200)),      # runs past the end
+])
+@pytest.mark.parametrize("sliced", [False, True])
+def test_bounded_state_scores_match_oracle(scn, shift, warmup, pat, sliced):
+    rng = np.random.default_rng(shift * 1000 + warmup + 7 * sliced)
+    n, px = 1501, 320 * 180
+    hist = _shot_hists(rng, n, px)
+    bnd = (rng.random(n) < 0.02).astype(np.uint8) if sliced else None
+    d_hist = torch.from_numpy(hist.astype(np.int32)).cuda()
+    d_bnd = torch.from_numpy(bnd).cuda() if sliced else None
+    s, f = _state_run(scn, d_hist, n, px, shift, warmup, pat, d_bnd)
+    rs, rf = seqops.bounded_state_scores(hist, px, shift, warmup, *pat, boundary=bnd)
+    written = rs >= 0
+    assert np.array_equal(s[written], rs[written]) and np.array_equal(f[written], rf[written])
+    assert (s[~written] == 0xFFFFFFFF).all() and (f[~written] == 255).all()  # slots past n untouched
+    if shift == 0:
+        ps, pf = (seqops.sliced_scores(hist, bnd, px) if sliced else oracle_scores(hist, px))
+        for r in range(pat[3]):
+            k0 = pat[0] + r * pat[2]
+            for k in range(k0, min(k0 + pat[1], n)):
+                if k > 0 and (k > k0 or warmup > 0):
+                    assert s[r * pat[1] + k - k0] == ps[k]
+
+
+def oracle_scores(hist, px):
+    import oracle
+    return oracle.scores(hist.astype(np.uint32), px)
+
+
+def test_bounded_state_scores_edges_and_resident_slices(scn):
+    rng = np.random.default_rng(31)
+    n, px = 400, 64 * 36
+    hist = _shot_hists(rng, n, px)
+    d_hist = torch.from_numpy(hist.astype(np.int32)).cuda()
+    s0 = torch.zeros(4, dtype=torch.int32, device="cuda")
+    f0 = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    # nothing to do: no runs, an empty sequence, runs that start past the end
+    scn.scn_bounded_state_scores(d_hist, 0, n, n, px, 2, 5, 0, 4, 4, 0, s0, f0)
+    scn.scn_bounded_state_scores(d_hist, 0, 0, 0, px, 2, 5, 0, 4, 4, 1, s0, f0)
+    scn.scn_bounded_state_scores(d_hist, 0, n, n, px, 2, 5, n, 4, 4, 1, s0, f0)
+    assert not s0.any()
+    # one element: score 0, flag 0
+    s, f = _state_run(scn, d_hist[:1].clone(), 1, px, 2, 5, (0, 1, 1, 1))
+    assert s.tolist() == [0] and f.tolist() == [0]
+    # outputs [100, 200) with warmup 8 need elements [92, 200): a resident slice from 92 works, from 93 not
+    pat = (100, 100, 100, 1)
+    rs, rf = seqops.bounded_state_scores(hist, px, 2, 8, *pat)
+    s, f = _state_run(scn, d_hist[92:200].clone(), n, px, 2, 8, pat, hist_first=92, hist_count=108)
+    assert np.array_equal(s, rs[:100]) and np.array_equal(f, rf[:100])
+    with pytest.raises(scn.ScnError):
+        _state_run(scn, d_hist[93:200].clone(), n, px, 2, 8, pat, hist_first=93, hist_count=107)
+    with pytest.raises(scn.ScnError):
+        _state_run(scn, d_hist[92:199].clone(), n, px, 2, 8, pat, hist_first=92, hist_count=107)
+    for bad in [dict(shift=31), dict(shift=-1), dict(warmup=-1), dict(pat=(0, 0, 1, 1)), dict(pat=(0, 5, 4, 2)),
+                dict(px=715827883)]:
+        a = dict(shift=2, warmup=1, pat=(0, 10, 10, 1), px=px)
+        a.update(bad)
+        with pytest.raises(scn.ScnError):
+            _state_run(scn, d_hist, n, a["px"], a["shift"], a["warmup"], a["pat"])
+
+
+def test_bounded_state_scores_full_size_sharded(scn):
+    """200,000 elements as 1,184 shards (8 per SM) with warmup 32, and the serial run: the
+    serial run against the oracle in full, 40 sampled shards one by one; shards whose warmup
+    reaches a slice start agree with the serial run."""
+    from paper_1805_07339_b300 import stencil
+    rng = np.random.default_rng(32)
+    n, px = 200_000, 640 * 360
+    hist = _shot_hists(rng, n, px)
+    bnd = np.zeros(n, np.uint8)
+    bnd[rng.choice(n, 400, replace=False)] = 1
+    d_hist = torch.from_numpy(hist.astype(np.int32)).cuda()
+    d_bnd = torch.from_numpy(bnd).cuda()
+    serial, sflag = _state_run(scn, d_hist, n, px, 3, 0, (0, n, n, 1), d_bnd)
+    rs, rf = seqops.bounded_state_scores(hist, px, 3, 0, 0, n, n, 1, boundary=bnd)
+    assert np.array_equal(serial, rs) and np.array_equal(sflag, rf)
+    pat = stencil.state_shards(n, 1184)
+    s, f = _state_run(scn, d_hist, n, px, 3, 32, pat, d_bnd)
+    first, length, stride, runs = pat
+    for r in rng.choice(runs, 40, replace=False):
+        k0 = first + r * stride
+        k1 = min(k0 + length, n)
+        es, ef = seqops.bounded_state_run(hist, px, 3, max(0, k0 - 32), k0, k1, boundary=bnd)
+        assert s[r * length:r * length + k1 - k0].tolist() == es and f[r * length:r * length + k1 - k0].tolist() == ef
+    for r in range(runs):
+        k0 = first + r * stride
+        if k0 == 0 or bnd[max(0, k0 - 32):k0 + 1].any():
+            k1 = min(k0 + length, n)
+            assert np.array_equal(s[r * length:r * length + k1 - k0], serial[k0:k1])

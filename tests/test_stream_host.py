@@ -39,3 +39,21 @@ def test_plan_chunks():
         stream.plan_chunks(spec, max(need) - 1)
     v = spec[0]
     assert np.array_equal(stream.sampled_rows(v), np.union1d(v["stride"], v["gather"]))
+
+
+def test_state_run_patterns_and_input_sets():
+    """The bounded-state run patterns and their input sets against the oracle's brute-force set."""
+    from oracle import seqops
+    from paper_1805_07339_b300 import stencil
+    assert stencil.state_shards(10, 3) == (0, 4, 4, 3)
+    assert stencil.state_shards(0, 3)[3] == 0
+    assert stencil.state_sparse(100, 24) == (0, 1, 24, 5)
+    assert stencil.state_sparse(100, 24, 5) == (5, 1, 24, 4)
+    for n in (1, 7, 50, 301):
+        for pat in (stencil.state_shards(n, 1), stencil.state_shards(n, 4), stencil.state_shards(n, 64),
+                    stencil.state_sparse(n, 24), stencil.state_sparse(n, 5, 2), (3, 2, 7, 40)):
+            for w in (0, 1, 3, 30):
+                got = [i for a, b in stencil.state_inputs(*pat, w, n) for i in range(a, b)]
+                assert got == seqops.bounded_state_inputs(*pat, w, n), (n, pat, w)
+    # every 24th of 7200 outputs after 3 warmup elements: 4 inputs per output, 1 for output 0
+    assert stencil.state_input_fraction(*stencil.state_sparse(7200, 24), 3, 7200) == (299 * 4 + 1) / 7200
