@@ -414,10 +414,7 @@ constexpr int kFzE3Pitch = 8 * 16, kFzO3Pitch = 9 * 16;
 constexpr int kFzE3Plane = kFzA2Rows * kFzE3Pitch, kFzO3Plane = kFzA2Rows * kFzO3Pitch;
 constexpr int kFzA2Bytes = 4 * (kFzE3Plane + kFzO3Plane);
 constexpr int kFzG3 = kFzPairs * 5;
-// head scratch in region 0 after a2 (phases 2-4): pooled g, hidden v
 constexpr int kFzF1T = 24576;  // end of what layer-3 reads of region 0
-constexpr int kFzGs = kFzF1T;
-constexpr int kFzVs = kFzGs + kFzPairs * 32 * 4;
 // MMA descriptor table: conv1 2 per tile, conv2 9 per tile, conv3 18
 constexpr int kFzD1 = 0, kFzD2 = kFzD1 + 2 * kFzT1, kFzD3 = kFzD2 + 4 * 9, kFzNDesc = kFzD3 + 18;
 // shared-memory map (bytes)
@@ -430,20 +427,23 @@ constexpr int kFzBar = kFzDesc + kFzNDesc * 16;    // mbarriers, TMEM address
 constexpr int kFzNBar = kFzT1 + 8 + 3;  // conv1 tiles, conv2 tile x tap range, conv3 tap range
 constexpr int kFzReg0 = kFzBar + 256;              // X1, later a2 + head scratch
 constexpr int kFzReg0Bytes = 2 * kFzX1Plane;
-constexpr int kFzReg1 = kFzReg0 + kFzReg0Bytes;    // A1, later a3 (fp32) over its first plane
+constexpr int kFzReg1 = kFzReg0 + kFzReg0Bytes;    // A1
 constexpr int kFzReg1Bytes = 2 * kFzE2Plane + 2 * kFzO2Plane;
-constexpr int kFzSmem = kFzReg1 + kFzReg1Bytes;
-constexpr int kFzA3Pitch = 41;  // a3 as [pair][channel][position], odd pitch: conflict-free pooling
-constexpr int kFzG3Bytes = kFzPairs * 32 * kFzA3Pitch * 4;
+// head scratch, outside the activation regions so that the head of a batch runs
+// during the next batch's phases 0-2: per pair the 5 row sums of a3 (fp32 [5][32];
+// row 0 later holds the pooled g), then the FC2 partial sum of each of 4 warps
+constexpr int kFzPart = kFzReg1 + kFzReg1Bytes;
+constexpr int kFzWsum = kFzPart + kFzPairs * 5 * 32 * 4;
+constexpr int kFzSmem = kFzWsum + 4 * 4;
 static_assert(kFzNBar * 8 + 4 <= 256, "barrier area");
-static_assert(kFzG3Bytes <= kFzE2Plane, "a3 overlays the first a1 plane");
 static_assert(kFzSmem <= 115712, "two CTAs per SM");
 static_assert(kFzG1 >= 16 && kFzG2 >= 16, "every layer-1/2 tile lies inside the buffers");
 // every row the MMAs read lies inside its plane (layers 1, 2) or inside region 0 (layer 3)
 static_assert((kFzG1 - 1) / 4 + 1 < kFzX1Rows, "layer-1 reads");
 static_assert(2 * (kFzG2 - 1) + 2 < kFzA1Rows, "layer-2 reads");
 static_assert(4 * kFzE3Plane + 3 * kFzO3Plane + (2 * 15 + 2 + 1) * kFzO3Pitch <= kFzF1T, "layer-3 reads");
-static_assert(kFzA2Bytes <= kFzF1T && kFzVs + kFzPairs * 64 * 4 <= kFzReg0Bytes, "region 0 in phases 2-4");
+static_assert(kFzA2Bytes <= kFzF1T && kFzF1T <= kFzReg0Bytes, "region 0 in phases 2-3");
+static_assert(kFzPairs == 2, "the head's warp split (warp w: pair w / 2, units 32 (w % 2) ..) assumes two pairs");
 
 struct FusedArgs {
     const uint8_t* thumbs;
@@ -507,11 +507,10 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
     uint8_t* E1 = reg0 + kFzX1Plane;
     uint8_t* E3 = reg0;
     uint8_t* O3 = reg0 + 4 * kFzE3Plane;
-    float* gs = reinterpret_cast<float*>(reg0 + kFzGs);
-    float* vs = reinterpret_cast<float*>(reg0 + kFzVs);
+    float* part = reinterpret_cast<float*>(smem + kFzPart);  // [pair][5][32]; [pair][0][c] = g after step A
+    float* wsum = reinterpret_cast<float*>(smem + kFzWsum);  // [4]
     uint8_t* E2 = reg1;
     uint8_t* O2 = reg1 + 2 * kFzE2Plane;
-    float* a3 = reinterpret_cast<float*>(reg1);
     const uint32_t sbase = ptx::smem_u32(smem);
 
     // ---- once: weights in tensor-core layouts, biases, descriptors, zeroed A1, barriers, TMEM
@@ -604,12 +603,41 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
         pair_thumbs(blockIdx.x, 0, ip0, ic0);
         pair_thumbs(blockIdx.x, 1, ip1, ic1);
     }
+    // The head of a batch runs in three steps during the next batch's phases 0, 1 and 2
+    // (after the last batch, on its own): A pools a3 from its row sums (64 threads), B
+    // computes FC1 and each warp's share of FC2 (128 threads), C adds the shares.
+    auto head_a = [&]() {
+        if (tid < kFzPairs * 32) {
+            float* q = part + (tid >> 5) * 160 + (tid & 31);
+            q[0] = (q[0] + q[32] + q[64] + q[96] + q[128]) * (1.f / 40.f);
+        }
+    };
+    auto head_b = [&]() {
+        if (tid < kFzPairs * 64) {
+            const int p = tid >> 6, j = tid & 63;
+            const float* g = part + p * 160;
+            float v = bias[80 + j];
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c) v = fmaf(__ldg(a.f1t + c * 64 + j), g[c], v);
+            float zz = bias[144 + j] * fmaxf(v, 0.f);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
+            if (lane == 0) wsum[warp] = zz;
+        }
+    };
+    auto head_c = [&](int64_t hb) {
+        if (tid < kFzPairs) {
+            const int64_t b = hb * kFzPairs + tid;
+            if (b < a.pairs) a.logits[b] = wsum[2 * tid] + wsum[2 * tid + 1] + bias[208];
+        }
+    };
+    int64_t prev = -1;  // the batch whose head is pending
     uint32_t it = 0;
     for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x, ++it) {
         const uint32_t par = it & 1u;
         // ---- phase 0: layer-1 input planes, one warp per input row of a pair (lane = output
         //      column, so each store writes one contiguous 512-byte plane row); zero rows;
-        //      zero rows of the first A1 plane that a3 overwrote
+        //      head step A of the previous batch
         constexpr int kRowsPerWarp = kFzPairs * 36 / (kFzThreads / 32);
         static_assert(kRowsPerWarp * (kFzThreads / 32) == kFzPairs * 36, "rows split evenly over warps");
         uint32_t vps[kRowsPerWarp], vqs[kRowsPerWarp];
@@ -634,19 +662,13 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
             uint8_t* row = (iy & 1) ? O1 + (p * kFzR1 + ((iy + 1) >> 1)) * 512 : E1 + (p * kFzR1 + (iy >> 1)) * 512;
             *reinterpret_cast<uint4*>(row + lane * 16) = make_uint4(w0, w1, w2, 0u);
         }
-        for (int z = tid; z < 6 * 32 + kFzPairs * 16; z += kFzThreads) {
-            uint8_t* dst;
-            if (z < 6 * 32) {  // zero rows: O1 {0, 19, 38}, E1 {18, 37, 38}
-                const int which = z >> 5, ox = z & 31;
-                const int zr = which == 0 ? 0 : which == 1 ? kFzR1 : which == 2 ? 2 * kFzR1
-                             : which == 3 ? kFzR1 - 1 : which == 4 ? 2 * kFzR1 - 1 : 2 * kFzR1;
-                dst = (which < 3 ? O1 : E1) + zr * 512 + ox * 16;
-            } else {
-                const int y = z - 6 * 32;
-                dst = E2 + ((y >> 4) * kFzR2) * kFzE2Pitch + (y & 15) * 16;
-            }
-            *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+        for (int z = tid; z < 6 * 32; z += kFzThreads) {  // zero rows: O1 {0, 19, 38}, E1 {18, 37, 38}
+            const int which = z >> 5, ox = z & 31;
+            const int zr = which == 0 ? 0 : which == 1 ? kFzR1 : which == 2 ? 2 * kFzR1
+                         : which == 3 ? kFzR1 - 1 : which == 4 ? 2 * kFzR1 - 1 : 2 * kFzR1;
+            *reinterpret_cast<uint4*>((which < 3 ? O1 : E1) + zr * 512 + ox * 16) = make_uint4(0, 0, 0, 0);
         }
+        if (prev >= 0) head_a();
         fz_sync();
 
         // the next batch's thumbnail indices: loads in flight through phases 1-4
@@ -666,6 +688,7 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
             }
         }
         __syncwarp();
+        if (prev >= 0) head_b();  // FC1 of the previous batch while the tensor core runs conv1
         for (int t2 = half; t2 < kFzT1; t2 += 6) {
             // up to three tiles of this warp's parity per TMEM round trip (each tcgen05.ld
             // round trip costs hundreds of cycles; loads in flight together share it)
@@ -724,6 +747,7 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
             }
             *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
         }
+        if (prev >= 0) head_c(prev);
         for (int tt = half; tt < 4; tt += 2) {
             ok = fz_wait(bar + kFzT1 + 2 * tt, par, ok, a.status);
             ok = fz_wait(bar + kFzT1 + 2 * tt + 1, par, ok, a.status);
@@ -785,51 +809,41 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
                 for (int c = 0; c < 16; ++c)
                     acc[c] = __float_as_uint(__uint_as_float(u0[c]) + __uint_as_float(u1[c]) + __uint_as_float(u2[c]));
             }
+            // a3 (BF16-rounded) summed over the 8 positions of each output row: the 8 lanes
+            // of a group hold one row of one pair; groups past kFzG3 are dropped
             const int g = r >> 3;
-            if (g < kFzG3) {
-                // [pair][channel][position]: the lanes of one store write consecutive positions
-                const int p = g / 5, oy = g - 5 * p, pos = oy * 8 + (r & 7);
-                float* dst = a3 + (p * 32 + 16 * half) * kFzA3Pitch + pos;
+            if (4 * quad < kFzG3) {  // warps of quad 3 hold dropped groups only
                 const float* b3 = bias + 48 + 16 * half;
+                float v[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c)
-                    dst[c * kFzA3Pitch] =
-                        __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c]) + b3[c], 0.f)));
+                    v[c] = g < kFzG3 ? __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c]) + b3[c], 0.f)))
+                                     : 0.f;
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+                if (g < kFzG3 && (lane & 7) == 0) {
+                    const int p = g / 5, oy = g - 5 * p;
+                    float4* dst = reinterpret_cast<float4*>(part + (p * 5 + oy) * 32 + 16 * half);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
             }
         }
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-
-        // ---- phase 4: pooling (thread per pair and channel), FC 32->64 (thread per pair and
-        //      unit), FC 64->1 (warp per pair); the next batch's pair indices are fetched meanwhile
-        if (tid < kFzPairs * 32) {
-            const float* src = a3 + tid * kFzA3Pitch;  // pair tid / 32, channel tid % 32
-            float s = 0.f;
-            for (int pos = 0; pos < 40; ++pos) s += src[pos];
-            gs[tid] = s * (1.f / 40.f);
-        }
-        __syncthreads();
-        if (tid < kFzPairs * 64) {
-            const int p = tid >> 6, j = tid & 63;
-            const float* g = gs + p * 32;
-            float v = bias[80 + j];
-#pragma unroll 8
-            for (int c = 0; c < 32; ++c) v = fmaf(__ldg(a.f1t + c * 64 + j), g[c], v);
-            vs[tid] = v;
-        }
-        __syncthreads();
-        if (warp < kFzPairs) {
-            const int64_t b = batch * kFzPairs + warp;
-            if (b < a.pairs) {
-                const float* v = vs + warp * 64;
-                float zz = bias[144 + lane] * fmaxf(v[lane], 0.f) + bias[144 + lane + 32] * fmaxf(v[lane + 32], 0.f);
-                for (int o = 16; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
-                if (lane == 0) a.logits[b] = zz + bias[208];
-            }
-        }
-        __syncthreads();
+        prev = batch;
     }
+    if (prev >= 0) {  // the last batch's head
+        head_a();
+        __syncthreads();
+        head_b();
+        __syncthreads();
+        head_c(prev);
+    }
+
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
