@@ -8,8 +8,9 @@
 //   ly = sy - y0 (same for x); v = (1-ly)((1-lx)P00 + lx P01) + ly((1-lx)P10 + lx P11)
 //   out[c][oy][ox] = (v / 255 - mean[c]) / std[c]
 // on the BT.601 fixed-point RGB of each source pixel.  The source coordinate is
-// the rational ((2o+1)*S - O) / (2*O); floor and fraction come from exact
-// integer arithmetic so the weights carry a single fp32 rounding.
+// the rational ((2o+1)*S - O) / (2*O): its floor and the fraction's numerator
+// come from integer arithmetic, the horizontal step is exact in integers, and
+// only the vertical step and the normalisation round (in fp32).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -24,60 +25,88 @@ struct ResizeArgs {
     int W, H;
     const int32_t* slot;
     int oh, ow;
-    float scale[3], bias[3];  // out = v * scale + bias, scale = 1/(255 std), bias = -mean/std
-    float inv255;
-    float mean[3], istd[3];
+    float scale[3], bias[3];  // out = V * scale + bias: scale = 1/(255 std dx dy), bias = -mean/std
     float* out32;            // [n][3][oh][ow] FP32, or null
     __nv_bfloat16* out16;    // [n][3][oh][ow] BF16 (RNE of the FP32 value), or null
 };
 
-__device__ __forceinline__ void src_coord(int o, int S, int O, int& i0, int& i1, float& l) {
+// Source tap of output index o (size O) in a source of size S: first index i0
+// and weight numerator r of the second one, over the denominator 2 O.
+__device__ __forceinline__ void src_tap(int o, int S, int O, int& i0, int& r) {
     const int num = (2 * o + 1) * S - O;
     if (num <= 0) {
         i0 = 0;
-        l = 0.f;
+        r = 0;
     } else {
-        const int den = 2 * O;
-        i0 = num / den;
-        l = static_cast<float>(num - i0 * den) / static_cast<float>(den);
+        i0 = num / (2 * O);
+        r = num - i0 * (2 * O);
     }
-    i1 = min(i0 + 1, S - 1);
 }
 
-__device__ __forceinline__ void rgb_at(const uint8_t* f, int W, int H, int x, int y, int rgb[3]) {
-    const int Y = __ldg(f + static_cast<int64_t>(y) * W + x);
-    const uint8_t* uv = f + static_cast<int64_t>(W) * H + static_cast<int64_t>(y >> 1) * W + (x & ~1);
-    const int U = __ldg(uv), V = __ldg(uv + 1);
-    const int C = 298 * (Y - 16) + 128, D = U - 128, E = V - 128;
-    rgb[0] = min(max((C + 409 * E) >> 8, 0), 255);
-    rgb[1] = min(max((C - 100 * D - 208 * E) >> 8, 0), 255);
-    rgb[2] = min(max((C + 516 * D) >> 8, 0), 255);
+// BT.601 fixed-point RGB of luma Y with the chroma word uv (U in byte 0, V in byte 1)
+__device__ __forceinline__ void rgb601(int Y, uint32_t uv, int (&p)[3]) {
+    const int C = 298 * Y - 4640;  // 298 (Y - 16) + 128
+    const int D = static_cast<int>(uv & 0xFFu) - 128, E = static_cast<int>(uv >> 8) - 128;
+    p[0] = min(max((C + 409 * E) >> 8, 0), 255);
+    p[1] = min(max((C - 100 * D - 208 * E) >> 8, 0), 255);
+    p[2] = min(max((C + 516 * D) >> 8, 0), 255);
 }
+
+// v as fp32, exactly, for 0 <= v < 2^23: v in the mantissa of 2^23, minus 2^23
+__device__ __forceinline__ float small_to_float(int v) { return __int_as_float(v | 0x4B000000) - 8388608.f; }
+
+// One CTA per 32 x 32 output tile of one element: the tile's source columns and
+// rows are computed once into shared memory; thread (lane, warp) produces column
+// lane of rows warp, warp + 8, warp + 16, warp + 24.  With dx = 2 ow, dy = 2 oh:
+//   top = (dx - rx) P00 + rx P01, bottom = (dx - rx) P10 + rx P11   (exact integers < 2^23)
+//   V = (dy - ry) top + ry bottom = dx dy v,  out = V * scale + bias
+constexpr int kRzTile = 32;
 
 __global__ void __launch_bounds__(256) resize_kernel(ResizeArgs a) {
-    const int k = blockIdx.y;
-    const int npix = a.oh * a.ow;
+    __shared__ int2 tap[2 * kRzTile];  // columns, then rows: (first index, weight numerator)
+    const int k = blockIdx.z, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ox0 = blockIdx.x * kRzTile, oy0 = blockIdx.y * kRzTile;
+    if (tid < 2 * kRzTile) {
+        int i0, r;
+        if (tid < kRzTile)
+            src_tap(min(ox0 + tid, a.ow - 1), a.W, a.ow, i0, r);
+        else
+            src_tap(min(oy0 + tid - kRzTile, a.oh - 1), a.H, a.oh, i0, r);
+        tap[tid] = make_int2(i0, r);
+    }
+    __syncthreads();
+    const int ox = ox0 + lane;
+    if (ox >= a.ow) return;
     const uint8_t* f = a.nv12 + static_cast<int64_t>(a.slot[k]) * a.stride;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
-        const int oy = i / a.ow, ox = i - oy * a.ow;
-        int y0, y1, x0, x1;
-        float ly, lx;
-        src_coord(oy, a.H, a.oh, y0, y1, ly);
-        src_coord(ox, a.W, a.ow, x0, x1, lx);
+    const uint8_t* uvp = f + static_cast<int64_t>(a.W) * a.H;
+    const int x0 = tap[lane].x, x1 = min(x0 + 1, a.W - 1), rx = tap[lane].y;
+    const int cx0 = x0 & ~1, cx1 = x1 & ~1;
+    const int wx0 = 2 * a.ow - rx;
+    const int64_t npix = static_cast<int64_t>(a.oh) * a.ow;
+    const int64_t base = static_cast<int64_t>(k) * 3 * npix + ox;
+    for (int j = warp; j < kRzTile; j += 8) {
+        const int oy = oy0 + j;
+        if (oy >= a.oh) break;
+        const int y0 = tap[kRzTile + j].x, y1 = min(y0 + 1, a.H - 1), ry = tap[kRzTile + j].y;
+        const uint8_t* l0 = f + static_cast<int64_t>(y0) * a.W;
+        const uint8_t* l1 = f + static_cast<int64_t>(y1) * a.W;
+        const uint8_t* c0 = uvp + static_cast<int64_t>(y0 >> 1) * a.W;
+        const uint8_t* c1 = uvp + static_cast<int64_t>(y1 >> 1) * a.W;
         int p00[3], p01[3], p10[3], p11[3];
-        rgb_at(f, a.W, a.H, x0, y0, p00);
-        rgb_at(f, a.W, a.H, x1, y0, p01);
-        rgb_at(f, a.W, a.H, x0, y1, p10);
-        rgb_at(f, a.W, a.H, x1, y1, p11);
+        rgb601(__ldg(l0 + x0), __ldg(reinterpret_cast<const uint16_t*>(c0 + cx0)), p00);
+        rgb601(__ldg(l0 + x1), __ldg(reinterpret_cast<const uint16_t*>(c0 + cx1)), p01);
+        rgb601(__ldg(l1 + x0), __ldg(reinterpret_cast<const uint16_t*>(c1 + cx0)), p10);
+        rgb601(__ldg(l1 + x1), __ldg(reinterpret_cast<const uint16_t*>(c1 + cx1)), p11);
+        const float wy0 = static_cast<float>(2 * a.oh - ry), wy1 = static_cast<float>(ry);
+        const int64_t o = base + static_cast<int64_t>(oy) * a.ow;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float top = (1.f - lx) * static_cast<float>(p00[c]) + lx * static_cast<float>(p01[c]);
-            const float bot = (1.f - lx) * static_cast<float>(p10[c]) + lx * static_cast<float>(p11[c]);
-            const float v = (1.f - ly) * top + ly * bot;
-            const float o = (v * a.inv255 - a.mean[c]) * a.istd[c];
-            const int64_t idx = (static_cast<int64_t>(k) * 3 + c) * npix + i;
-            if (a.out32) a.out32[idx] = o;
-            if (a.out16) a.out16[idx] = __float2bfloat16_rn(o);
+            const int top = wx0 * p00[c] + rx * p01[c];
+            const int bot = wx0 * p10[c] + rx * p11[c];
+            const float V = fmaf(wy0, small_to_float(top), wy1 * small_to_float(bot));
+            const float out = fmaf(V, a.scale[c], a.bias[c]);
+            if (a.out32) a.out32[o + c * npix] = out;
+            if (a.out16) a.out16[o + c * npix] = __float2bfloat16_rn(out);
         }
     }
 }
@@ -105,7 +134,7 @@ scn_status launch_resize(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean
     for (int c = 0; c < 3; ++c)
         if (!(h_std[c] != 0.f)) return SCN_EINVAL;
     if (s->n == 0) return SCN_OK;
-    if (s->n > 65535) return SCN_ERANGE;  // one grid row per element
+    if (s->n > 65535) return SCN_ERANGE;  // one grid z index per element
     ResizeArgs a;
     a.nv12 = s->table->d_nv12;
     a.stride = s->table->frame_stride;
@@ -114,16 +143,14 @@ scn_status launch_resize(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean
     a.slot = s->d_slot;
     a.oh = oh;
     a.ow = ow;
-    a.inv255 = 1.f / 255.f;
+    const double dxdy = 4.0 * static_cast<double>(oh) * static_cast<double>(ow);
     for (int c = 0; c < 3; ++c) {
-        a.mean[c] = h_mean[c];
-        a.istd[c] = 1.f / h_std[c];
+        a.scale[c] = static_cast<float>(1.0 / (255.0 * static_cast<double>(h_std[c]) * dxdy));
+        a.bias[c] = static_cast<float>(-static_cast<double>(h_mean[c]) / static_cast<double>(h_std[c]));
     }
     a.out32 = out32;
     a.out16 = out16;
-    const int npix = oh * ow;
-    const int bx = std::min((npix + 255) / 256, 1024);
-    dim3 grid(bx, static_cast<unsigned>(s->n));
+    dim3 grid((ow + kRzTile - 1) / kRzTile, (oh + kRzTile - 1) / kRzTile, static_cast<unsigned>(s->n));
     resize_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(a);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
