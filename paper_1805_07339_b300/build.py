@@ -12,8 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libscn.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-shared", "-cudart", "shared",
-         "--expt-relaxed-constexpr"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 
 
 def sources() -> list[str]:
@@ -32,11 +31,32 @@ def stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps())
 
 
+def _compile(src: str, obj: str, extra: list[str], verbose: bool) -> None:
+    cmd = [NVCC, *ARCH, *FLAGS, *extra, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.check_call(cmd)
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+    """Each source is compiled to its own object (in parallel; the sources are
+    separate translation units either way), then one link makes libscn.so."""
     if not (force or stale()):
         return LIB
-    cmd = [NVCC, *ARCH, *FLAGS, *(extra or []), "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp",
-           *sources()]
+    from concurrent.futures import ThreadPoolExecutor
+    extra = extra or []
+    objdir = os.path.join(ROOT, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    objs = [os.path.join(objdir, os.path.basename(src)[:-3] + ".o") for src in sources()]
+    # an object is rebuilt when forced, or when its source, a header or this script is newer
+    shared = [p for p in deps() if not p.endswith(".cu")]
+    todo = [(src, obj) for src, obj in zip(sources(), objs)
+            if force or extra or not os.path.exists(obj)
+            or any(os.path.getmtime(p) > os.path.getmtime(obj) for p in [src, *shared])]
+    with ThreadPoolExecutor(max_workers=max(1, min(len(objs), os.cpu_count() or 1))) as pool:
+        for f in [pool.submit(_compile, src, obj, extra, verbose) for src, obj in todo]:
+            f.result()
+    cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *objs]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd)
