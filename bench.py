@@ -345,6 +345,7 @@ def main():
                 "frac": dom["GB_per_s"] / peak, "traffic": profiled_traffic(dom["frames"]), "peak_source": peak_kind,
                 "kernel": "hist_kernel (scn_hist_scores, stride-1, 7200 frames)",
                 "alg_bytes_per_launch": dom["frames"] * ALG_BYTES_PER_FRAME}
+    roofline["binding_unit"] = binding_unit(scn, torch, np, dom, W * H, clk, stream)
 
     # ---- the bounded-state shot score over the stride-1 histograms: serial vs shards with warmup
     state = None
@@ -441,6 +442,27 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def binding_unit(scn, torch, np, dom: dict, px_per_frame: int, clk: dict, stream, iters: int = 4096, reps: int = 5):
+    """The fused hist kernel's rate of shared-memory reductions (three per pixel, one
+    warp-wide wavefront per 32 pixel-channels) per SM clock, against the ceiling the
+    probe measures for the same reductions in the same table layout."""
+    sms = scn.scn_device_sm_count()
+    cyc = torch.zeros(sms, dtype=torch.int64, device="cuda")
+    peak = 0.0
+    for _ in range(reps):
+        scn.scn_probe_shared_reductions(iters, sms, cyc, stream)
+        torch.cuda.synchronize()
+        peak = max(peak, 20 * 8 * iters / float(np.median(cyc.cpu().numpy())))
+    mhz, src = clk.get("sm_mhz"), "median SM clock sampled during the timed region"
+    if not mhz:
+        mhz, src = measured_peaks().get("sm_max_mhz") or 2032.0, "maximum SM clock (no samples)"
+    warp_reds = 3 * px_per_frame * dom["frames"] / 32
+    achieved = warp_reds / (sms * (dom["ms"] / 1000) * mhz * 1e6)
+    return {"unit": "warp-wide shared-memory reductions per SM clock", "achieved": achieved, "peak": peak,
+            "frac": achieved / peak, "reductions_per_pixel": 3, "sm_mhz": mhz, "clock_source": src,
+            "probe": f"scn_probe_shared_reductions: {sms} CTAs x 20 warps x {8 * iters} reductions, best of {reps}"}
 
 
 def run_bounded_state(scn, torch, hist, px, stream, shift=3, warmup=24, reps=20):
