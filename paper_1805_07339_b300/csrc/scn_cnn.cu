@@ -617,8 +617,11 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
             const int p = tid >> 6, j = tid & 63;
             const float* g = part + p * 160;
             float v = bias[80 + j];
-#pragma unroll 8
-            for (int c = 0; c < 32; ++c) v = fmaf(__ldg(a.f1t + c * 64 + j), g[c], v);
+            float f[32];  // every load in flight before the first fma
+#pragma unroll
+            for (int c = 0; c < 32; ++c) f[c] = __ldg(a.f1t + c * 64 + j);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v = fmaf(f[c], g[c], v);
             float zz = bias[144 + j] * fmaxf(v, 0.f);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
