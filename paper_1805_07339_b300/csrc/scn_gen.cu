@@ -86,71 +86,85 @@ __device__ __forceinline__ const scn_shot* shot_of(const scn_shot* shots, int ns
     return shots + lo;
 }
 
-__global__ void __launch_bounds__(256) gen_kernel(GenArgs a) {
-    const int vecs = a.W / 16;
-    const int rows = a.H + a.H / 2;
-    const int64_t per_frame = static_cast<int64_t>(rows) * vecs;
-    const int64_t total = per_frame * a.count;
-    for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < total;
-         w += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t k = w / per_frame;
-        const int64_t r = w - k * per_frame;
-        const int row = static_cast<int>(r / vecs);
-        const int vec = static_cast<int>(r - static_cast<int64_t>(row) * vecs);
-        const int64_t f = a.frames ? a.frames[k] : a.first + k;
-        const scn_shot* sh = shot_of(a.shots, a.nshots, f);
-        const int dt = static_cast<int>(f - sh->start);
-        uint8_t b[16];
-        // Along a row the sample index q steps by 1, so the counter s_pix + (2q+1) kGolden
-        // steps by 2 kGolden, and floor(gx (x - dt) / W) is kept as quotient and remainder.
-        if (row < a.H) {
-            const int y = row;
-            const int x0 = vec * 16;
-            const int base = sh->base[0] + floordiv_pos(sh->gy[0] * y, a.H);
-            const uint64_t q0 = (static_cast<uint64_t>(f) * 3 * a.H + y) * a.W + x0;
-            uint64_t c = a.s_pix + (2 * q0 + 1) * kGolden;
-            FloorStep rx;
-            rx.init(sh->gx[0] * (x0 - dt), a.W);
-            const int gx = sh->gx[0];
+// One 16-byte vector (16 luma samples of one row, or 8 U/V pairs of one chroma
+// row) of frame f, shot fields sh.  Along a row the sample index q steps by 1, so
+// the counter s_pix + (2q+1) kGolden steps by 2 kGolden, and floor(gx (x - dt) / W)
+// is kept as quotient and remainder.
+__device__ __forceinline__ uint4 gen_vector(const GenArgs& a, int64_t f, const scn_shot& sh, int row, int vec) {
+    const int dt = static_cast<int>(f - sh.start);
+    uint8_t b[16];
+    if (row < a.H) {
+        const int y = row;
+        const int x0 = vec * 16;
+        const int base = sh.base[0] + floordiv_pos(sh.gy[0] * y, a.H);
+        const uint64_t q0 = (static_cast<uint64_t>(f) * 3 * a.H + y) * a.W + x0;
+        uint64_t c = a.s_pix + (2 * q0 + 1) * kGolden;
+        FloorStep rx;
+        rx.init(sh.gx[0] * (x0 - dt), a.W);
+        const int gx = sh.gx[0];
 #pragma unroll 4
-            for (int i = 0; i < 16; ++i) {
-                const int v = base + rx.q + noise_from_counter(c);
-                b[i] = static_cast<uint8_t>(min(max(v, 16), 235));
-                c += 2 * kGolden;
-                rx.step(gx, a.W);
-            }
-        } else {
-            const int cy = row - a.H;
-            const int Wc = a.W / 2, Hc = a.H / 2;
-            const int cx0 = vec * 8;
-            uint64_t c[2];
-            FloorStep rx[2];
-            int base[2], gx2[2];
+        for (int i = 0; i < 16; ++i) {
+            const int v = base + rx.q + noise_from_counter(c);
+            b[i] = static_cast<uint8_t>(min(max(v, 16), 235));
+            c += 2 * kGolden;
+            rx.step(gx, a.W);
+        }
+    } else {
+        const int cy = row - a.H;
+        const int Wc = a.W / 2, Hc = a.H / 2;
+        const int cx0 = vec * 8;
+        uint64_t c[2];
+        FloorStep rx[2];
+        int base[2], gx2[2];
 #pragma unroll
-            for (int pl = 1; pl <= 2; ++pl) {
-                const uint64_t q0 = ((static_cast<uint64_t>(f) * 3 + pl) * Hc + cy) * Wc + cx0;
-                c[pl - 1] = a.s_pix + (2 * q0 + 1) * kGolden;
-                rx[pl - 1].init(sh->gx[pl] * (2 * cx0 - dt), a.W);
-                base[pl - 1] = sh->base[pl] + floordiv_pos(sh->gy[pl] * (2 * cy), a.H);
-                gx2[pl - 1] = 2 * sh->gx[pl];
-            }
+        for (int pl = 1; pl <= 2; ++pl) {
+            const uint64_t q0 = ((static_cast<uint64_t>(f) * 3 + pl) * Hc + cy) * Wc + cx0;
+            c[pl - 1] = a.s_pix + (2 * q0 + 1) * kGolden;
+            rx[pl - 1].init(sh.gx[pl] * (2 * cx0 - dt), a.W);
+            base[pl - 1] = sh.base[pl] + floordiv_pos(sh.gy[pl] * (2 * cy), a.H);
+            gx2[pl - 1] = 2 * sh.gx[pl];
+        }
 #pragma unroll 2
-            for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 8; ++j) {
 #pragma unroll
-                for (int pl = 0; pl < 2; ++pl) {
-                    const int v = base[pl] + rx[pl].q + noise_from_counter(c[pl]);
-                    b[2 * j + pl] = static_cast<uint8_t>(min(max(v, 16), 240));
-                    c[pl] += 2 * kGolden;
-                    rx[pl].step(gx2[pl], a.W);
-                }
+            for (int pl = 0; pl < 2; ++pl) {
+                const int v = base[pl] + rx[pl].q + noise_from_counter(c[pl]);
+                b[2 * j + pl] = static_cast<uint8_t>(min(max(v, 16), 240));
+                c[pl] += 2 * kGolden;
+                rx[pl].step(gx2[pl], a.W);
             }
         }
-        uint4 o;
-        o.x = b[0] | (b[1] << 8) | (b[2] << 16) | (static_cast<unsigned>(b[3]) << 24);
-        o.y = b[4] | (b[5] << 8) | (b[6] << 16) | (static_cast<unsigned>(b[7]) << 24);
-        o.z = b[8] | (b[9] << 8) | (b[10] << 16) | (static_cast<unsigned>(b[11]) << 24);
-        o.w = b[12] | (b[13] << 8) | (b[14] << 16) | (static_cast<unsigned>(b[15]) << 24);
-        *reinterpret_cast<uint4*>(a.out + k * a.stride + static_cast<int64_t>(row) * a.W + vec * 16) = o;
+    }
+    uint4 o;
+    o.x = b[0] | (b[1] << 8) | (b[2] << 16) | (static_cast<unsigned>(b[3]) << 24);
+    o.y = b[4] | (b[5] << 8) | (b[6] << 16) | (static_cast<unsigned>(b[7]) << 24);
+    o.z = b[8] | (b[9] << 8) | (b[10] << 16) | (static_cast<unsigned>(b[11]) << 24);
+    o.w = b[12] | (b[13] << 8) | (b[14] << 16) | (static_cast<unsigned>(b[15]) << 24);
+    return o;
+}
+
+constexpr int kGenThreads = 256;
+constexpr int kGenVecsPerThread = 4;  // vectors of one frame per thread (about)
+
+// blockIdx.y walks the frames, blockIdx.x spans one frame's vectors: the frame's
+// shot is found once per block (one thread) and read from shared memory, and the
+// vector index within a frame stays in 32 bits (rows x W/16 < 2^31, checked on the host).
+__global__ void __launch_bounds__(kGenThreads) gen_kernel(GenArgs a) {
+    __shared__ scn_shot s_shot;
+    const int vecs = a.W / 16;
+    const int per_frame = (a.H + a.H / 2) * vecs;
+    for (int64_t k = blockIdx.y; k < a.count; k += gridDim.y) {
+        const int64_t f = a.frames ? a.frames[k] : a.first + k;
+        __syncthreads();  // the previous frame's readers are done with s_shot
+        if (threadIdx.x == 0) s_shot = *shot_of(a.shots, a.nshots, f);
+        __syncthreads();
+        const scn_shot sh = s_shot;
+        uint8_t* out = a.out + k * a.stride;
+        for (int r = blockIdx.x * kGenThreads + threadIdx.x; r < per_frame; r += gridDim.x * kGenThreads) {
+            const int row = r / vecs;
+            const int vec = r - row * vecs;
+            *reinterpret_cast<uint4*>(out + static_cast<int64_t>(row) * a.W + vec * 16) = gen_vector(a, f, sh, row, vec);
+        }
     }
 }
 
@@ -181,9 +195,11 @@ scn_status launch_gen(const scn_video* v, const int64_t* d_frames, int64_t first
     a.out = d_out;
     const int sms = device_sm_count();
     if (sms <= 0) return SCN_EUNSUPPORTED;
-    const int64_t work = (static_cast<int64_t>(a.H) * 3 / 2) * (a.W / 16) * count;
-    const int64_t blocks = std::min<int64_t>((work + 255) / 256, static_cast<int64_t>(sms) * 16);
-    gen_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    const int64_t per_frame = (static_cast<int64_t>(a.H) + a.H / 2) * (a.W / 16);
+    if (per_frame > 0x7fffffff) return SCN_ERANGE;
+    const int64_t bx = (per_frame + kGenThreads * kGenVecsPerThread - 1) / (kGenThreads * kGenVecsPerThread);
+    const dim3 grid(static_cast<unsigned>(bx), static_cast<unsigned>(std::min<int64_t>(count, 65535)));
+    gen_kernel<<<grid, kGenThreads, 0, static_cast<cudaStream_t>(stream)>>>(a);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }
