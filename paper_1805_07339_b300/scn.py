@@ -10,6 +10,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 from . import build as _build
 
 c_i32, c_i64, c_u64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
@@ -151,9 +153,13 @@ def _stream(stream) -> int | None:
 
 
 def _i64_array(values):
-    vals = [int(v) for v in values]
-    arr = (c_i64 * max(len(vals), 1))(*vals)
-    return arr, len(vals)
+    """values (list, tuple or array of ints) as one contiguous int64 buffer:
+    (pointer, count, owner); the owner must outlive the call that reads the pointer."""
+    arr = np.ascontiguousarray(values, dtype=np.int64).reshape(-1)
+    n = int(arr.size)
+    if n == 0:
+        arr = np.zeros(1, dtype=np.int64)
+    return arr.ctypes.data_as(ctypes.POINTER(c_i64)), n, arr
 
 
 def _ptr(t) -> int | None:
@@ -227,12 +233,13 @@ def scn_table_create(nv12, width: int, height: int, num_frames: int, frame_strid
     """nv12: a CUDA uint8 tensor (or pass d_nv12 as a raw device address)."""
     if frame_stride is None:
         frame_stride = width * height * 3 // 2
-    rows_arr, nrows = _i64_array(rows) if rows is not None else (None, 0)
-    kf_arr, nkf = _i64_array(keyframes) if keyframes is not None else (None, 0)
+    rows_arr, nrows, rows_keep = _i64_array(rows) if rows is not None else (None, 0, None)
+    kf_arr, nkf, kf_keep = _i64_array(keyframes) if keyframes is not None else (None, 0, None)
     d = scn_table_desc(width, height, num_frames, frame_stride, d_nv12 if d_nv12 is not None else _ptr(nv12),
                        rows_arr, nrows, kf_arr, nkf)
     h = c_vp()
     _check(_lib.scn_table_create(ctypes.byref(d), ctypes.byref(h)), "scn_table_create")
+    del rows_keep, kf_keep  # the library copied the lists
     return h.value
 
 
@@ -242,10 +249,10 @@ def scn_table_destroy(t: int) -> None:
 
 def _spec(kind: int, start: int = 0, stop: int = 0, step: int = 1, indices=None):
     if indices is not None:
-        arr, n = _i64_array(indices)
+        arr, n, keep = _i64_array(indices)
     else:
-        arr, n = None, 0
-    return scn_sample_spec(kind, start, stop, step, arr, n), arr
+        arr, n, keep = None, 0, None
+    return scn_sample_spec(kind, start, stop, step, arr, n), keep
 
 
 def scn_sample_indices(t: int, kind: int, start: int = 0, stop: int = 0, step: int = 1, indices=None) -> list[int]:

@@ -28,11 +28,13 @@ def sampled_rows(v: dict) -> np.ndarray:
     return np.union1d(v["stride"], v["gather"]).astype(np.int64)
 
 
-def plan_chunks(spec: list[dict], chunk_bytes: int) -> list[list[int]]:
-    """Consecutive videos grouped so that each group's sampled rows fit chunk_bytes."""
+def plan_chunks(spec: list[dict], chunk_bytes: int, rows_of: list | None = None) -> list[list[int]]:
+    """Consecutive videos grouped so that each group's sampled rows fit chunk_bytes
+    (rows_of: each video's sampled rows, when the caller has them already)."""
     chunks, cur, used = [], [], 0
     for i, v in enumerate(spec):
-        need = len(sampled_rows(v)) * (v["width"] * v["height"] * 3 // 2)
+        nrows = len(rows_of[i]) if rows_of is not None else len(sampled_rows(v))
+        need = nrows * (v["width"] * v["height"] * 3 // 2)
         if need > chunk_bytes:
             raise ValueError(f"video {v['video_id']} needs {need} bytes, more than a chunk")
         if cur and used + need > chunk_bytes:
@@ -79,15 +81,15 @@ def run_stream(torch, spec: list[dict], chunk_bytes: int = 4 << 30, tune: dict |
     if any(v["width"] != W or v["height"] != H for v in spec):
         raise ValueError("one frame size per stream")
     fb = W * H * 3 // 2
-    chunks = plan_chunks(spec, chunk_bytes)
+    # every video's row list, computed once and uploaded once (a per-video copy from
+    # pageable memory could make the host wait for the stream)
+    rows_of = [sampled_rows(v) for v in spec]
+    chunks = plan_chunks(spec, chunk_bytes, rows_of)
     nbuf = 2 if len(chunks) > 1 else 1
-    cap = max(sum(len(sampled_rows(spec[i])) for i in c) for c in chunks) * fb
+    cap = max(sum(len(rows_of[i]) for i in c) for c in chunks) * fb
     bufs = [torch.empty(cap, dtype=torch.uint8, device="cuda") for _ in range(nbuf)]
     st = torch.cuda.Stream()
     keep_hist = set(keep_hist)
-    # every video's row list, uploaded once (a per-video copy from pageable memory
-    # could make the host wait for the stream)
-    rows_of = [sampled_rows(v) for v in spec]
     row_off = np.concatenate([[0], np.cumsum([len(r) for r in rows_of])])
     d_rows_all = torch.from_numpy(np.concatenate(rows_of)).pin_memory().to("cuda")
     res = StreamResult()
