@@ -100,7 +100,8 @@ scn_status scn_video_shots(const scn_video* v, scn_shot* h_out, int64_t cap, int
 scn_status scn_video_keyframes(const scn_video* v, int64_t* h_out, int64_t cap, int64_t* n);
 /* Generate frames first_frame .. first_frame+count-1 into d_out, frame k at
  * d_out + k*frame_stride (frame_stride >= W*H*3/2, % 16 == 0; d_out 16-byte
- * aligned).  Asynchronous on stream. */
+ * aligned, else SCN_EINVAL; frames outside the video, or a frame of 2^31 or
+ * more 16-byte vectors: SCN_ERANGE).  Asynchronous on stream. */
 scn_status scn_generate(const scn_video* v, uint8_t* d_out, int64_t first_frame, int64_t count,
                         int64_t frame_stride, void* stream);
 /* Sparse materialisation: generate frame d_frames[k] (device int64 array of n
