@@ -26,6 +26,12 @@
  *  - A sequence carries device scratch (completion counters and cross-CTA
  *    partial histograms, left zeroed by every call); two calls on the same
  *    sequence must not overlap on the GPU (use one stream per sequence).
+ *  - Object creation (scn_video_create, scn_sample, scn_plan_create) returns
+ *    once the object's device memory is filled, but does not wait for kernels
+ *    already running on other streams: that memory comes from a library pool
+ *    (grown ahead in large steps, kept until the process exits) and is filled
+ *    by copies on a library stream.  *_destroy first waits for the device, as
+ *    cudaFree does, so a sequence may be destroyed right after its last call.
  *  - Layouts: NV12 frame = W*H luma bytes then H/2 rows of W interleaved U,V
  *    bytes; histogram = uint32 [n][3][16] (R, G, B; bin = value >> 4);
  *    score = uint32 [n]; flag = uint8 [n]; resize output = [n][3][oh][ow].
@@ -88,8 +94,8 @@ typedef struct scn_video scn_video;
  * SCN_EINVAL for bad params. */
 scn_status scn_gen_shots(const scn_gen_params* params, scn_shot* h_out, int64_t cap, int64_t* n);
 
-/* Build the shot table on the host and upload it.  Errors: SCN_EINVAL (bad
- * params), SCN_ECUDA. */
+/* Build the shot table on the host and upload it (done on return; no wait for
+ * running kernels).  Errors: SCN_EINVAL (bad params), SCN_ENOMEM, SCN_ECUDA. */
 scn_status scn_video_create(const scn_gen_params* params, scn_video** out);
 scn_status scn_video_destroy(scn_video* v);
 /* Number of shots; copy of the first min(cap, n) shots into h_out. */
@@ -153,8 +159,9 @@ typedef struct {
 scn_status scn_sample_indices(const scn_table* t, const scn_sample_spec* spec, int64_t* h_out,
                               int64_t cap, int64_t* n);
 /* Create a sequence: the selected rows' storage slots uploaded to the device
- * plus the sequence's scratch (allocated here with cudaMalloc, freed by
- * scn_seq_destroy).  Synchronous. */
+ * plus the sequence's zeroed scratch (about 204 bytes per element, from the
+ * library's object pool; freed by scn_seq_destroy).  Returns once both are on
+ * the device; does not wait for running kernels. */
 scn_status scn_sample(const scn_table* t, const scn_sample_spec* spec, scn_seq** out);
 scn_status scn_seq_length(const scn_seq* s, int64_t* n);
 scn_status scn_seq_destroy(scn_seq* s);
@@ -222,7 +229,8 @@ typedef struct scn_plan scn_plan;
 
 /* Build a plan over nseq distinct sequences with their outputs (device,
  * caller-owned; entry i as in scn_hist_scores for seqs[i]).  tune may be NULL
- * (automatic shapes).  Uploads the job and item lists (synchronous).  The
+ * (automatic shapes).  Uploads the job and item lists (done on return; no wait
+ * for running kernels).  The
  * sequences' scratch is used by the plan's launches: do not run a sequence
  * and a plan containing it concurrently.  Errors: SCN_EINVAL (NULL entries,
  * repeated sequence, misaligned outputs), SCN_ECUDA. */

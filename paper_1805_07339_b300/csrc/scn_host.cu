@@ -181,13 +181,16 @@ scn_status scn_video_create(const scn_gen_params* params, scn_video** out) {
         return SCN_EINVAL;
     }
     const size_t bytes = v->shots.size() * sizeof(scn_shot);
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&v->d_shots), bytes);
-    if (e == cudaSuccess) e = cudaMemcpy(v->d_shots, v->shots.data(), bytes, cudaMemcpyHostToDevice);
+    void* d = nullptr;
+    cudaError_t e = obj_alloc(&d, bytes);
+    v->d_shots = static_cast<scn_shot*>(d);
+    if (e == cudaSuccess) e = obj_upload(v->d_shots, v->shots.data(), bytes);
+    if (e == cudaSuccess) e = obj_finish();
     if (e != cudaSuccess) {
         set_cuda_error(e);
-        if (v->d_shots) cudaFree(v->d_shots);
+        obj_free(v->d_shots);
         delete v;
-        return SCN_ECUDA;
+        return e == cudaErrorMemoryAllocation ? SCN_ENOMEM : SCN_ECUDA;
     }
     *out = v;
     return SCN_OK;
@@ -195,7 +198,7 @@ scn_status scn_video_create(const scn_gen_params* params, scn_video** out) {
 
 scn_status scn_video_destroy(scn_video* v) {
     if (!v) return SCN_EINVAL;
-    if (v->d_shots) cudaFree(v->d_shots);
+    obj_free(v->d_shots);
     delete v;
     return SCN_OK;
 }
@@ -352,7 +355,7 @@ scn_status scn_sample(const scn_table* t, const scn_sample_spec* spec, scn_seq**
     const size_t b_slot = up(n * 4), b_done = up(n * 4), b_pair = up(n * 4);
     const size_t b_part = up(n * 48 * 4), b_stat = 256;
     const size_t total = b_slot + b_done + b_pair + b_part + b_stat;
-    cudaError_t e = cudaMalloc(&s->d_block, total);
+    cudaError_t e = obj_alloc(&s->d_block, total);
     if (e != cudaSuccess) {
         set_cuda_error(e);
         delete s;
@@ -365,12 +368,12 @@ scn_status scn_sample(const scn_table* t, const scn_sample_spec* spec, scn_seq**
     s->d_partial = reinterpret_cast<uint32_t*>(p + b_slot + b_done + b_pair);
     s->d_status = reinterpret_cast<int*>(p + b_slot + b_done + b_pair + b_part);
     s->d_queue = reinterpret_cast<uint32_t*>(p + b_slot + b_done + b_pair + b_part + 64);
-    e = cudaMemset(s->d_block, 0, total);
-    if (e == cudaSuccess && s->n > 0)
-        e = cudaMemcpy(s->d_slot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice);
+    e = obj_zero(s->d_block, total);
+    if (e == cudaSuccess && s->n > 0) e = obj_upload(s->d_slot, slot.data(), slot.size() * 4);
+    if (e == cudaSuccess) e = obj_finish();  // the slot list is read from host memory: done before return
     if (e != cudaSuccess) {
         set_cuda_error(e);
-        cudaFree(s->d_block);
+        obj_free(s->d_block);
         delete s;
         return SCN_ECUDA;
     }
@@ -388,7 +391,7 @@ scn_status scn_seq_destroy(scn_seq* s) {
     if (!s) return SCN_EINVAL;
     free_gate_workspace(s);
     free_space_workspace(s);
-    if (s->d_block) cudaFree(s->d_block);
+    obj_free(s->d_block);
     delete s;
     return SCN_OK;
 }

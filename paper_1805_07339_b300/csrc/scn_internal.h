@@ -24,6 +24,19 @@ void set_cuda_error(cudaError_t e);
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Device memory of library objects (videos, sequences, plans), in scn_mem.cu:
+// from a per-device pool grown ahead in large steps and filled on a library
+// stream that waits for no other stream, by copies only (a kernel would queue
+// behind running grids), so creating an object does not wait for kernels
+// already running.  obj_finish() waits for the fills issued so
+// far; obj_free() first waits for the device, as cudaFree does.
+cudaError_t obj_stream(cudaStream_t* s);
+cudaError_t obj_alloc(void** p, size_t bytes);
+cudaError_t obj_upload(void* dst, const void* src, size_t bytes);
+cudaError_t obj_zero(void* dst, size_t bytes);
+cudaError_t obj_finish();
+void obj_free(void* p);
+
 // Device status word bits (per sequence).
 constexpr int kStatusTimeout = 1;
 

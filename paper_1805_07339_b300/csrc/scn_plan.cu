@@ -102,15 +102,17 @@ scn_status build_items(scn_plan* p) {
     p->grid = static_cast<int>(std::min<int64_t>(grid_req, std::max<int64_t>(p->n_items, 1)));
     // device copies (synchronous: plans are built once, then run many times)
     if (p->items_cap < p->n_items) {
-        if (p->d_items) cudaFree(p->d_items);
+        obj_free(p->d_items);
         p->d_items = nullptr;
         p->items_cap = 0;
-        SCN_CUDA_TRY(cudaMalloc(&p->d_items, static_cast<size_t>(std::max<int64_t>(p->n_items, 1)) * sizeof(Item)));
+        void* d = nullptr;
+        SCN_CUDA_TRY(obj_alloc(&d, static_cast<size_t>(std::max<int64_t>(p->n_items, 1)) * sizeof(Item)));
+        p->d_items = static_cast<Item*>(d);
         p->items_cap = p->n_items;
     }
-    if (p->n_items > 0)
-        SCN_CUDA_TRY(cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice));
-    SCN_CUDA_TRY(cudaMemcpy(p->d_jobs, p->jobs.data(), p->jobs.size() * sizeof(Job), cudaMemcpyHostToDevice));
+    if (p->n_items > 0) SCN_CUDA_TRY(obj_upload(p->d_items, items.data(), items.size() * sizeof(Item)));
+    SCN_CUDA_TRY(obj_upload(p->d_jobs, p->jobs.data(), p->jobs.size() * sizeof(Job)));
+    SCN_CUDA_TRY(obj_finish());  // items and jobs are read from host vectors: done before return
     if (p->graph) {
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
@@ -131,9 +133,9 @@ Launch plan_launch(const scn_plan* p) {
 
 void free_plan(scn_plan* p) {
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    if (p->d_items) cudaFree(p->d_items);
-    if (p->d_jobs) cudaFree(p->d_jobs);
-    if (p->d_block) cudaFree(p->d_block);
+    obj_free(p->d_items);
+    obj_free(p->d_jobs);
+    obj_free(p->d_block);
     delete p;
 }
 
@@ -165,9 +167,11 @@ scn_status scn_plan_create(scn_seq* const* seqs, int32_t nseq, uint32_t* const* 
     p->score.assign(d_score, d_score + nseq);
     p->flag.assign(d_flag, d_flag + nseq);
     if (tune) p->tune = *tune;
-    cudaError_t e = cudaMalloc(&p->d_block, 256);
-    if (e == cudaSuccess) e = cudaMemset(p->d_block, 0, 256);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_jobs, static_cast<size_t>(nseq) * sizeof(Job));
+    void* djobs = nullptr;
+    cudaError_t e = obj_alloc(&p->d_block, 256);
+    if (e == cudaSuccess) e = obj_zero(p->d_block, 256);
+    if (e == cudaSuccess) e = obj_alloc(&djobs, static_cast<size_t>(nseq) * sizeof(Job));
+    p->d_jobs = static_cast<Job*>(djobs);
     if (e != cudaSuccess) {
         set_cuda_error(e);
         free_plan(p);
