@@ -46,13 +46,13 @@ scn_status ensure_space_ws(scn_seq* s, SpaceWs*& ws) {
     ws = new (std::nothrow) SpaceWs;
     if (!ws) return SCN_ENOMEM;
     const size_t m = f.size(), up = ((std::max<size_t>(m, 1) * 4) + 255) & ~size_t(255);
-    cudaError_t err = cudaMalloc(&ws->block, 2 * up + kMaxElem);
-    if (err == cudaSuccess && m) err = cudaMemcpy(ws->block, f.data(), m * 4, cudaMemcpyHostToDevice);
-    if (err == cudaSuccess && m)
-        err = cudaMemcpy(static_cast<char*>(ws->block) + up, e.data(), m * 4, cudaMemcpyHostToDevice);
+    cudaError_t err = obj_alloc(&ws->block, 2 * up + kMaxElem);
+    if (err == cudaSuccess && m) err = obj_upload(ws->block, f.data(), m * 4);
+    if (err == cudaSuccess && m) err = obj_upload(static_cast<char*>(ws->block) + up, e.data(), m * 4);
+    if (err == cudaSuccess) err = obj_finish();  // f and e are host vectors of this call
     if (err != cudaSuccess) {
         set_cuda_error(err);
-        if (ws->block) cudaFree(ws->block);
+        obj_free(ws->block);
         delete ws;
         ws = nullptr;
         return SCN_ECUDA;
@@ -337,7 +337,7 @@ int grid_for(int64_t work, int threads) {
 void free_space_workspace(scn_seq* s) {
     SpaceWs* ws = static_cast<SpaceWs*>(s->space_ws);
     if (!ws) return;
-    if (ws->block) cudaFree(ws->block);
+    obj_free(ws->block);
     delete ws;
     s->space_ws = nullptr;
 }

@@ -90,7 +90,7 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
     ws = static_cast<GateWs*>(s->gate_ws);
     if (ws && ws->cap >= s->n) return SCN_OK;
     if (ws) {
-        if (ws->block) cudaFree(ws->block);
+        obj_free(ws->block);
         delete ws;
         s->gate_ws = nullptr;
     }
@@ -102,11 +102,12 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
                             up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c * 4), 256, 256, 256};
     size_t total = 0;
     for (size_t p : parts) total += p;
-    cudaError_t e = cudaMalloc(&ws->block, total);
-    if (e == cudaSuccess) e = cudaMemset(ws->block, 0, total);
+    cudaError_t e = obj_alloc(&ws->block, total);
+    if (e == cudaSuccess) e = obj_zero(ws->block, total);
+    if (e == cudaSuccess) e = obj_finish();
     if (e != cudaSuccess) {
         set_cuda_error(e);
-        if (ws->block) cudaFree(ws->block);
+        obj_free(ws->block);
         delete ws;
         ws = nullptr;
         return SCN_ECUDA;
@@ -132,7 +133,7 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
 void free_gate_workspace(scn_seq* s) {
     GateWs* ws = static_cast<GateWs*>(s->gate_ws);
     if (!ws) return;
-    if (ws->block) cudaFree(ws->block);
+    obj_free(ws->block);
     delete ws;
     s->gate_ws = nullptr;
 }
