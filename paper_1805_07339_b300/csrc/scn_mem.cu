@@ -128,10 +128,19 @@ cudaError_t obj_finish() {
 
 void obj_free(void* p) {
     if (!p) return;
+    // the block's own device, which need not be the current one when the object is destroyed
+    int cur = 0, dev = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return;
+    cudaPointerAttributes at = {};
+    if (cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeDevice) dev = at.device;
+    cudaGetLastError();
+    if (dev < 0) dev = cur;
+    if (dev != cur && cudaSetDevice(dev) != cudaSuccess) return;
     // as cudaFree would: no launch on any stream may still use the block
     cudaDeviceSynchronize();
     cudaStream_t s = nullptr;
     if (obj_stream(&s) == cudaSuccess) cudaFreeAsync(p, s);
+    if (dev != cur) cudaSetDevice(cur);
 }
 
 }  // namespace scn
