@@ -4,9 +4,9 @@
 // score kernel, which keeps the final say: an unproposed pair gets score 0 and
 // flag 0, a proposed pair gets its exact score and flag.
 //
-// Steps: proposals -> compacted list of proposed elements k (pair k-1, k) ->
-// storage slots of both frames of every proposed pair -> one launch of the
-// fused kernel over that 2m-element sequence -> scatter of each pair's score.
+// Steps: proposals, compacted into a list of proposed elements k (pair k-1, k)
+// with the storage slots of both frames of each -> one launch of the fused
+// kernel over that 2m-element sequence -> scatter of each pair's score.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,26 +34,25 @@ struct GateWs {
     int* count = nullptr;
 };
 
+// Each proposed pair (k-1, k) is appended to the list together with the storage
+// slots of its two frames, the 2m-element sequence the exact pass reads.  The
+// count m stays on the device (*count), so no host round trip sits between the
+// gate and the exact pass.
 __global__ void propose_kernel(const float* gate, int64_t n, float tau, uint8_t* proposed, int32_t* list, int* count,
-                               uint32_t* score, uint8_t* flag) {
+                               uint32_t* score, uint8_t* flag, const int32_t* slot, int32_t* slots2) {
     for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
          k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const bool p = k >= 1 && gate[k] > tau;
         proposed[k] = p ? 1 : 0;
         score[k] = 0;
         flag[k] = 0;
-        if (p) list[atomicAdd(count, 1)] = static_cast<int32_t>(k);
+        if (p) {
+            const int i = atomicAdd(count, 1);
+            list[i] = static_cast<int32_t>(k);
+            slots2[2 * i] = slot[k - 1];
+            slots2[2 * i + 1] = slot[k];
+        }
     }
-}
-
-// the proposal count m is read on the device (*count), so no host round trip sits
-// between the gate and the exact pass
-__global__ void pair_slots(const int32_t* list, const int* count, const int32_t* slot, int32_t* slots2) {
-    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= *count) return;
-    const int32_t k = list[i];
-    slots2[2 * i] = slot[k - 1];
-    slots2[2 * i + 1] = slot[k];
 }
 
 __global__ void scatter_scores(const int32_t* list, const int* count, const uint32_t* score2, const uint8_t* flag2,
@@ -167,14 +166,12 @@ scn_status scn_gated_hist_scores(scn_seq* s, const float* d_gate, float tau, uin
     SCN_CUDA_TRY(cudaMemsetAsync(ws->count, 0, sizeof(int), cs));
     const int64_t blocks = std::min<int64_t>((s->n + 255) / 256, 148 * 8);
     propose_kernel<<<static_cast<unsigned>(blocks), 256, 0, cs>>>(d_gate, s->n, tau, d_proposed, ws->list, ws->count,
-                                                                  d_score, d_flag);
+                                                                  d_score, d_flag, s->d_slot, ws->slots2);
     SCN_CUDA_TRY(cudaGetLastError());
     // m = *ws->count stays on the device: every later launch is sized for the
     // largest m (n - 1 pairs) and reads m itself
     const int64_t cap = s->n;
     const unsigned pblocks = static_cast<unsigned>((cap + 255) / 256);
-    pair_slots<<<pblocks, 256, 0, cs>>>(ws->list, ws->count, s->d_slot, ws->slots2);
-    SCN_CUDA_TRY(cudaGetLastError());
     // the exact kernel over the 2m frames of the proposed pairs: one contiguous
     // range of row pairs per CTA, each CTA computing its range from m on the device
     scn_seq q;
