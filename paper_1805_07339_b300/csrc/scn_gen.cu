@@ -102,7 +102,7 @@ __device__ __forceinline__ uint4 gen_vector(const GenArgs& a, int64_t f, const s
         FloorStep rx;
         rx.init(sh.gx[0] * (x0 - dt), a.W);
         const int gx = sh.gx[0];
-#pragma unroll 4
+#pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int v = base + rx.q + noise_from_counter(c);
             b[i] = static_cast<uint8_t>(min(max(v, 16), 235));
@@ -124,7 +124,7 @@ __device__ __forceinline__ uint4 gen_vector(const GenArgs& a, int64_t f, const s
             base[pl - 1] = sh.base[pl] + floordiv_pos(sh.gy[pl] * (2 * cy), a.H);
             gx2[pl - 1] = 2 * sh.gx[pl];
         }
-#pragma unroll 2
+#pragma unroll
         for (int j = 0; j < 8; ++j) {
 #pragma unroll
             for (int pl = 0; pl < 2; ++pl) {
