@@ -402,14 +402,16 @@ def main():
         torch.cuda.empty_cache()
         res = proposal.run(torch)
         res.pop("params", None)
+        C = res["cascade"]
         prop = {"workload": "train 201,572 consecutive 1080p pairs (28 videos), thresholds on 8 held-out videos, "
                             "evaluate 100,800 fresh frames (14 videos)",
-                "recall": res["learned"]["recall"], "precision": res["learned"]["precision"],
-                "speedup": res["learned"]["speedup"], "t_plain_ms": res["t_plain_ms"],
-                "t_proposal_ms": res["learned"]["t_ms"], "boundaries": res["boundaries"],
-                "proposed": res["learned"]["proposed"], "tau": res["tau"],
-                "exact_on_proposed": res["learned"]["exact_on_proposed"],
+                "path": "cascade: the thumbnail-difference gate as prefilter, the network on the pairs it passes",
+                "recall": C["recall"], "precision": C["precision"], "speedup": C["speedup"],
+                "t_plain_ms": res["t_plain_ms"], "t_proposal_ms": C["t_ms"], "boundaries": res["boundaries"],
+                "proposed": C["proposed"], "exact_on_proposed": C["exact_on_proposed"],
+                "tau_diff": res["tau_pre"], "tau_network": res["tau_cascade"],
                 "train_seconds": res["train"]["seconds"], "train_steps": res["train"]["steps"],
+                "network_alone": dict(res["learned"], tau=res["tau"]),
                 "thumbnail_difference_gate": res["diff"]}
 
     cpu = None

@@ -428,6 +428,18 @@ scn_status scn_proposal_hist_scores(scn_seq* s, scn_cnn* net, float tau, uint8_t
 /* The non-learned gate: d_diff[k] = mean |thumb[k] - thumb[k-1]| over the
  * 2304 samples (d_diff[0] = 0); d_thumbs 4-byte aligned. */
 scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, void* stream);
+/* The cascade: the non-learned gate as a cheap prefilter, the network on what
+ * it passes.  Thumbnails into d_thumbs ([n][36][64], 16-byte aligned) and
+ * their differences into d_diff ([n]); every pair with d_diff[k] > tau_diff
+ * gets the network's logit in d_gate[k], every other pair -infinity; then
+ * scn_gated_hist_scores with tau_net, so a pair is proposed only when both
+ * thresholds pass and the exact kernel keeps the final say.  The network runs
+ * on the listed pairs only (their count stays on the device: no host round
+ * trip).  Workspace as scn_gated_hist_scores.  d_diff, d_gate 4-byte aligned
+ * (SCN_EINVAL); more than 2^31 - 1 elements: SCN_ERANGE. */
+scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, float tau_net, uint8_t* d_thumbs,
+                                   float* d_diff, float* d_gate, uint8_t* d_proposed, uint32_t* d_score,
+                                   uint8_t* d_flag, int64_t* h_nproposed, void* stream);
 
 typedef enum { SCN_F32 = 0, SCN_BF16 = 1 } scn_dtype;
 /* Bilinear resize (half-pixel centres, no antialias, stretch) of the RGB

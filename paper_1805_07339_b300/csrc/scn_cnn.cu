@@ -459,6 +459,7 @@ struct FusedArgs {
     const float* f1t;          // [32][64] fp32 (BF16 values), transposed F1
     float* logits;
     int* status;
+    const int* d_pairs;        // non-null: the pair count, read on the device (at most pairs)
 };
 
 // (byte k of w - 128) / 64 as fp32: the byte placed in the mantissa of 2^23
@@ -591,10 +592,11 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
     bool ok = true;
 
     // thumbnail indices of the batch's two pairs (every thread keeps them; fetched a batch ahead)
-    const int64_t nbatch = (a.pairs + kFzPairs - 1) / kFzPairs;
+    const int64_t npairs = a.d_pairs ? min(static_cast<int64_t>(max(*a.d_pairs, 0)), a.pairs) : a.pairs;
+    const int64_t nbatch = (npairs + kFzPairs - 1) / kFzPairs;
     auto pair_thumbs = [&](int64_t batch, int p, int64_t& ip, int64_t& ic) {
         int64_t b = batch * kFzPairs + p;
-        if (b >= a.pairs) b = a.pairs - 1;
+        if (b >= npairs) b = npairs - 1;
         ip = a.prev ? a.prev[b] : b;
         ic = a.cur ? a.cur[b] : b + 1;
     };
@@ -631,7 +633,7 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
     auto head_c = [&](int64_t hb) {
         if (tid < kFzPairs) {
             const int64_t b = hb * kFzPairs + tid;
-            if (b < a.pairs) a.logits[b] = wsum[2 * tid] + wsum[2 * tid + 1] + bias[208];
+            if (b < npairs) a.logits[b] = wsum[2 * tid] + wsum[2 * tid + 1] + bias[208];
         }
     };
     int64_t prev = -1;  // the batch whose head is pending
@@ -854,7 +856,7 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
 }
 
 scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* prev, const int32_t* cur, int64_t pairs,
-                                float* logits, cudaStream_t st) {
+                                float* logits, cudaStream_t st, const int* d_pairs = nullptr) {
     static int attr_dev = -1;
     int dev = 0;
     SCN_CUDA_TRY(cudaGetDevice(&dev));
@@ -878,6 +880,7 @@ scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* pr
     a.f1t = n->f1t;
     a.logits = logits;
     a.status = n->status;
+    a.d_pairs = d_pairs;
     const int64_t nbatch = (pairs + kFzPairs - 1) / kFzPairs;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
@@ -1302,6 +1305,16 @@ scn_status prep(Net* n, cudaStream_t st) {
 struct scn_cnn {
     scn::cnn::Net net;
 };
+
+namespace scn {
+scn_status cnn_forward_counted(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
+                               int64_t max_pairs, const int* d_pairs, float* d_logits, cudaStream_t st) {
+    if (!c || !d_thumbs || !d_prev || !d_cur || !d_pairs || !d_logits || max_pairs < 0) return SCN_EINVAL;
+    if (max_pairs == 0) return SCN_OK;
+    if (reinterpret_cast<uintptr_t>(d_thumbs) % 16) return SCN_EINVAL;
+    return cnn::launch_forward_fused(&c->net, d_thumbs, d_prev, d_cur, max_pairs, d_logits, st, d_pairs);
+}
+}  // namespace scn
 
 using namespace scn;
 using namespace scn::cnn;

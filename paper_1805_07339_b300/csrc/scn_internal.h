@@ -164,6 +164,11 @@ HistShape resolve_hist_shape(const scn_seq* s);
 // (outputs, scratch, queue and status are filled in by the caller).
 Launch single_launch(const scn_table* t, int64_t n, const int32_t* slot, const HistShape& sh);
 int device_sm_count();
+
+// The fused proposal forward over pairs (d_prev[b], d_cur[b]) whose count is
+// read on the device (*d_pairs, at most max_pairs): logits into d_logits[b].
+scn_status cnn_forward_counted(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
+                               int64_t max_pairs, const int* d_pairs, float* d_logits, cudaStream_t st);
 // Release a sequence's gated-path workspace (scn_proposal.cu).
 void free_gate_workspace(scn_seq* s);
 void free_space_workspace(scn_seq* s);

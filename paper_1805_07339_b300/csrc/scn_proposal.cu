@@ -32,6 +32,12 @@ struct GateWs {
     uint32_t* queue = nullptr;
     int* status = nullptr;
     int* count = nullptr;
+    // the cascade's prefiltered pairs: thumbnail indices, element, network logit, count
+    int32_t* pre_prev = nullptr;
+    int32_t* pre_cur = nullptr;
+    int32_t* pre_elem = nullptr;
+    float* pre_logit = nullptr;
+    int* pre_count = nullptr;
 };
 
 // Each proposed pair (k-1, k) is appended to the list together with the storage
@@ -85,6 +91,29 @@ __global__ void __launch_bounds__(256) thumb_diff_kernel(const uint8_t* thumbs, 
     }
 }
 
+// Cascade prefilter: every gate value starts below any threshold, and each pair
+// whose thumbnail difference exceeds tau_diff is listed for the network
+// (thumbnail indices k-1, k and element k).
+__global__ void prefilter_kernel(const float* diff, int64_t n, float tau_diff, float* gate, int32_t* prev, int32_t* cur,
+                                 int32_t* elem, int* count) {
+    for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+         k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        gate[k] = -INFINITY;
+        if (k >= 1 && diff[k] > tau_diff) {
+            const int i = atomicAdd(count, 1);
+            prev[i] = static_cast<int32_t>(k - 1);
+            cur[i] = static_cast<int32_t>(k);
+            elem[i] = static_cast<int32_t>(k);
+        }
+    }
+}
+
+// the network's logit of each listed pair back to its element (count read on the device)
+__global__ void scatter_logits(const int32_t* elem, const int* count, const float* logit, float* gate) {
+    const int m = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) gate[elem[i]] = logit[i];
+}
+
 scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
     ws = static_cast<GateWs*>(s->gate_ws);
     if (ws && ws->cap >= s->n) return SCN_OK;
@@ -98,7 +127,8 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
     const int64_t c = std::max<int64_t>(s->n, 1);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t parts[] = {up(c * 4), up(2 * c * 4), up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c),
-                            up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c * 4), 256, 256, 256};
+                            up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c * 4), 256, 256, 256,
+                            up(c * 4), up(c * 4), up(c * 4), up(c * 4), 256};
     size_t total = 0;
     for (size_t p : parts) total += p;
     cudaError_t e = obj_alloc(&ws->block, total);
@@ -117,8 +147,11 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
                     reinterpret_cast<void**>(&ws->flag2),   reinterpret_cast<void**>(&ws->partial),
                     reinterpret_cast<void**>(&ws->done),    reinterpret_cast<void**>(&ws->pair),
                     reinterpret_cast<void**>(&ws->queue),   reinterpret_cast<void**>(&ws->status),
-                    reinterpret_cast<void**>(&ws->count)};
-    for (int i = 0; i < 11; ++i) {
+                    reinterpret_cast<void**>(&ws->count),   reinterpret_cast<void**>(&ws->pre_prev),
+                    reinterpret_cast<void**>(&ws->pre_cur), reinterpret_cast<void**>(&ws->pre_elem),
+                    reinterpret_cast<void**>(&ws->pre_logit), reinterpret_cast<void**>(&ws->pre_count)};
+    static_assert(sizeof(parts) / sizeof(parts[0]) == sizeof(dst) / sizeof(dst[0]), "workspace parts");
+    for (size_t i = 0; i < sizeof(parts) / sizeof(parts[0]); ++i) {
         *dst[i] = p;
         p += parts[i];
     }
@@ -223,6 +256,40 @@ scn_status scn_proposal_hist_scores(scn_seq* s, scn_cnn* net, float tau, uint8_t
         if (st != SCN_OK) return st;
     }
     return scn_gated_hist_scores(s, d_logits, tau, d_proposed, d_score, d_flag, h_nproposed, stream);
+}
+
+
+scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, float tau_net, uint8_t* d_thumbs,
+                                   float* d_diff, float* d_gate, uint8_t* d_proposed, uint32_t* d_score,
+                                   uint8_t* d_flag, int64_t* h_nproposed, void* stream) {
+    if (!s || !net || !d_thumbs || !d_diff || !d_gate || !d_proposed || !d_score || !d_flag) return SCN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_thumbs) & 15u) return SCN_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_diff) | reinterpret_cast<uintptr_t>(d_gate)) & 3u) return SCN_EINVAL;
+    if (h_nproposed) *h_nproposed = 0;
+    if (s->n == 0) return SCN_OK;
+    if (s->n > 0x7fffffff) return SCN_ERANGE;
+    GateWs* ws = nullptr;
+    scn_status st = ensure_ws(s, ws);
+    if (st != SCN_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    st = scn_thumbs(s, d_thumbs, stream);
+    if (st != SCN_OK) return st;
+    st = scn_thumb_diff(d_thumbs, s->n, d_diff, stream);
+    if (st != SCN_OK) return st;
+    SCN_CUDA_TRY(cudaMemsetAsync(ws->pre_count, 0, sizeof(int), cs));
+    const int64_t blocks = std::min<int64_t>((s->n + 255) / 256, 148 * 8);
+    prefilter_kernel<<<static_cast<unsigned>(blocks), 256, 0, cs>>>(d_diff, s->n, tau_diff, d_gate, ws->pre_prev,
+                                                                    ws->pre_cur, ws->pre_elem, ws->pre_count);
+    SCN_CUDA_TRY(cudaGetLastError());
+    if (s->n > 1) {
+        // the network only on the listed pairs; the launch is sized for all n-1 and reads the count
+        st = cnn_forward_counted(net, d_thumbs, ws->pre_prev, ws->pre_cur, s->n - 1, ws->pre_count, ws->pre_logit, cs);
+        if (st != SCN_OK) return st;
+        scatter_logits<<<static_cast<unsigned>(blocks), 256, 0, cs>>>(ws->pre_elem, ws->pre_count, ws->pre_logit,
+                                                                      d_gate);
+        SCN_CUDA_TRY(cudaGetLastError());
+    }
+    return scn_gated_hist_scores(s, d_gate, tau_net, d_proposed, d_score, d_flag, h_nproposed, stream);
 }
 
 }  // extern "C"

@@ -141,9 +141,11 @@ def choose_tau(score: np.ndarray, labels: np.ndarray, recall: float = 0.995, fp_
     return min(t_rec, t_neg)
 
 
-def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids: list[int], reps: int = 3):
-    """Per video: the plain exact path over all frames vs the learned gate and the
-    thumbnail-difference gate (thumbnails + gate + exact path on proposed pairs)."""
+def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids: list[int], reps: int = 3,
+             tau_pre: float | None = None, tau_cascade: float | None = None):
+    """Per video: the plain exact path over all frames vs the learned gate, the
+    thumbnail-difference gate and (when tau_pre is given) the cascade, each as
+    thumbnails + gate + exact path on proposed pairs."""
     T = src.T
     thumbs = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
     zl = torch.full((T,), -1e30, dtype=torch.float32, device="cuda")
@@ -152,8 +154,9 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
     sc = torch.empty(T, dtype=torch.int32, device="cuda")
     fl = torch.empty(T, dtype=torch.uint8, device="cuda")
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))  # noqa: E731
-    tot = dict(frames=0, boundaries=0, t_plain=0.0, t_learned=0.0, t_diff=0.0)
-    for gate in ("learned", "diff"):
+    tot = dict(frames=0, boundaries=0, t_plain=0.0, t_learned=0.0, t_diff=0.0, t_cascade=0.0)
+    gates = ("learned", "diff") + (("cascade",) if tau_pre is not None else ())
+    for gate in gates:
         tot[gate] = dict(tp=0, proposed=0, exact_equal=True)
     for vid in ids:
         src.load(vid)
@@ -170,12 +173,15 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
         b.record()
         torch.cuda.synchronize()
         tot["t_plain"] += a.elapsed_time(b) / reps
-        for gate in ("learned", "diff"):
+        for gate in gates:
             a, b = ev()
             a.record()
             for _ in range(reps):
                 if gate == "learned":
                     scn.scn_proposal_hist_scores(src.seq, net, tau, thumbs, zl, prop, sc, fl, count=False)
+                elif gate == "cascade":
+                    scn.scn_cascade_hist_scores(src.seq, net, tau_pre, tau if tau_cascade is None else tau_cascade,
+                                                thumbs, diff, zl, prop, sc, fl, count=False)
                 else:
                     src.thumbs(thumbs)
                     scn.scn_thumb_diff(thumbs, T, diff)
@@ -191,7 +197,7 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
             fl_np = fl.cpu().numpy()[1:]
             r["exact_equal"] &= bool(np.array_equal(fl_np[p], ex[p].astype(np.uint8))) and not fl_np[~p].any()
     out = {"frames": tot["frames"], "boundaries": tot["boundaries"], "t_plain_ms": tot["t_plain"]}
-    for gate in ("learned", "diff"):
+    for gate in gates:
         r = tot[gate]
         out[gate] = {"recall": r["tp"] / max(tot["boundaries"], 1), "precision": r["tp"] / max(r["proposed"], 1),
                      "proposed": r["proposed"], "t_ms": tot["t_" + gate],
@@ -220,9 +226,22 @@ def run(torch, steps: int = 6000, batch: int = 256, lr: float = 1e-3, seed: int 
             scn.scn_thumb_diff(vth, vth.shape[0], d)
             dd = d.cpu().numpy()
             # diff of pair (k-1, k) sits at thumbnail k; pairs never span two videos
-            tau_d = choose_tau(dd[vc.cpu().numpy()], vlab)
-            res = evaluate(torch, fwd, tau, tau_d, src, eval_ids or EVAL_IDS)
-            res.update({"train": tr, "tau": tau, "tau_diff": tau_d, "train_pairs": int(lab.numel()),
+            dv = dd[vc.cpu().numpy()]
+            tau_d = choose_tau(dv, vlab)
+            # cascade: the difference gate's own threshold as the prefilter (non-boundary pairs
+            # crowd just below it, so a looser one would pass most pairs), then the network as a
+            # precision filter on what passes, with a threshold that keeps every held-out boundary
+            # there (and never stricter than the network's own)
+            tau_pre = tau_d
+            pas = dv > tau_pre
+            tau_c = min(tau_for_recall(z[pas], vlab[pas], recall=1.0), tau) if pas.any() else tau
+            pos = vlab > 0.5
+            val_cascade = {"recall": float(np.mean(pas[pos] & (z[pos] > tau_c))), "prefilter_pass": float(np.mean(pas)),
+                           "proposed_fraction": float(np.mean(pas & (z > tau_c)))}
+            res = evaluate(torch, fwd, tau, tau_d, src, eval_ids or EVAL_IDS, tau_pre=tau_pre, tau_cascade=tau_c)
+            res.update({"train": tr, "tau": tau, "tau_diff": tau_d, "tau_pre": tau_pre, "tau_cascade": tau_c,
+                        "val_cascade": val_cascade,
+                        "train_pairs": int(lab.numel()),
                         "train_positives": int(lab.sum().item()), "val_pairs": int(vl.numel()),
                         "params": scn.scn_cnn_get_params(fwd)})
             return res

@@ -105,6 +105,8 @@ SIGNATURES = [
     ("scn_gated_hist_scores", c_i32, [c_vp, c_vp, ctypes.c_float, c_vp, c_vp, c_vp, _P(c_i64), c_vp]),
     ("scn_proposal_hist_scores", c_i32, [c_vp, c_vp, ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_vp, _P(c_i64), c_vp]),
     ("scn_thumb_diff", c_i32, [c_vp, c_i64, c_vp, c_vp]),
+    ("scn_cascade_hist_scores", c_i32, [c_vp, c_vp, ctypes.c_float, ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                        c_vp, _P(c_i64), c_vp]),
     ("scn_resize_norm", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_i32, c_vp, c_vp]),
     ("scn_thumbs", c_i32, [c_vp, c_vp, c_vp]),
     ("scn_resize_norm_both", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_vp, c_vp, c_vp]),
@@ -444,6 +446,17 @@ def scn_proposal_hist_scores(s: int, net: int, tau: float, thumbs, logits, propo
     _check(_lib.scn_proposal_hist_scores(s, net, tau, _ptr(thumbs), _ptr(logits), _ptr(proposed), _ptr(score),
                                          _ptr(flag), ctypes.byref(m) if count else None, _stream(stream)),
            "scn_proposal_hist_scores")
+    return m.value if count else None
+
+
+def scn_cascade_hist_scores(s: int, net: int, tau_diff: float, tau_net: float, thumbs, diff, gate, proposed, score,
+                            flag, stream=None, count: bool = True):
+    """The difference gate as a prefilter, the network on what passes, the exact kernel on
+    pairs that pass both (see include/scn.h)."""
+    m = c_i64()
+    _check(_lib.scn_cascade_hist_scores(s, net, tau_diff, tau_net, _ptr(thumbs), _ptr(diff), _ptr(gate), _ptr(proposed),
+                                        _ptr(score), _ptr(flag), ctypes.byref(m) if count else None, _stream(stream)),
+           "scn_cascade_hist_scores")
     return m.value if count else None
 
 

@@ -119,6 +119,43 @@ def test_learned_proposal_path_consistent(scn, tiny):
         scn.scn_cnn_destroy(net)
 
 
+@pytest.mark.parametrize("q_diff,q_net", [(0.5, 0.5), (0.0, 0.0), (1.1, 0.5), (0.2, 0.9)])
+def test_cascade_matches_its_two_thresholds(scn, tiny, q_diff, q_net):
+    """The cascade proposes exactly the pairs whose thumbnail difference and network
+    logit both pass (thresholds at quantiles of the tiny video's own scores; 1.1 lists
+    no pair at all); its gate holds the full forward's logits bit for bit on the listed
+    pairs and -inf elsewhere; the exact kernel keeps the final say."""
+    from paper_1805_07339_b300.proposal import he_uniform
+    T = tiny["T"]
+    net = scn.scn_cnn_create(64)
+    try:
+        scn.scn_cnn_set_params(net, he_uniform(3))
+        th = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
+        d = torch.empty(T, dtype=torch.float32, device="cuda")
+        zz = torch.empty(T - 1, dtype=torch.float32, device="cuda")
+        scn.scn_thumbs(tiny["seq"], th)
+        scn.scn_thumb_diff(th, T, d)
+        scn.scn_cnn_forward(net, th, T - 1, zz)
+        dh, zh = d.cpu().numpy(), zz.cpu().numpy()
+        tau_d = float(np.quantile(dh[1:], min(q_diff, 1.0))) + (1.0 if q_diff > 1.0 else 0.0)
+        tau_n = float(np.quantile(zh, q_net))
+        th2 = torch.zeros_like(th)
+        d2 = torch.zeros_like(d)
+        gate = torch.zeros(T, dtype=torch.float32, device="cuda")
+        prop, sc, fl = _outs(T)
+        m = scn.scn_cascade_hist_scores(tiny["seq"], net, tau_d, tau_n, th2, d2, gate, prop, sc, fl)
+        p = _check(prop, sc, fl, tiny["exact"])
+        listed = np.concatenate([[False], dh[1:] > tau_d])
+        want = listed & np.concatenate([[False], zh > tau_n])
+        assert np.array_equal(p, want) and m == int(want.sum())
+        assert torch.equal(th2, th) and np.array_equal(d2.cpu().numpy(), dh)
+        g = gate.cpu().numpy()
+        assert np.array_equal(g[listed].view(np.uint32), np.concatenate([[0.0], zh]).astype(np.float32)[listed].view(np.uint32))
+        assert np.all(np.isneginf(g[~listed]))
+    finally:
+        scn.scn_cnn_destroy(net)
+
+
 def test_training_pipeline_small(scn):
     """A short GPU training run on two 1080p videos: the loss falls, the gated
     path stays exact on proposed pairs, and the report is complete."""
@@ -126,7 +163,7 @@ def test_training_pipeline_small(scn):
     res = proposal.run(torch, steps=300, train_ids=[2000, 2001], val_ids=[3000], eval_ids=[4000])
     curve = res["train"]["curve"]
     assert curve[-1][1] < curve[0][1]
-    for g in ("learned", "diff"):
+    for g in ("learned", "diff", "cascade"):
         assert res[g]["exact_on_proposed"]
         assert 0.0 <= res[g]["recall"] <= 1.0 and res[g]["speedup"] > 0
     assert res["boundaries"] > 0 and res["frames"] == 7200
@@ -145,3 +182,9 @@ def test_learned_gate_gains_over_thumbnail_difference(scn):
     assert L["precision"] > D["precision"]
     assert L["recall"] >= D["recall"]
     assert L["speedup"] > 1.0
+    # the cascade (the difference gate as prefilter, the network as precision filter on what
+    # it passes) keeps the target recall, proposes a subset of the difference gate's pairs,
+    # and is more precise than it
+    C = res["cascade"]
+    assert C["exact_on_proposed"] and C["recall"] >= 0.99
+    assert C["proposed"] <= D["proposed"] and C["precision"] > D["precision"]
