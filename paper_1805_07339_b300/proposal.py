@@ -230,11 +230,11 @@ def run(torch, steps: int = 6000, batch: int = 256, lr: float = 1e-3, seed: int 
             tau_d = choose_tau(dv, vlab)
             # cascade: the difference gate's own threshold as the prefilter (non-boundary pairs
             # crowd just below it, so a looser one would pass most pairs), then the network as a
-            # precision filter on what passes, with a threshold that keeps every held-out boundary
-            # there (and never stricter than the network's own)
+            # precision filter on what passes, with a threshold 2 logits below the lowest held-out
+            # boundary there (and never stricter than the network's own): recall is the prefilter's
             tau_pre = tau_d
             pas = dv > tau_pre
-            tau_c = min(tau_for_recall(z[pas], vlab[pas], recall=1.0), tau) if pas.any() else tau
+            tau_c = min(tau_for_recall(z[pas], vlab[pas], recall=1.0) - 2.0, tau) if pas.any() else tau
             pos = vlab > 0.5
             val_cascade = {"recall": float(np.mean(pas[pos] & (z[pos] > tau_c))), "prefilter_pass": float(np.mean(pas)),
                            "proposed_fraction": float(np.mean(pas & (z > tau_c)))}
