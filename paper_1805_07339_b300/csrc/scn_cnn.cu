@@ -460,6 +460,7 @@ struct FusedArgs {
     float* logits;
     int* status;
     const int* d_pairs;        // non-null: the pair count, read on the device (at most pairs)
+    const int32_t* out_index;  // non-null: pair b's logit goes to logits[out_index[b]]
 };
 
 // (byte k of w - 128) / 64 as fp32: the byte placed in the mantissa of 2^23
@@ -633,7 +634,7 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
     auto head_c = [&](int64_t hb) {
         if (tid < kFzPairs) {
             const int64_t b = hb * kFzPairs + tid;
-            if (b < npairs) a.logits[b] = wsum[2 * tid] + wsum[2 * tid + 1] + bias[208];
+            if (b < npairs) a.logits[a.out_index ? a.out_index[b] : b] = wsum[2 * tid] + wsum[2 * tid + 1] + bias[208];
         }
     };
     int64_t prev = -1;  // the batch whose head is pending
@@ -856,7 +857,8 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
 }
 
 scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* prev, const int32_t* cur, int64_t pairs,
-                                float* logits, cudaStream_t st, const int* d_pairs = nullptr) {
+                                float* logits, cudaStream_t st, const int* d_pairs = nullptr,
+                                const int32_t* out_index = nullptr) {
     static int attr_dev = -1;
     int dev = 0;
     SCN_CUDA_TRY(cudaGetDevice(&dev));
@@ -881,6 +883,7 @@ scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* pr
     a.logits = logits;
     a.status = n->status;
     a.d_pairs = d_pairs;
+    a.out_index = out_index;
     const int64_t nbatch = (pairs + kFzPairs - 1) / kFzPairs;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
@@ -1308,11 +1311,12 @@ struct scn_cnn {
 
 namespace scn {
 scn_status cnn_forward_counted(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
-                               int64_t max_pairs, const int* d_pairs, float* d_logits, cudaStream_t st) {
+                               int64_t max_pairs, const int* d_pairs, float* d_logits, cudaStream_t st,
+                               const int32_t* d_out_index) {
     if (!c || !d_thumbs || !d_prev || !d_cur || !d_pairs || !d_logits || max_pairs < 0) return SCN_EINVAL;
     if (max_pairs == 0) return SCN_OK;
     if (reinterpret_cast<uintptr_t>(d_thumbs) % 16) return SCN_EINVAL;
-    return cnn::launch_forward_fused(&c->net, d_thumbs, d_prev, d_cur, max_pairs, d_logits, st, d_pairs);
+    return cnn::launch_forward_fused(&c->net, d_thumbs, d_prev, d_cur, max_pairs, d_logits, st, d_pairs, d_out_index);
 }
 }  // namespace scn
 

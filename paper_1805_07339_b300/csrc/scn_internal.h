@@ -166,9 +166,11 @@ Launch single_launch(const scn_table* t, int64_t n, const int32_t* slot, const H
 int device_sm_count();
 
 // The fused proposal forward over pairs (d_prev[b], d_cur[b]) whose count is
-// read on the device (*d_pairs, at most max_pairs): logits into d_logits[b].
+// read on the device (*d_pairs, at most max_pairs): logit of pair b into
+// d_logits[b], or into d_logits[d_out_index[b]] when d_out_index is given.
 scn_status cnn_forward_counted(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
-                               int64_t max_pairs, const int* d_pairs, float* d_logits, cudaStream_t st);
+                               int64_t max_pairs, const int* d_pairs, float* d_logits, cudaStream_t st,
+                               const int32_t* d_out_index);
 // Release a sequence's gated-path workspace (scn_proposal.cu).
 void free_gate_workspace(scn_seq* s);
 void free_space_workspace(scn_seq* s);

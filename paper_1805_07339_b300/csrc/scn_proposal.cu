@@ -32,11 +32,10 @@ struct GateWs {
     uint32_t* queue = nullptr;
     int* status = nullptr;
     int* count = nullptr;
-    // the cascade's prefiltered pairs: thumbnail indices, element, network logit, count
+    // the cascade's prefiltered pairs: thumbnail indices, element, count
     int32_t* pre_prev = nullptr;
     int32_t* pre_cur = nullptr;
     int32_t* pre_elem = nullptr;
-    float* pre_logit = nullptr;
     int* pre_count = nullptr;
 };
 
@@ -91,27 +90,38 @@ __global__ void __launch_bounds__(256) thumb_diff_kernel(const uint8_t* thumbs, 
     }
 }
 
-// Cascade prefilter: every gate value starts below any threshold, and each pair
-// whose thumbnail difference exceeds tau_diff is listed for the network
-// (thumbnail indices k-1, k and element k).
-__global__ void prefilter_kernel(const float* diff, int64_t n, float tau_diff, float* gate, int32_t* prev, int32_t* cur,
-                                 int32_t* elem, int* count) {
-    for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
-         k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+// Cascade prefilter, in the thumbnail-difference launch: d_diff[k] as
+// thumb_diff_kernel writes it, every gate value set below any threshold, and
+// each pair whose difference exceeds tau_diff listed for the network
+// (thumbnail indices k-1, k, whose logit goes to gate element k).
+__global__ void __launch_bounds__(256) diff_prefilter_kernel(const uint8_t* thumbs, int64_t n, float tau_diff,
+                                                             float* diff, float* gate, int32_t* prev, int32_t* cur,
+                                                             int32_t* elem, int* count) {
+    const int64_t k = blockIdx.x;
+    if (k >= n) return;
+    __shared__ unsigned part[8];
+    unsigned s = 0;
+    if (k > 0) {
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(thumbs + k * 2304);
+        const uint32_t* b = reinterpret_cast<const uint32_t*>(thumbs + (k - 1) * 2304);
+        for (int i = threadIdx.x; i < 576; i += 256) s = __vsadu4(a[i], b[i]) + s;
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < 8; ++w) t += part[w];
+        const float dk = static_cast<float>(t) / 2304.f;
+        diff[k] = dk;
         gate[k] = -INFINITY;
-        if (k >= 1 && diff[k] > tau_diff) {
+        if (k > 0 && dk > tau_diff) {
             const int i = atomicAdd(count, 1);
             prev[i] = static_cast<int32_t>(k - 1);
             cur[i] = static_cast<int32_t>(k);
             elem[i] = static_cast<int32_t>(k);
         }
     }
-}
-
-// the network's logit of each listed pair back to its element (count read on the device)
-__global__ void scatter_logits(const int32_t* elem, const int* count, const float* logit, float* gate) {
-    const int m = *count;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) gate[elem[i]] = logit[i];
 }
 
 scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
@@ -128,7 +138,7 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t parts[] = {up(c * 4), up(2 * c * 4), up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c),
                             up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c * 4), 256, 256, 256,
-                            up(c * 4), up(c * 4), up(c * 4), up(c * 4), 256};
+                            up(c * 4), up(c * 4), up(c * 4), 256};
     size_t total = 0;
     for (size_t p : parts) total += p;
     cudaError_t e = obj_alloc(&ws->block, total);
@@ -149,7 +159,7 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
                     reinterpret_cast<void**>(&ws->queue),   reinterpret_cast<void**>(&ws->status),
                     reinterpret_cast<void**>(&ws->count),   reinterpret_cast<void**>(&ws->pre_prev),
                     reinterpret_cast<void**>(&ws->pre_cur), reinterpret_cast<void**>(&ws->pre_elem),
-                    reinterpret_cast<void**>(&ws->pre_logit), reinterpret_cast<void**>(&ws->pre_count)};
+                    reinterpret_cast<void**>(&ws->pre_count)};
     static_assert(sizeof(parts) / sizeof(parts[0]) == sizeof(dst) / sizeof(dst[0]), "workspace parts");
     for (size_t i = 0; i < sizeof(parts) / sizeof(parts[0]); ++i) {
         *dst[i] = p;
@@ -274,20 +284,17 @@ scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, flo
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     st = scn_thumbs(s, d_thumbs, stream);
     if (st != SCN_OK) return st;
-    st = scn_thumb_diff(d_thumbs, s->n, d_diff, stream);
-    if (st != SCN_OK) return st;
     SCN_CUDA_TRY(cudaMemsetAsync(ws->pre_count, 0, sizeof(int), cs));
-    const int64_t blocks = std::min<int64_t>((s->n + 255) / 256, 148 * 8);
-    prefilter_kernel<<<static_cast<unsigned>(blocks), 256, 0, cs>>>(d_diff, s->n, tau_diff, d_gate, ws->pre_prev,
-                                                                    ws->pre_cur, ws->pre_elem, ws->pre_count);
+    diff_prefilter_kernel<<<static_cast<unsigned>(s->n), 256, 0, cs>>>(d_thumbs, s->n, tau_diff, d_diff, d_gate,
+                                                                      ws->pre_prev, ws->pre_cur, ws->pre_elem,
+                                                                      ws->pre_count);
     SCN_CUDA_TRY(cudaGetLastError());
     if (s->n > 1) {
-        // the network only on the listed pairs; the launch is sized for all n-1 and reads the count
-        st = cnn_forward_counted(net, d_thumbs, ws->pre_prev, ws->pre_cur, s->n - 1, ws->pre_count, ws->pre_logit, cs);
+        // the network only on the listed pairs (the launch is sized for all n-1 and reads the
+        // count); the logit of listed pair i goes straight to d_gate[elem[i]]
+        st = cnn_forward_counted(net, d_thumbs, ws->pre_prev, ws->pre_cur, s->n - 1, ws->pre_count, d_gate, cs,
+                                 ws->pre_elem);
         if (st != SCN_OK) return st;
-        scatter_logits<<<static_cast<unsigned>(blocks), 256, 0, cs>>>(ws->pre_elem, ws->pre_count, ws->pre_logit,
-                                                                      d_gate);
-        SCN_CUDA_TRY(cudaGetLastError());
     }
     return scn_gated_hist_scores(s, d_gate, tau_net, d_proposed, d_score, d_flag, h_nproposed, stream);
 }
