@@ -69,49 +69,51 @@ __global__ void scatter_scores(const int32_t* list, const int* count, const uint
     flag[k] = flag2[2 * i + 1];
 }
 
-// mean |thumb[k] - thumb[k-1]| over the 2304 samples, 0 for k = 0
-__global__ void __launch_bounds__(256) thumb_diff_kernel(const uint8_t* thumbs, int64_t n, float* diff) {
-    const int64_t k = blockIdx.x;
-    if (k >= n) return;
-    __shared__ unsigned part[8];
+// Sum of |thumb[k] - thumb[k-1]| over the 2304 samples (0 for k = 0), by one
+// warp: each lane takes 16-byte pieces of both thumbnails (4-byte pieces when
+// the array is only 4-byte aligned); the total is in every lane.
+__device__ __forceinline__ unsigned thumb_l1(const uint8_t* thumbs, int64_t k, int lane) {
     unsigned s = 0;
     if (k > 0) {
-        const uint32_t* a = reinterpret_cast<const uint32_t*>(thumbs + k * 2304);
-        const uint32_t* b = reinterpret_cast<const uint32_t*>(thumbs + (k - 1) * 2304);
-        for (int i = threadIdx.x; i < 576; i += 256) s = __vsadu4(a[i], b[i]) + s;
+        if ((reinterpret_cast<uintptr_t>(thumbs) & 15u) == 0) {
+            const uint4* a = reinterpret_cast<const uint4*>(thumbs + k * 2304);
+            const uint4* b = reinterpret_cast<const uint4*>(thumbs + (k - 1) * 2304);
+#pragma unroll
+            for (int i = lane; i < 144; i += 32) {
+                const uint4 x = a[i], y = b[i];
+                s = __vsadu4(x.x, y.x) + __vsadu4(x.y, y.y) + __vsadu4(x.z, y.z) + __vsadu4(x.w, y.w) + s;
+            }
+        } else {
+            const uint32_t* a = reinterpret_cast<const uint32_t*>(thumbs + k * 2304);
+            const uint32_t* b = reinterpret_cast<const uint32_t*>(thumbs + (k - 1) * 2304);
+            for (int i = lane; i < 576; i += 32) s = __vsadu4(a[i], b[i]) + s;
+        }
     }
-    s = __reduce_add_sync(0xffffffffu, s);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = 0;
-        for (int w = 0; w < 8; ++w) t += part[w];
-        diff[k] = static_cast<float>(t) / 2304.f;
-    }
+    return __reduce_add_sync(0xffffffffu, s);
+}
+
+constexpr int kDiffWarps = 8;  // frames per 256-thread block, one warp each
+
+// mean |thumb[k] - thumb[k-1]| over the 2304 samples, 0 for k = 0
+__global__ void __launch_bounds__(32 * kDiffWarps) thumb_diff_kernel(const uint8_t* thumbs, int64_t n, float* diff) {
+    const int64_t k = blockIdx.x * static_cast<int64_t>(kDiffWarps) + (threadIdx.x >> 5);
+    if (k >= n) return;
+    const unsigned t = thumb_l1(thumbs, k, threadIdx.x & 31);
+    if ((threadIdx.x & 31) == 0) diff[k] = static_cast<float>(t) / 2304.f;
 }
 
 // Cascade prefilter, in the thumbnail-difference launch: d_diff[k] as
 // thumb_diff_kernel writes it, every gate value set below any threshold, and
 // each pair whose difference exceeds tau_diff listed for the network
 // (thumbnail indices k-1, k, whose logit goes to gate element k).
-__global__ void __launch_bounds__(256) diff_prefilter_kernel(const uint8_t* thumbs, int64_t n, float tau_diff,
-                                                             float* diff, float* gate, int32_t* prev, int32_t* cur,
-                                                             int32_t* elem, int* count) {
-    const int64_t k = blockIdx.x;
+__global__ void __launch_bounds__(32 * kDiffWarps) diff_prefilter_kernel(const uint8_t* thumbs, int64_t n,
+                                                                         float tau_diff, float* diff, float* gate,
+                                                                         int32_t* prev, int32_t* cur, int32_t* elem,
+                                                                         int* count) {
+    const int64_t k = blockIdx.x * static_cast<int64_t>(kDiffWarps) + (threadIdx.x >> 5);
     if (k >= n) return;
-    __shared__ unsigned part[8];
-    unsigned s = 0;
-    if (k > 0) {
-        const uint32_t* a = reinterpret_cast<const uint32_t*>(thumbs + k * 2304);
-        const uint32_t* b = reinterpret_cast<const uint32_t*>(thumbs + (k - 1) * 2304);
-        for (int i = threadIdx.x; i < 576; i += 256) s = __vsadu4(a[i], b[i]) + s;
-    }
-    s = __reduce_add_sync(0xffffffffu, s);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = 0;
-        for (int w = 0; w < 8; ++w) t += part[w];
+    const unsigned t = thumb_l1(thumbs, k, threadIdx.x & 31);
+    if ((threadIdx.x & 31) == 0) {
         const float dk = static_cast<float>(t) / 2304.f;
         diff[k] = dk;
         gate[k] = -INFINITY;
@@ -191,7 +193,8 @@ scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, voi
     if (n == 0) return SCN_OK;
     if (!d_thumbs || !d_diff || (reinterpret_cast<uintptr_t>(d_thumbs) & 3u)) return SCN_EINVAL;
     if (n > 0x7fffffff) return SCN_ERANGE;
-    thumb_diff_kernel<<<static_cast<unsigned>(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_thumbs, n, d_diff);
+    thumb_diff_kernel<<<static_cast<unsigned>((n + kDiffWarps - 1) / kDiffWarps), 32 * kDiffWarps, 0,
+                        static_cast<cudaStream_t>(stream)>>>(d_thumbs, n, d_diff);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }
@@ -285,9 +288,8 @@ scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, flo
     st = scn_thumbs(s, d_thumbs, stream);
     if (st != SCN_OK) return st;
     SCN_CUDA_TRY(cudaMemsetAsync(ws->pre_count, 0, sizeof(int), cs));
-    diff_prefilter_kernel<<<static_cast<unsigned>(s->n), 256, 0, cs>>>(d_thumbs, s->n, tau_diff, d_diff, d_gate,
-                                                                      ws->pre_prev, ws->pre_cur, ws->pre_elem,
-                                                                      ws->pre_count);
+    diff_prefilter_kernel<<<static_cast<unsigned>((s->n + kDiffWarps - 1) / kDiffWarps), 32 * kDiffWarps, 0, cs>>>(
+        d_thumbs, s->n, tau_diff, d_diff, d_gate, ws->pre_prev, ws->pre_cur, ws->pre_elem, ws->pre_count);
     SCN_CUDA_TRY(cudaGetLastError());
     if (s->n > 1) {
         // the network only on the listed pairs (the launch is sized for all n-1 and reads the

@@ -96,6 +96,13 @@ def test_thumb_diff(scn, orc, tiny):
     t = th.cpu().numpy().astype(np.int64)
     ref = np.concatenate([[0.0], np.abs(np.diff(t, axis=0)).sum(axis=(1, 2)) / 2304.0])
     assert np.allclose(d.cpu().numpy(), ref, rtol=1e-6, atol=1e-6)
+    # a 4-byte-aligned (not 16-byte-aligned) array takes the narrow-load path: same values
+    raw = torch.zeros(T * 2304 + 16, dtype=torch.uint8, device="cuda")
+    off = raw[4:4 + T * 2304]
+    off.copy_(th.reshape(-1))
+    d4 = torch.empty(T, dtype=torch.float32, device="cuda")
+    scn.scn_thumb_diff(off, T, d4)
+    assert torch.equal(d4, d)
 
 
 def test_learned_proposal_path_consistent(scn, tiny):
