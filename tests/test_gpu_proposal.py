@@ -180,7 +180,8 @@ def test_learned_gate_gains_over_thumbnail_difference(scn):
     """Full workload: train on 201,572 pairs (28 videos), pick thresholds on 8
     held-out videos, evaluate on 100,800 fresh 1080p frames.  The learned gate
     reaches >= 99% recall of the exact detector's boundaries and proposes fewer
-    non-boundaries than the thumbnail-difference gate under the same rule."""
+    non-boundaries than the thumbnail-difference gate under the same rule; the
+    cascade keeps >= 99% recall and is faster than the difference gate alone."""
     from paper_1805_07339_b300 import proposal
     res = proposal.run(torch)
     L, D = res["learned"], res["diff"]
@@ -195,3 +196,6 @@ def test_learned_gate_gains_over_thumbnail_difference(scn):
     C = res["cascade"]
     assert C["exact_on_proposed"] and C["recall"] >= 0.99
     assert C["proposed"] <= D["proposed"] and C["precision"] > D["precision"]
+    # and what the network gains: the exact pass it saves costs more than its forward on the
+    # prefiltered pairs, so the cascade beats the difference gate alone end to end
+    assert C["speedup"] > D["speedup"]
