@@ -12,7 +12,7 @@ import argparse
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("kernel", choices=["hist", "resize", "thumbs", "proposal"])
+    ap.add_argument("kernel", choices=["hist", "resize", "thumbs", "proposal", "cascade"])
     ap.add_argument("--frames", type=int, default=512)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--stride", type=int, default=1)
@@ -48,6 +48,28 @@ def main() -> None:
         o = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
         for _ in range(a.reps):
             scn.scn_thumbs(seq, o)
+    elif a.kernel == "cascade":
+        # cascade proposal path with He-uniform weights: the difference prefilter at the
+        # 98.5% quantile of this video's differences, the network threshold at its median
+        from .proposal import he_uniform
+        net = scn.scn_cnn_create(8)
+        scn.scn_cnn_set_params(net, he_uniform(0))
+        th = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
+        d = torch.empty(n, dtype=torch.float32, device="cuda")
+        z = torch.empty(max(n - 1, 1), dtype=torch.float32, device="cuda")
+        scn.scn_thumbs(seq, th)
+        scn.scn_thumb_diff(th, n, d)
+        scn.scn_cnn_forward(net, th, n - 1, z)
+        tau_d = float(torch.quantile(d[1:], 0.985).item())
+        tau_n = float(torch.quantile(z[:n - 1], 0.5).item())
+        g = torch.empty(n, dtype=torch.float32, device="cuda")
+        pr = torch.empty(n, dtype=torch.uint8, device="cuda")
+        sc = torch.empty(n, dtype=torch.int32, device="cuda")
+        fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_cascade_hist_scores(seq, net, tau_d, tau_n, th, d, g, pr, sc, fl)
+        assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
+        scn.scn_cnn_destroy(net)
     else:
         # learned proposal path with He-uniform weights and a threshold that
         # proposes about 1% of the pairs
