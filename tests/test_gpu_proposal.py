@@ -163,6 +163,44 @@ def test_cascade_matches_its_two_thresholds(scn, tiny, q_diff, q_net):
         scn.scn_cnn_destroy(net)
 
 
+@pytest.mark.parametrize("n", [0, 1, 2, 3])
+def test_cascade_short_sequences(scn, tiny, n):
+    """0 elements: nothing written; 1: no pair, nothing proposed, no network launch;
+    2-3: one or two pairs, each proposed exactly when both thresholds pass."""
+    from paper_1805_07339_b300.proposal import he_uniform
+    buf = tiny["buf"]
+    W, H = 320, 180
+    t = scn.scn_table_create(buf, W, H, tiny["T"])
+    seq = scn.scn_sample(t, scn.SCN_STRIDE, start=10, stop=10 + n, step=1)
+    net = scn.scn_cnn_create(8)
+    try:
+        scn.scn_cnn_set_params(net, he_uniform(4))
+        m = max(n, 1)
+        th = torch.full((m, 36, 64), 7, dtype=torch.uint8, device="cuda")
+        d = torch.full((m,), 5.0, dtype=torch.float32, device="cuda")
+        gate = torch.full((m,), 5.0, dtype=torch.float32, device="cuda")
+        prop, sc, fl = (torch.full((m,), 9, dtype=torch.uint8, device="cuda"), torch.full((m,), 9, dtype=torch.int32, device="cuda"),
+                        torch.full((m,), 9, dtype=torch.uint8, device="cuda"))
+        cnt = scn.scn_cascade_hist_scores(seq, net, -1.0, -1e30, th, d, gate, prop, sc, fl)
+        torch.cuda.synchronize()
+        if n == 0:
+            assert cnt == 0 and int(prop[0]) == 9 and float(gate[0]) == 5.0
+            return
+        # every difference passes -1 and every logit passes -1e30: all n-1 pairs proposed
+        assert cnt == n - 1 and prop.cpu().numpy().tolist() == [0] + [1] * (n - 1)
+        g = gate.cpu().numpy()
+        assert np.isneginf(g[0]) and np.all(np.isfinite(g[1:]))
+        h = torch.empty((n, 48), dtype=torch.int32, device="cuda")
+        s2, f2 = torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.uint8, device="cuda")
+        scn.scn_hist_scores(seq, h, s2, f2)
+        torch.cuda.synchronize()
+        assert torch.equal(sc, s2) and torch.equal(fl, f2)
+    finally:
+        scn.scn_cnn_destroy(net)
+        scn.scn_seq_destroy(seq)
+        scn.scn_table_destroy(t)
+
+
 def test_training_pipeline_small(scn):
     """A short GPU training run on two 1080p videos: the loss falls, the gated
     path stays exact on proposed pairs, and the report is complete."""
