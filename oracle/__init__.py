@@ -174,17 +174,6 @@ def sample(kind: int, num_frames: int, start: int = 0, stop: int = 0, step: int 
     raise ValueError("unknown sampling kind")
 
 
-def floyd_sample(seed: int, num_frames: int, m: int) -> np.ndarray:
-    """m distinct frame indices by Floyd's algorithm driven by SM(seed, .), sorted."""
-    chosen: set[int] = set()
-    c = 0
-    for j in range(num_frames - m, num_frames):
-        t = sm(seed, c) % (j + 1)
-        c += 1
-        chosen.add(t if t not in chosen else j)
-    return np.array(sorted(chosen), dtype=np.int64)
-
-
 # --------------------------------------------------------------------------- pixel math
 def yuv_to_rgb(Y: int, U: int, V: int) -> tuple[int, int, int]:
     out = (ctypes.c_int32 * 3)()

@@ -56,6 +56,49 @@ def test_conversion_within_one_level_of_float_matrix_exhaustive(orc):
     assert worst <= 1
 
 
+def _bt601_fixed_point_coefficients():
+    """The five x256 integer coefficients of 8-bit BT.601 limited-range YCbCr -> RGB,
+    derived from the standard's luma weights Kr = 0.299, Kb = 0.114 and the 219-level
+    luma / 224-level chroma excursions: round(256 * matrix entry)."""
+    Kr, Kb = 0.299, 0.114
+    Kg = 1 - Kr - Kb
+    sy, sc = 255.0 / 219.0, 255.0 / 224.0
+    entries = {
+        "Y": sy,                                # R, G, B from luma
+        "R_Cr": 2 * (1 - Kr) * sc,               # R from Cr
+        "G_Cb": 2 * (1 - Kb) * Kb / Kg * sc,     # G from Cb (subtracted)
+        "G_Cr": 2 * (1 - Kr) * Kr / Kg * sc,     # G from Cr (subtracted)
+        "B_Cb": 2 * (1 - Kb) * sc,               # B from Cb
+    }
+    return {k: int(np.floor(256 * v + 0.5)) for k, v in entries.items()}
+
+
+def test_fixed_point_coefficients_from_kr_kb():
+    c = _bt601_fixed_point_coefficients()
+    # the values that every integer BT.601 implementation with x256 scaling uses
+    assert c == {"Y": 298, "R_Cr": 409, "G_Cb": 100, "G_Cr": 208, "B_Cb": 516}
+
+
+def test_conversion_exact_against_derived_fixed_point_exhaustive(orc):
+    """Every (Y, U, V) byte triple: the oracle equals the fixed-point form built from
+    the coefficients derived above, C = Y-16, D = U-128, E = V-128,
+    value = clamp((coef . (C, D, E) + 128) >> 8, 0, 255) with an arithmetic shift."""
+    c = _bt601_fixed_point_coefficients()
+    Y, V = np.meshgrid(np.arange(256, dtype=np.int64), np.arange(256, dtype=np.int64), indexing="ij")
+    Y, V = Y.ravel(), V.ravel()
+    C, E = Y - 16, V - 128
+    for U in range(256):
+        D = U - 128
+        yuv = np.stack([Y, np.full_like(Y, U), V], axis=1).astype(np.uint8)
+        got = orc.yuv_to_rgb_array(yuv).astype(np.int64)
+        R = np.clip((c["Y"] * C + c["R_Cr"] * E + 128) >> 8, 0, 255)
+        G = np.clip((c["Y"] * C - c["G_Cb"] * D - c["G_Cr"] * E + 128) >> 8, 0, 255)
+        B = np.clip((c["Y"] * C + c["B_Cb"] * D + 128) >> 8, 0, 255)
+        assert np.array_equal(got[:, 0], R), U
+        assert np.array_equal(got[:, 1], G), U
+        assert np.array_equal(got[:, 2], B), U
+
+
 def test_hist_identity_clamp_shift():
     # the kernel folds clamp(x >> 8, 0, 255) >> 4 into clamp(x >> 12, 0, 15)
     x = np.arange(-(1 << 20), 1 << 20, dtype=np.int64)
