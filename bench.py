@@ -34,11 +34,16 @@ WORKLOAD = ("1080p NV12 video, 7200 frames (22.4 GB), 60 shots; per step: hist+s
 FRAME_BYTES = 1920 * 1080 * 3 // 2
 ALG_BYTES_PER_FRAME = FRAME_BYTES + 48 * 4 + 4 + 1  # NV12 read + hist, score, flag written
 
-# DRAM traffic of hist_kernel from one ncu capture (profiles/hist_kernel_1080p_512frames.md:
-# dram__bytes_read.sum + dram__bytes_write.sum over 512 frames), per frame; it scales with the
-# frames of a launch.  Valid only for the kernel sources it was taken on (hash below).
+# DRAM traffic of hist_kernel from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
+# over the first 512 frames of the 1080p video), per frame; it scales with the frames of a
+# launch.  Valid only for the kernel sources it was taken on (hash below).
 PROFILED_TRAFFIC = {"bytes_per_frame": 3116722.5, "frames_captured": 512,
                     "sources": ("scn_hist.cu", "scn_internal.h", "scn_ptx.cuh"), "sha256_16": "31db3e72fd06edeb"}
+
+
+# the HBM3e figure the ncu DRAM peak is quoted against ("roughly 8 TB/s"); the measured copy
+# peak of MEASURED_PEAKS.json is the lower, i.e. more lenient, denominator
+NOMINAL_HBM_GBS = 8000.0
 
 
 def profiled_traffic(frames: int):
@@ -65,7 +70,124 @@ def parse():
     ap.add_argument("--no-proposal", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-state", action="store_true")
+    # single-kernel runs for profiling (see run_case)
+    ap.add_argument("--case", choices=["hist", "resize", "thumbs", "proposal", "cascade"])
+    ap.add_argument("--frames", type=int, default=512)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--stride", type=int, default=1)
+    ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--chunk-rows", type=int, default=0)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
     return ap.parse_args()
+
+
+_PROBE = []
+
+
+def probe_lib():
+    """The measurement-only library with the shared-memory reduction probe
+    (libscn_probe.so, outside libscn.so's C ABI), built if needed."""
+    import ctypes
+    from paper_1805_07339_b300 import build
+    if _PROBE:
+        return _PROBE[0]
+    lib = ctypes.CDLL(build.build_probe())
+    _PROBE.append(lib)
+    lib.scn_probe_shared_reductions.restype = ctypes.c_int32
+    lib.scn_probe_shared_reductions.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    return lib
+
+
+def probe_shared_reductions(iters: int, grid: int, cycles, stream=None) -> None:
+    """cycles: CUDA int64 tensor of `grid` entries; entry b = CTA b's SM cycles for
+    20 warps x 8 x iters warp-wide shared-memory reductions."""
+    import torch
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    rc = probe_lib().scn_probe_shared_reductions(iters, grid, cycles.data_ptr(), st)
+    if rc != 0:
+        raise RuntimeError(f"scn_probe_shared_reductions: status {rc}")
+
+
+def run_case(a) -> None:
+    """Small, self-contained runs of single kernels, for profiling with ncu:
+        python bench.py --case hist --frames 512 --reps 3
+    runs the fused hist+score kernel over the first `frames` frames of a 1080p video
+    generated on the device, `reps` times.  Sizes stay a few GB so that a profiler
+    capture ends by itself."""
+    import torch
+    from paper_1805_07339_b300 import scn
+    from paper_1805_07339_b300.workloads import MASTER_SEED
+    W, H, T = a.width, a.height, a.frames
+    fb = W * H * 3 // 2
+    v = scn.scn_video_create(MASTER_SEED, 0, W, H, T, max(1, T // 120))
+    buf = torch.empty(T * fb, dtype=torch.uint8, device="cuda")
+    scn.scn_generate(v, buf, 0, T, fb)
+    t = scn.scn_table_create(buf, W, H, T)
+    seq = scn.scn_sample(t, scn.SCN_STRIDE, start=0, stop=T, step=a.stride)
+    n = scn.scn_seq_length(seq)
+    if a.grid or a.chunk_rows:
+        scn.scn_seq_set_tune(seq, chunk_rows=a.chunk_rows, grid=a.grid)
+    if a.case == "hist":
+        h = torch.empty((n, 48), dtype=torch.int32, device="cuda")
+        s = torch.empty(n, dtype=torch.int32, device="cuda")
+        f = torch.empty(n, dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_hist_scores(seq, h, s, f)
+    elif a.case == "resize":
+        o = torch.empty((n, 3, 224, 224), dtype=torch.float32, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_resize_norm(seq, 224, 224, (0.485, 0.456, 0.406), (0.229, 0.224, 0.225), scn.SCN_F32, o)
+    elif a.case == "thumbs":
+        o = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_thumbs(seq, o)
+    elif a.case == "cascade":
+        # cascade proposal path with He-uniform weights: the difference prefilter at the
+        # 98.5% quantile of this video's differences, the network threshold at its median
+        from paper_1805_07339_b300.proposal import he_uniform
+        net = scn.scn_cnn_create(8)
+        scn.scn_cnn_set_params(net, he_uniform(0))
+        th = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
+        d = torch.empty(n, dtype=torch.float32, device="cuda")
+        z = torch.empty(max(n - 1, 1), dtype=torch.float32, device="cuda")
+        scn.scn_thumbs(seq, th)
+        scn.scn_thumb_diff(th, n, d)
+        scn.scn_cnn_forward(net, th, n - 1, z)
+        tau_d = float(torch.quantile(d[1:], 0.985).item())
+        tau_n = float(torch.quantile(z[:n - 1], 0.5).item())
+        g = torch.empty(n, dtype=torch.float32, device="cuda")
+        pr = torch.empty(n, dtype=torch.uint8, device="cuda")
+        sc = torch.empty(n, dtype=torch.int32, device="cuda")
+        fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_cascade_hist_scores(seq, net, tau_d, tau_n, th, d, g, pr, sc, fl)
+        assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
+        scn.scn_cnn_destroy(net)
+    else:
+        # learned proposal path with He-uniform weights and a threshold that
+        # proposes about 1% of the pairs
+        from paper_1805_07339_b300.proposal import he_uniform
+        net = scn.scn_cnn_create(4096)
+        scn.scn_cnn_set_params(net, he_uniform(0))
+        th = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
+        z = torch.full((n,), -1e30, dtype=torch.float32, device="cuda")
+        scn.scn_thumbs(seq, th)
+        scn.scn_cnn_forward(net, th, n - 1, z[1:])
+        tau = float(torch.quantile(z[1:], 0.99).item())
+        pr = torch.empty(n, dtype=torch.uint8, device="cuda")
+        sc = torch.empty(n, dtype=torch.int32, device="cuda")
+        fl = torch.empty(n, dtype=torch.uint8, device="cuda")
+        for _ in range(a.reps):
+            scn.scn_proposal_hist_scores(seq, net, tau, th, z, pr, sc, fl)
+        assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
+        scn.scn_cnn_destroy(net)
+    torch.cuda.synchronize()
+    assert scn.scn_seq_sync_status(seq) == scn.SCN_OK
+    scn.scn_seq_destroy(seq)
+    scn.scn_table_destroy(t)
+    scn.scn_video_destroy(v)
+    print(f"ok {a.case} frames={n}")
 
 
 def dist_env():
@@ -245,6 +367,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.case:
+        run_case(args)
+        return
     import numpy as np
     import torch
     rank, world, local = dist_env()
@@ -343,6 +468,7 @@ def main():
     dom = kern["stride1"]
     roofline = {"bound": "hbm", "achieved": dom["GB_per_s"], "peak": peak, "unit": "GB/s",
                 "frac": dom["GB_per_s"] / peak, "traffic": profiled_traffic(dom["frames"]), "peak_source": peak_kind,
+                "frac_vs_nominal": dom["GB_per_s"] / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS,
                 "kernel": "hist_kernel (scn_hist_scores, stride-1, 7200 frames)",
                 "alg_bytes_per_launch": dom["frames"] * ALG_BYTES_PER_FRAME}
     roofline["binding_unit"] = binding_unit(scn, torch, np, dom, W * H, clk, stream)
@@ -454,7 +580,7 @@ def binding_unit(scn, torch, np, dom: dict, px_per_frame: int, clk: dict, stream
     cyc = torch.zeros(sms, dtype=torch.int64, device="cuda")
     peak = 0.0
     for _ in range(reps):
-        scn.scn_probe_shared_reductions(iters, sms, cyc, stream)
+        probe_shared_reductions(iters, sms, cyc, stream)
         torch.cuda.synchronize()
         peak = max(peak, 20 * 8 * iters / float(np.median(cyc.cpu().numpy())))
     mhz, src = clk.get("sm_mhz"), "median SM clock sampled during the timed region"

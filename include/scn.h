@@ -457,21 +457,6 @@ scn_status scn_resize_norm_both(scn_seq* s, int32_t out_h, int32_t out_w, const 
  * (requires W == 64*s and H == 36*s); output uint8 [n][36][64]. */
 scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream);
 
-/* ------------------------------------------------------------------------ */
-/* Measurement (the paper has no counterpart: this measures the hardware     */
-/* ceiling that the fused histogram kernel's roofline is stated against).  */
-/* ------------------------------------------------------------------------ */
-/* The fused hist kernel counts each pixel with three shared-memory
- * reductions, one warp-wide conflict-free wavefront per 32 pixel-channels, and
- * that unit, not HBM, sets its pace.  This launches `grid` CTAs of the hist
- * kernel's shape (672 threads, its 174,080-byte table) in which each of the 20
- * counting warps issues 8 * iters red.shared.add.u32 in the kernel's table
- * layout and nothing else; d_cycles[b] (device, 8-byte aligned, `grid`
- * entries) receives CTA b's elapsed SM clock cycles over that loop, so
- * 160 * iters / d_cycles[b] is the warp reductions per SM clock.  iters in
- * [1, 2^20], grid in [1, 65535], else SCN_EINVAL.  Asynchronous on stream. */
-scn_status scn_probe_shared_reductions(int32_t iters, int32_t grid, unsigned long long* d_cycles, void* stream);
-
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libscn.so")
+# measurement-only library (the shared-memory reduction probe), outside libscn.so's C ABI
+PROBE_SRC = os.path.join(CSRC, "measure", "scn_probe.cu")
+PROBE_LIB = os.path.join(HERE, "libscn_probe.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
@@ -62,6 +65,19 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     subprocess.check_call(cmd)
     os.replace(LIB + ".tmp", LIB)
     return LIB
+
+
+def build_probe(force: bool = False) -> str:
+    """Compile the measurement probe into its own library (libscn_probe.so)."""
+    hdrs = sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")))
+    if not force and os.path.exists(PROBE_LIB) and all(
+            os.path.getmtime(p) <= os.path.getmtime(PROBE_LIB) for p in [PROBE_SRC, __file__, *hdrs]):
+        return PROBE_LIB
+    cmd = [NVCC, *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-shared", "-cudart", "shared",
+           "-o", PROBE_LIB + ".tmp", PROBE_SRC]
+    subprocess.check_call(cmd)
+    os.replace(PROBE_LIB + ".tmp", PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

@@ -9,10 +9,25 @@
 // nothing else to do, and times them with the SM's own cycle counter, so the
 // rate it returns (warp reductions per SM clock) is the ceiling the fused
 // kernel's own rate is compared with.
+//
+// Measurement only: built into its own library (libscn_probe.so), outside the
+// C ABI of libscn.so; the benchmark and its test load it.  The paper has no
+// counterpart.
+//
+//   int scn_probe_shared_reductions(int32_t iters, int32_t grid,
+//                                   unsigned long long* d_cycles, void* stream)
+// launches `grid` CTAs of the hist kernel's shape (672 threads, its 174,080-byte
+// table) in which each of the 20 counting warps issues 8 * iters
+// red.shared.add.u32 in the kernel's table layout and nothing else; d_cycles[b]
+// (device, 8-byte aligned, `grid` entries) receives CTA b's elapsed SM clock
+// cycles over that loop, so 160 * iters / d_cycles[b] is the warp reductions
+// per SM clock.  Returns 0 (launched, asynchronous on `stream`), 1 for iters
+// outside [1, 2^20], grid outside [1, 65535] or a null / misaligned d_cycles,
+// 4 for a CUDA error (the status numbering of scn.h).
 #include <cuda_runtime.h>
 
-#include "scn_internal.h"
-#include "scn_ptx.cuh"
+#include "../scn_internal.h"
+#include "../scn_ptx.cuh"
 
 namespace scn {
 namespace {
@@ -48,16 +63,16 @@ __global__ void __launch_bounds__(kHistThreads, 1) red_probe_kernel(int32_t iter
 
 extern "C" {
 
-scn_status scn_probe_shared_reductions(int32_t iters, int32_t grid, unsigned long long* d_cycles, void* stream) {
+int scn_probe_shared_reductions(int32_t iters, int32_t grid, unsigned long long* d_cycles, void* stream) {
     if (iters < 1 || iters > (1 << 20) || grid < 1 || grid > 65535 || !d_cycles) return SCN_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_cycles) & 7u) return SCN_EINVAL;
     const size_t smem = static_cast<size_t>(scn::kTabBytes);
-    SCN_CUDA_TRY(cudaFuncSetAttribute(scn::red_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem)));
+    if (cudaFuncSetAttribute(scn::red_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+        return SCN_ECUDA;
     scn::red_probe_kernel<<<static_cast<unsigned>(grid), scn::kHistThreads, smem, static_cast<cudaStream_t>(stream)>>>(
         iters, d_cycles);
-    SCN_CUDA_TRY(cudaGetLastError());
-    return SCN_OK;
+    return cudaGetLastError() == cudaSuccess ? SCN_OK : SCN_ECUDA;
 }
 
 }  // extern "C"

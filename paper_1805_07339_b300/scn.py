@@ -116,7 +116,6 @@ SIGNATURES = [
     ("scn_shot_scores_sliced", c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
     ("scn_montage", c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_i32, c_vp, c_vp]),
     ("scn_window_scores", c_i32, [c_vp, c_i64, c_i64, c_i64, c_i32, c_i32, c_i64, c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
-    ("scn_probe_shared_reductions", c_i32, [c_i32, c_i32, c_vp, c_vp]),
     ("scn_bounded_state_scores", c_i32, [c_vp, c_i64, c_i64, c_i64, c_i64, c_i32, c_i64, c_i64, c_i64, c_i64, c_i64,
                                          c_vp, c_vp, c_vp, c_vp]),
 ]
@@ -526,9 +525,3 @@ def scn_bounded_state_scores(hist, hist_first: int, hist_count: int, n: int, pix
                                          run_first, run_len, run_stride, runs, _ptr(boundary), _ptr(score),
                                          _ptr(flag), _stream(stream)), "scn_bounded_state_scores")
 
-
-def scn_probe_shared_reductions(iters: int, grid: int, cycles, stream=None) -> None:
-    """cycles: CUDA int64 tensor of `grid` entries; entry b = CTA b's SM cycles for
-    20 warps x 8 x iters warp-wide shared-memory reductions."""
-    _check(_lib.scn_probe_shared_reductions(iters, grid, _ptr(cycles), _stream(stream)),
-           "scn_probe_shared_reductions")
