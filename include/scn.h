@@ -166,8 +166,22 @@ scn_status scn_sample(const scn_table* t, const scn_sample_spec* spec, scn_seq**
 scn_status scn_seq_length(const scn_seq* s, int64_t* n);
 scn_status scn_seq_destroy(scn_seq* s);
 /* Synchronise stream, read and clear the sequence's device status word.
- * Returns SCN_OK or SCN_ETIMEOUT. */
+ * Returns SCN_OK or SCN_ETIMEOUT.  On SCN_ETIMEOUT it also zeroes the
+ * sequence's kernel scratch (cross-CTA partial histograms, frame and pair
+ * counters, work queue) and its gated-path workspace, which a launch that gave
+ * up may have left part-way, so the next call on the sequence starts clean;
+ * the outputs of the launch that timed out are undefined. */
 scn_status scn_seq_sync_status(scn_seq* s, void* stream);
+/* Test hook for the bounded device waits (the paper has no counterpart; it
+ * exercises the status-word path of the conventions above without faulting or
+ * hanging the GPU).  Later scn_hist / scn_hist_scores launches of this sequence
+ * wait at most wait_limit_ns at each bounded wait (0 restores the default 2 s;
+ * otherwise it must lie in [1e5, 1e10] ns, else SCN_EINVAL), and with
+ * withhold_after = k >= 0 each CTA's producer hands out k chunks of work and
+ * then withholds the rest, so the consumers' waits run out: the launch ends by
+ * itself with SCN_ETIMEOUT in the status word and undefined outputs.
+ * withhold_after < 0 restores normal operation.  Host-only setter. */
+scn_status scn_seq_set_wait_test(scn_seq* s, uint64_t wait_limit_ns, int32_t withhold_after);
 
 /* ------------------------------------------------------------------------ */
 /* Launch shape of the fused kernel (chosen automatically when a field is 0). */
@@ -248,7 +262,9 @@ scn_status scn_plan_run(scn_plan* p, void* stream);
  * legacy default stream); scn_plan_replay launches it. */
 scn_status scn_plan_capture_graph(scn_plan* p, void* stream);
 scn_status scn_plan_replay(scn_plan* p, void* stream);
-/* Synchronise stream, read and clear the plan's device status word. */
+/* Synchronise stream, read and clear the plan's device status word; on
+ * SCN_ETIMEOUT also zero the plan's work queue and the kernel scratch of each
+ * of its sequences (see scn_seq_sync_status). */
 scn_status scn_plan_sync_status(scn_plan* p, void* stream);
 /* Autotuner: time candidate shapes (item size x chunk rows) with `reps`
  * runs each on stream (synchronous), keep the fastest; returns it and its

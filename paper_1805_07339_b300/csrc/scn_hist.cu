@@ -84,6 +84,7 @@ struct Smem {
     uint32_t* acc;      // [48]
     uint64_t* full;     // [kStages]
     uint64_t* empty;    // [kStages]
+    uint64_t* cbar;     // consumers' CTA barrier (every consumer thread arrives)
     int* abort_flag;
 };
 
@@ -94,12 +95,18 @@ __device__ __forceinline__ Smem carve(uint8_t* smem) {
     s.acc = reinterpret_cast<uint32_t*>(s.meta + kStages);
     s.full = reinterpret_cast<uint64_t*>(s.acc + 64);
     s.empty = s.full + kStages;
-    s.abort_flag = reinterpret_cast<int*>(s.empty + kStages);
+    s.cbar = s.empty + kStages;
+    s.abort_flag = reinterpret_cast<int*>(s.cbar + 1);
     return s;
 }
-static_assert(kStages * sizeof(ChunkMeta) + 64 * 4 + 2 * kStages * 8 + 16 <= kSmemMisc, "misc smem");
+static_assert(kStages * sizeof(ChunkMeta) + 64 * 4 + (2 * kStages + 1) * 8 + 16 <= kSmemMisc, "misc smem");
 
 __device__ __forceinline__ const Job& job_of(const Launch& L, int j) { return L.jobs ? L.jobs[j] : L.job0; }
+
+// how long a bounded wait of this launch waits before it gives up
+__device__ __forceinline__ uint64_t wait_limit(const Launch& L) {
+    return L.wait_limit_ns ? L.wait_limit_ns : kWaitLimitNs;
+}
 
 // elements of job0 when its count lives on the device
 __device__ __forceinline__ int64_t device_elems(const Launch& L) {
@@ -138,7 +145,7 @@ __device__ __forceinline__ bool stage_chunk(const Launch& L, const Smem& s, uint
                                             int rows, bool seg_end, int seg_rp) {
     const uint32_t st = it % kStages;
     if (it >= static_cast<uint32_t>(kStages)) {
-        if (!ptx::mbar_wait_bounded(&s.empty[st], ((it / kStages) - 1) & 1u, kWaitLimitNs)) {
+        if (!ptx::mbar_wait_bounded(&s.empty[st], ((it / kStages) - 1) & 1u, wait_limit(L))) {
             fail(L, s);
             return false;
         }
@@ -154,8 +161,16 @@ __device__ __forceinline__ bool stage_chunk(const Launch& L, const Smem& s, uint
     return true;
 }
 
+// Test hook: with withhold_after = k >= 0 the producer hands out k chunks and
+// then nothing more (no end marker either), so the consumers' bounded waits run
+// out and the launch ends with the timeout bit in the status word.
+__device__ __forceinline__ bool withheld(const Launch& L, uint32_t it) {
+    return L.withhold_after >= 0 && it >= static_cast<uint32_t>(L.withhold_after);
+}
+
 __device__ void produce(const Launch& L, const Smem& s) {
     uint32_t it = 0;
+    bool stop = false;  // withheld (test hook)
     if (L.rp_per_cta != 0) {
         // Contiguous split of job0's row pairs: every CTA does the same work and
         // flushes only at frame edges or every item_rp row pairs (16-bit bound).
@@ -169,6 +184,10 @@ __device__ void produce(const Launch& L, const Smem& s) {
         int rp = static_cast<int>(g - k * hp);
         int seg = 0;
         while (g < g_end && !aborted(s)) {
+            if (withheld(L, it)) {
+                stop = true;
+                break;
+            }
             int m = min(crp, hp - rp);
             if (g_end - g < m) m = static_cast<int>(g_end - g);
             m = min(m, srp - seg);
@@ -186,7 +205,7 @@ __device__ void produce(const Launch& L, const Smem& s) {
         }
     } else {
         const int64_t n_items = L.d_count ? device_elems(L) * L.job0.items_per_frame : L.n_items;
-        while (!aborted(s)) {
+        while (!aborted(s) && !stop) {
             const uint64_t i = atomicAdd(reinterpret_cast<unsigned long long*>(L.queue), 1ull);
             if (i >= static_cast<uint64_t>(n_items)) break;
             const Item item = item_at(L, static_cast<int64_t>(i));
@@ -194,6 +213,10 @@ __device__ void produce(const Launch& L, const Smem& s) {
             const int r_end = 2 * (item.rp0 + item.nrp);
             bool ok = true;
             for (int r = 2 * item.rp0; r < r_end && ok && !aborted(s); r += J.chunk_rows) {
+                if (withheld(L, it)) {
+                    stop = true;
+                    break;
+                }
                 const int rows = min(J.chunk_rows, r_end - r);
                 ok = stage_chunk(L, s, it, item.job, item.k, r, rows, r + rows == r_end, item.nrp);
                 if (ok) ++it;
@@ -208,11 +231,11 @@ __device__ void produce(const Launch& L, const Smem& s) {
         }
     }
     // Tell the consumers: a descriptor with job = -1.
-    if (!aborted(s)) {
+    if (!aborted(s) && !stop) {
         const uint32_t st = it % kStages;
         bool ok = true;
         if (it >= static_cast<uint32_t>(kStages)) {
-            ok = ptx::mbar_wait_bounded(&s.empty[st], ((it / kStages) - 1) & 1u, kWaitLimitNs);
+            ok = ptx::mbar_wait_bounded(&s.empty[st], ((it / kStages) - 1) & 1u, wait_limit(L));
             if (!ok) fail(L, s);
         }
         if (ok) {
@@ -226,7 +249,8 @@ __device__ void produce(const Launch& L, const Smem& s) {
 // consumers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void red_shared(uint32_t addr, uint32_t v) {
-    // no memory clobber: the table is only read after a named barrier (which has one)
+    // no memory clobber: the table is only read after the consumer barrier (whose
+    // arrive and wait have one)
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 
@@ -383,6 +407,18 @@ __device__ void publish(const Job& J, int64_t n, int64_t k, int seg_rp, uint32_t
 
 __device__ __forceinline__ uint4 ldg128(const uint8_t* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
 
+// Barrier of the consumer threads, bounded: every consumer thread arrives
+// (release) and waits (acquire) for the phase.  A consumer that gave up earlier
+// has left the loop, so the others would wait for it forever on a named
+// barrier; here they give up too, after the launch's wait limit.
+__device__ __forceinline__ bool consumer_sync(const Launch& L, const Smem& s, uint32_t& phase) {
+    ptx::mbar_arrive(s.cbar);
+    const bool ok = ptx::mbar_wait_bounded(s.cbar, phase & 1u, wait_limit(L));
+    ++phase;
+    if (!ok) fail(L, s);
+    return ok;
+}
+
 
 __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
     const int ctid = warp * 32 + lane;
@@ -396,6 +432,7 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
     const uint32_t cG = static_cast<uint32_t>(kCG) + rowbase + (static_cast<uint32_t>(kBaseG) << 16);
     const uint32_t cB = static_cast<uint32_t>(kCB) + rowbase + (static_cast<uint32_t>(kBaseB) << 16);
     uint32_t it = 0;
+    uint32_t cphase = 0;  // completed phases of the consumer barrier
     int rot = 0;
     // geometry of the current job, kept in registers: reloaded only when a chunk
     // belongs to another job (global loads at every chunk start stall all warps)
@@ -407,7 +444,7 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
         // Every consumer reaches the same chunk before any of them gives up, so
         // they leave the loop together (no named barrier is left half-full).
         if (aborted(s)) break;
-        if (!ptx::mbar_wait_bounded(&s.full[st], (it / kStages) & 1u, kWaitLimitNs)) {
+        if (!ptx::mbar_wait_bounded(&s.full[st], (it / kStages) & 1u, wait_limit(L))) {
             fail(L, s);
             break;
         }
@@ -466,9 +503,9 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&s.empty[st]);
         if (m.seg_end) {
-            ptx::named_bar_sync(1, kNT);  // every consumer has counted the item
+            if (!consumer_sync(L, s, cphase)) break;  // every consumer has counted the item
             flush_table(s.tab, s.acc, ctid);
-            ptx::named_bar_sync(1, kNT);  // table zeroed, acc complete
+            if (!consumer_sync(L, s, cphase)) break;  // table zeroed, acc complete
             if (warp == 0) publish(J, L.d_count ? n_dev : J.n, m.k, m.seg_rp, s.acc, lane);
         }
     }
@@ -486,6 +523,7 @@ __global__ void __launch_bounds__(kHistThreads, 1) hist_kernel(const __grid_cons
             ptx::mbar_init(&s.full[i], 1);
             ptx::mbar_init(&s.empty[i], kConsumerWarps);
         }
+        ptx::mbar_init(s.cbar, kNT);
         *s.abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -520,7 +558,7 @@ __global__ void scores_kernel(const uint32_t* hist, int64_t n, int64_t pixel_cou
     }
 }
 
-int g_attr_device = -1;
+std::atomic<uint64_t> g_attr_done{0};  // kernel attribute set, one bit per device
 
 }  // namespace
 
@@ -561,13 +599,10 @@ void choose_items(Job& j, int64_t item_px, int grid) {
 }
 
 scn_status prepare_hist() {
-    int dev = 0;
-    SCN_CUDA_TRY(cudaGetDevice(&dev));
-    if (g_attr_device != dev) {
+    return once_per_device(g_attr_done, [] {
         SCN_CUDA_TRY(cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-        g_attr_device = dev;
-    }
-    return SCN_OK;
+        return SCN_OK;
+    });
 }
 
 scn_status launch_hist(const Launch& L, cudaStream_t st) {
@@ -650,6 +685,8 @@ static scn_status run_hist(scn_seq* s, uint32_t* d_hist, uint32_t* d_score, uint
     L.job0.pair = s->d_pair;
     L.queue = s->d_queue;
     L.status = s->d_status;
+    L.wait_limit_ns = s->test_wait_ns;
+    L.withhold_after = s->test_withhold;
     return launch_hist(L, static_cast<cudaStream_t>(stream));
 }
 

@@ -136,6 +136,14 @@ bool gen_params_ok(const scn_gen_params* p) {
 
 using namespace scn;
 
+namespace scn {
+cudaError_t reset_seq_scratch(scn_seq* s, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(static_cast<char*>(s->d_block) + s->scratch_off, 0, s->scratch_bytes, st);
+    if (e == cudaSuccess) e = reset_gate_workspace(s, st);
+    return e;
+}
+}  // namespace scn
+
 extern "C" {
 
 const char* scn_status_str(scn_status s) {
@@ -368,6 +376,8 @@ scn_status scn_sample(const scn_table* t, const scn_sample_spec* spec, scn_seq**
     s->d_partial = reinterpret_cast<uint32_t*>(p + b_slot + b_done + b_pair);
     s->d_status = reinterpret_cast<int*>(p + b_slot + b_done + b_pair + b_part);
     s->d_queue = reinterpret_cast<uint32_t*>(p + b_slot + b_done + b_pair + b_part + 64);
+    s->scratch_off = b_slot;
+    s->scratch_bytes = total - b_slot;
     e = obj_zero(s->d_block, total);
     if (e == cudaSuccess && s->n > 0) e = obj_upload(s->d_slot, slot.data(), slot.size() * 4);
     if (e == cudaSuccess) e = obj_finish();  // the slot list is read from host memory: done before return
@@ -403,10 +413,20 @@ scn_status scn_seq_sync_status(scn_seq* s, void* stream) {
     SCN_CUDA_TRY(cudaMemcpyAsync(&h, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     SCN_CUDA_TRY(cudaStreamSynchronize(st));
     if (h != 0) {
-        SCN_CUDA_TRY(cudaMemsetAsync(s->d_status, 0, sizeof(int), st));
+        // a launch that gave up may have left its self-clearing scratch part-way
+        // (partial histograms, counters, the queue): zero it with the status word
+        SCN_CUDA_TRY(reset_seq_scratch(s, st));
         SCN_CUDA_TRY(cudaStreamSynchronize(st));
         return SCN_ETIMEOUT;
     }
+    return SCN_OK;
+}
+
+scn_status scn_seq_set_wait_test(scn_seq* s, uint64_t wait_limit_ns, int32_t withhold_after) {
+    if (!s) return SCN_EINVAL;
+    if (wait_limit_ns != 0 && (wait_limit_ns < 100000ull || wait_limit_ns > 10000000000ull)) return SCN_EINVAL;
+    s->test_wait_ns = wait_limit_ns;
+    s->test_withhold = withhold_after < 0 ? -1 : withhold_after;
     return SCN_OK;
 }
 

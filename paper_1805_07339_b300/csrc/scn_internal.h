@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/scn.h"
@@ -23,6 +24,22 @@ void set_cuda_error(cudaError_t e);
     } while (0)
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Runs set() once per device for the current device: `done` holds one bit per
+// device (at most 64).  Safe from several host threads on different devices;
+// two threads on one device may both run set(), which only repeats an
+// idempotent attribute call.  Later calls cost one atomic load.
+template <class F>
+inline scn_status once_per_device(std::atomic<uint64_t>& done, F&& set) {
+    int dev = 0;
+    SCN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SCN_EUNSUPPORTED;
+    const uint64_t bit = uint64_t(1) << dev;
+    if (done.load(std::memory_order_acquire) & bit) return SCN_OK;
+    const scn_status s = set();
+    if (s == SCN_OK) done.fetch_or(bit, std::memory_order_acq_rel);
+    return s;
+}
 
 // Device memory of library objects (videos, sequences, plans), in scn_mem.cu:
 // from a per-device pool grown ahead in large steps and filled on a library
@@ -48,6 +65,7 @@ constexpr int kGroupWarps = 4;                            // warps sharing one t
 constexpr int kRegions = kConsumerWarps / kGroupWarps;
 constexpr int kTabRowsPerRegion = 136;                    // 45 (R) + 39 (G) + 52 (B) extended bins
 constexpr int kTabBytes = kRegions * kTabRowsPerRegion * 256;
+constexpr int kReductionsPerPixel = 3;                    // one shared-memory count per channel
 constexpr int kSmemLimit = 232448;                        // 227 KB opt-in per CTA
 constexpr int kSmemMisc = 1024;                           // accumulators + barriers + flags
 static_assert(kTabBytes + kSmemMisc <= kSmemLimit, "tables fit in shared memory");
@@ -88,7 +106,11 @@ struct scn_seq {
     uint32_t* d_queue = nullptr;     // work-queue counters (2 words, left zero)
     void* gate_ws = nullptr;         // gated-path workspace, made on first use
     void* space_ws = nullptr;        // spacing workspace (sorted sampled frames), made on first use
+    size_t scratch_off = 0;          // byte offset of the kernel scratch (done .. queue) in d_block
+    size_t scratch_bytes = 0;        // its size
     scn_tune tune{0, 0, 0};          // 0 fields: chosen per call
+    uint64_t test_wait_ns = 0;       // scn_seq_set_wait_test: wait limit of this sequence's launches
+    int32_t test_withhold = -1;      // scn_seq_set_wait_test: chunks handed out before withholding
 };
 
 namespace scn {
@@ -135,6 +157,8 @@ struct Launch {
     // upper bound; the count is read by the kernel, so the host need not wait for it
     const int32_t* d_count = nullptr;
     int32_t count_mul = 0;
+    uint64_t wait_limit_ns = 0;   // bounded waits give up after this long (0: 2 s)
+    int32_t withhold_after = -1;  // test hook, >= 0: each producer stops after this many chunks
 };
 
 // Luma rows per work descriptor: the requested even count, or (0) the whole
@@ -173,5 +197,11 @@ scn_status cnn_forward_counted(scn_cnn* c, const uint8_t* d_thumbs, const int32_
                                const int32_t* d_out_index);
 // Release a sequence's gated-path workspace (scn_proposal.cu).
 void free_gate_workspace(scn_seq* s);
+// Zero the gated-path workspace's kernel scratch after a device timeout, on st.
+cudaError_t reset_gate_workspace(scn_seq* s, cudaStream_t st);
+// Zero a sequence's kernel scratch (cross-CTA accumulators, counters, queue,
+// status) and its gated-path workspace, on st: what a timed-out launch may have
+// left non-zero.
+cudaError_t reset_seq_scratch(scn_seq* s, cudaStream_t st);
 void free_space_workspace(scn_seq* s);
 }  // namespace scn

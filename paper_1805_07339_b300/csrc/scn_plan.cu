@@ -270,7 +270,10 @@ scn_status scn_plan_sync_status(scn_plan* p, void* stream) {
     SCN_CUDA_TRY(cudaMemcpyAsync(&h, p->d_block, sizeof(int), cudaMemcpyDeviceToHost, st));
     SCN_CUDA_TRY(cudaStreamSynchronize(st));
     if (h != 0) {
-        SCN_CUDA_TRY(cudaMemsetAsync(p->d_block, 0, sizeof(int), st));
+        // a launch that gave up may have left the queue and its sequences'
+        // self-clearing scratch part-way: zero them with the status word
+        SCN_CUDA_TRY(cudaMemsetAsync(p->d_block, 0, 256, st));
+        for (scn_seq* s : p->seqs) SCN_CUDA_TRY(reset_seq_scratch(s, st));
         SCN_CUDA_TRY(cudaStreamSynchronize(st));
         return SCN_ETIMEOUT;
     }

@@ -20,6 +20,7 @@ namespace {
 
 struct GateWs {
     void* block = nullptr;
+    size_t bytes = 0;
     int64_t cap = 0;          // elements of the sequence it was made for
     int32_t* list = nullptr;  // [cap] proposed elements
     int32_t* slots2 = nullptr;  // [2 cap]
@@ -168,11 +169,19 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
         p += parts[i];
     }
     ws->cap = c;
+    ws->bytes = total;
     s->gate_ws = ws;
     return SCN_OK;
 }
 
 }  // namespace
+
+cudaError_t reset_gate_workspace(scn_seq* s, cudaStream_t st) {
+    GateWs* ws = static_cast<GateWs*>(s->gate_ws);
+    if (!ws) return cudaSuccess;
+    // everything in the block is scratch of one call: zero all of it
+    return cudaMemsetAsync(ws->block, 0, ws->bytes, st);
+}
 
 void free_gate_workspace(scn_seq* s) {
     GateWs* ws = static_cast<GateWs*>(s->gate_ws);
