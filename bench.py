@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-state", action="store_true")
     # single-kernel runs for profiling (see run_case)
-    ap.add_argument("--case", choices=["hist", "resize", "thumbs", "proposal", "cascade"])
+    ap.add_argument("--case", choices=["hist", "resize", "thumbs", "proposal", "cascade", "train"])
     ap.add_argument("--frames", type=int, default=512)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--stride", type=int, default=1)
@@ -93,20 +93,58 @@ def probe_lib():
     if _PROBE:
         return _PROBE[0]
     lib = ctypes.CDLL(build.build_probe())
+    lib.scn_probe_geometry.restype = None
+    lib.scn_probe_geometry.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     _PROBE.append(lib)
     lib.scn_probe_shared_reductions.restype = ctypes.c_int32
     lib.scn_probe_shared_reductions.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
     return lib
 
 
+def probe_geometry() -> tuple[int, int]:
+    """(counting warps per CTA, shared-memory reductions per pixel) of the hist kernel."""
+    import ctypes
+    w, r = ctypes.c_int32(0), ctypes.c_int32(0)
+    probe_lib().scn_probe_geometry(ctypes.byref(w), ctypes.byref(r))
+    return w.value, r.value
+
+
 def probe_shared_reductions(iters: int, grid: int, cycles, stream=None) -> None:
     """cycles: CUDA int64 tensor of `grid` entries; entry b = CTA b's SM cycles for
-    20 warps x 8 x iters warp-wide shared-memory reductions."""
+    (counting warps) x 8 x iters warp-wide shared-memory reductions."""
     import torch
     st = (stream or torch.cuda.current_stream()).cuda_stream
     rc = probe_lib().scn_probe_shared_reductions(iters, grid, cycles.data_ptr(), st)
     if rc != 0:
         raise RuntimeError(f"scn_probe_shared_reductions: status {rc}")
+
+
+def run_train_case(torch, scn, steps: int, batch: int = 256, frames: int = 4096) -> None:
+    """Training steps (forward, backward, Adam) of the proposal network on batches of
+    random thumbnail pairs, timed with CUDA events after 10 warm-up steps."""
+    import numpy as np
+    from paper_1805_07339_b300.proposal import he_uniform
+    rng = np.random.default_rng(0)
+    th = torch.from_numpy(rng.integers(0, 256, (frames, 36, 64), dtype=np.uint8)).cuda()
+    net = scn.scn_cnn_create(batch)
+    scn.scn_cnn_set_params(net, he_uniform(0))
+    prev = torch.from_numpy(rng.integers(0, frames - 1, (steps + 10, batch)).astype(np.int32)).cuda()
+    cur = prev + 1
+    y = torch.from_numpy((rng.random((steps + 10, batch)) < 0.1).astype(np.float32)).cuda()
+    for i in range(10):
+        scn.scn_cnn_train_step(net, th, y[i], batch, 4.0, 1e-3, prev=prev[i], cur=cur[i])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(10, steps + 10):
+        scn.scn_cnn_train_step(net, th, y[i], batch, 4.0, 1e-3, prev=prev[i], cur=cur[i])
+    e1.record()
+    torch.cuda.synchronize()
+    assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
+    scn.scn_cnn_destroy(net)
+    ms = e0.elapsed_time(e1) / steps
+    print(json.dumps({"case": "train", "batch": batch, "steps": steps, "ms_per_step": ms,
+                      "pairs_per_s": batch / ms * 1000}), flush=True)
 
 
 def run_case(a) -> None:
@@ -118,6 +156,9 @@ def run_case(a) -> None:
     import torch
     from paper_1805_07339_b300 import scn
     from paper_1805_07339_b300.workloads import MASTER_SEED
+    if a.case == "train":
+        run_train_case(torch, scn, a.reps)
+        return
     W, H, T = a.width, a.height, a.frames
     fb = W * H * 3 // 2
     v = scn.scn_video_create(MASTER_SEED, 0, W, H, T, max(1, T // 120))
@@ -537,6 +578,7 @@ def main():
                 "proposed": C["proposed"], "exact_on_proposed": C["exact_on_proposed"],
                 "tau_diff": res["tau_pre"], "tau_network": res["tau_cascade"],
                 "train_seconds": res["train"]["seconds"], "train_steps": res["train"]["steps"],
+                "train_pairs_per_s": res["train"]["steps"] * res["train"]["batch"] / res["train"]["seconds"],
                 "network_alone": dict(res["learned"], tau=res["tau"]),
                 "thumbnail_difference_gate": res["diff"]}
 
@@ -573,24 +615,26 @@ def main():
 
 
 def binding_unit(scn, torch, np, dom: dict, px_per_frame: int, clk: dict, stream, iters: int = 4096, reps: int = 5):
-    """The fused hist kernel's rate of shared-memory reductions (three per pixel, one
-    warp-wide wavefront per 32 pixel-channels) per SM clock, against the ceiling the
-    probe measures for the same reductions in the same table layout."""
+    """The fused hist kernel's rate of shared-memory reductions (two per pixel, one
+    warp-wide wavefront per 32 counts) per SM clock, against the ceiling the probe
+    measures for the same reductions in the same table layout."""
     sms = scn.scn_device_sm_count()
+    warps, reds = probe_geometry()
     cyc = torch.zeros(sms, dtype=torch.int64, device="cuda")
     peak = 0.0
     for _ in range(reps):
         probe_shared_reductions(iters, sms, cyc, stream)
         torch.cuda.synchronize()
-        peak = max(peak, 20 * 8 * iters / float(np.median(cyc.cpu().numpy())))
+        peak = max(peak, warps * 8 * iters / float(np.median(cyc.cpu().numpy())))
     mhz, src = clk.get("sm_mhz"), "median SM clock sampled during the timed region"
     if not mhz:
         mhz, src = measured_peaks().get("sm_max_mhz") or 2032.0, "maximum SM clock (no samples)"
-    warp_reds = 3 * px_per_frame * dom["frames"] / 32
+    warp_reds = reds * px_per_frame * dom["frames"] / 32
     achieved = warp_reds / (sms * (dom["ms"] / 1000) * mhz * 1e6)
     return {"unit": "warp-wide shared-memory reductions per SM clock", "achieved": achieved, "peak": peak,
-            "frac": achieved / peak, "reductions_per_pixel": 3, "sm_mhz": mhz, "clock_source": src,
-            "probe": f"scn_probe_shared_reductions: {sms} CTAs x 20 warps x {8 * iters} reductions, best of {reps}"}
+            "frac": achieved / peak, "reductions_per_pixel": reds, "sm_mhz": mhz, "clock_source": src,
+            "probe": f"scn_probe_shared_reductions: {sms} CTAs x {warps} warps x {8 * iters} reductions, "
+                     f"best of {reps}"}
 
 
 def run_bounded_state(scn, torch, hist, px, stream, shift=3, warmup=24, reps=20):

@@ -4,8 +4,8 @@
 // each warp-wide reduction is one conflict-free shared-memory wavefront; its
 // throughput, not HBM, sets that kernel's pace.  This probe issues the same
 // reductions in the same table layout (lane column, two warps per 128-byte half
-// of a 256-byte row, two warps per 16-bit counter half, 136 rows per region of
-// four warps) from the same 20 counting warps of a 672-thread CTA, with
+// of a 256-byte row, two warps per 16-bit counter half, one region of rows per
+// four warps) from the same counting warps of a CTA of the same size, with
 // nothing else to do, and times them with the SM's own cycle counter, so the
 // rate it returns (warp reductions per SM clock) is the ceiling the fused
 // kernel's own rate is compared with.
@@ -16,14 +16,18 @@
 //
 //   int scn_probe_shared_reductions(int32_t iters, int32_t grid,
 //                                   unsigned long long* d_cycles, void* stream)
-// launches `grid` CTAs of the hist kernel's shape (672 threads, its 174,080-byte
-// table) in which each of the 20 counting warps issues 8 * iters
-// red.shared.add.u32 in the kernel's table layout and nothing else; d_cycles[b]
-// (device, 8-byte aligned, `grid` entries) receives CTA b's elapsed SM clock
-// cycles over that loop, so 160 * iters / d_cycles[b] is the warp reductions
-// per SM clock.  Returns 0 (launched, asynchronous on `stream`), 1 for iters
-// outside [1, 2^20], grid outside [1, 65535] or a null / misaligned d_cycles,
-// 4 for a CUDA error (the status numbering of scn.h).
+// launches `grid` CTAs of the hist kernel's shape (its threads and its counter
+// table) in which each counting warp issues 8 * iters red.shared.add.u32 in the
+// kernel's table layout and nothing else; d_cycles[b] (device, 8-byte aligned,
+// `grid` entries) receives CTA b's elapsed SM clock cycles over that loop, so
+// warps * 8 * iters / d_cycles[b] is the warp reductions per SM clock.
+// Returns 0 (launched, asynchronous on `stream`), 1 for iters outside
+// [1, 2^20], grid outside [1, 65535] or a null / misaligned d_cycles, 4 for a
+// CUDA error (the status numbering of scn.h).
+//
+//   void scn_probe_geometry(int32_t* warps, int32_t* reductions_per_pixel)
+// reports the counting warps per CTA and the kernel's shared-memory reductions
+// per pixel.
 #include <cuda_runtime.h>
 
 #include "../scn_internal.h"
@@ -62,6 +66,11 @@ __global__ void __launch_bounds__(kHistThreads, 1) red_probe_kernel(int32_t iter
 }  // namespace scn
 
 extern "C" {
+
+void scn_probe_geometry(int32_t* warps, int32_t* reductions_per_pixel) {
+    if (warps) *warps = scn::kConsumerWarps;
+    if (reductions_per_pixel) *reductions_per_pixel = scn::kReductionsPerPixel;
+}
 
 int scn_probe_shared_reductions(int32_t iters, int32_t grid, unsigned long long* d_cycles, void* stream) {
     if (iters < 1 || iters > (1 << 20) || grid < 1 || grid > 65535 || !d_cycles) return SCN_EINVAL;

@@ -17,7 +17,11 @@
 //  * conv backward-data (layers 2, 3): tcgen05 GEMM dXcol = dU * W (M = 128
 //    rows, N = K columns, contraction over COUT), then a gather col2im that
 //    applies the ReLU mask of the layer below.
-//  * conv backward-weights, head forward/backward, Adam: CUDA cores.
+//  * conv backward-weights: tcgen05 GEMM dW^T = Xcol^T dU with the contraction
+//    over all rows of the batch (pairs x output positions), operands staged
+//    MN-major from the forward's im2col chunks and the rows of dU, the bias
+//    gradient from a column of ones; accumulated in TMEM per CTA.
+//  * head forward/backward, Adam: CUDA cores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -315,14 +319,13 @@ __global__ void prep_weights(const float* m, __nv_bfloat16* w1b, __nv_bfloat16* 
 
 template <int L>
 scn_status launch_conv_fwd(const ConvFwdArgs& a, cudaStream_t st) {
-    static int attr_dev = -1;
-    int dev = 0;
-    SCN_CUDA_TRY(cudaGetDevice(&dev));
-    if (attr_dev != dev) {
+    static std::atomic<uint64_t> attr_done{0};
+    const scn_status sa = once_per_device(attr_done, [] {
         SCN_CUDA_TRY(cudaFuncSetAttribute(conv_fwd_tc<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           ConvSmem<L>::BYTES));
-        attr_dev = dev;
-    }
+        return SCN_OK;
+    });
+    if (sa != SCN_OK) return sa;
     const int64_t tiles = (a.pairs * Shape<L>::P + 127) / 128;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
@@ -859,15 +862,14 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
 scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* prev, const int32_t* cur, int64_t pairs,
                                 float* logits, cudaStream_t st, const int* d_pairs = nullptr,
                                 const int32_t* out_index = nullptr) {
-    static int attr_dev = -1;
-    int dev = 0;
-    SCN_CUDA_TRY(cudaGetDevice(&dev));
-    if (attr_dev != dev) {
+    static std::atomic<uint64_t> attr_done{0};
+    const scn_status sa = once_per_device(attr_done, [] {
         SCN_CUDA_TRY(cudaFuncSetAttribute(cnn_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFzSmem));
         SCN_CUDA_TRY(cudaFuncSetAttribute(cnn_forward_fused, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           cudaSharedmemCarveoutMaxShared));
-        attr_dev = dev;
-    }
+        return SCN_OK;
+    });
+    if (sa != SCN_OK) return sa;
     FusedArgs a{};
     a.thumbs = thumbs;
     a.prev = prev;
@@ -1100,8 +1102,7 @@ __global__ void col2im_mask(const float* __restrict__ dxcol, const __nv_bfloat16
     }
 }
 
-// conv backward-weights on CUDA cores: dW[co][k] += sum_r dU[r][co] Xcol[r][k],
-// db[co] += sum_r dU[r][co]; rows in chunks of 64 staged in shared memory.
+// Arguments of the backward-weights kernel.
 struct ConvWgtArgs {
     const uint8_t* thumbs;
     const int32_t* prev;
@@ -1111,75 +1112,155 @@ struct ConvWgtArgs {
     float* gw;                 // grad + kW
     float* gb;                 // grad + kB
     int64_t pairs;
+    int* status;               // tensor-core path: bounded-wait status word
 };
 
+// conv backward-weights on tcgen05: D[k][co] = sum_r Xcol[r][k] dU[r][co] over
+// the CTA's rows r (pairs x output positions), i.e. dW^T with the contraction
+// over rows; row K of Xcol is set to 1 so that D[K][co] = sum_r dU[r][co] is
+// the bias gradient.  M = k (tiles of 128, K + 1 rounded up), N = COUT, rows
+// in chunks of 128 (8 MMAs of 16 rows per M tile).  Both operands are staged
+// "MN-major" (no swizzle): a core matrix is 8 rows r x 8 consecutive k (or co)
+// values, i.e. 16 contiguous bytes of one im2col or dU row, so the staging is
+// the forward's im2col chunk writes and plain 16-byte copies of dU.  The
+// accumulator stays in TMEM across all chunks of the CTA; the epilogue adds it
+// to the fp32 gradient (oracle layout) with one atomic per element.
 template <int L>
-__global__ void __launch_bounds__(256) conv_bwd_weight(const __grid_constant__ ConvWgtArgs a) {
+struct WgtTc {
     using S = Shape<L>;
-    constexpr int R = 64, NOUT = S::COUT * S::K, PER = (NOUT + 255) / 256;
-    extern __shared__ __align__(16) float wsm[];
-    float* xs = wsm;                 // [R][K]
-    float* us = wsm + R * S::K;      // [R][COUT]
-    float acc[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) acc[i] = 0.f;
-    float bacc = 0.f;
-    const int tid = threadIdx.x;
+    static constexpr int MT = (S::K + 1 + 127) / 128;   // M tiles (k, plus the ones row)
+    static constexpr int MP = MT * 128;
+    static constexpr int KCH = S::K / 8 + 1;             // 8-wide k chunks written per row (ones included)
+    static constexpr int A_BYTES = MP * 128 * 2, B_BYTES = S::COUT * 128 * 2;
+    static constexpr int BYTES = A_BYTES + B_BYTES + 64;
+    static constexpr uint32_t TMEM_COLS = MT * S::COUT <= 32 ? 32 : (MT * S::COUT <= 64 ? 64 : 128);
+    static_assert(MT * S::COUT <= 128, "TMEM columns");
+    static_assert(S::K % 8 != 0 || S::K / 8 < MP / 8, "ones chunk inside the tile");
+};
+// element E of 8 packed BF16 values |= 1.0 (the element is zero before)
+template <int E>
+__device__ __forceinline__ void set_bf16_one(uint4& v) {
+    constexpr uint32_t bits = (E & 1) ? (0x3F80u << 16) : 0x3F80u;
+    if constexpr (E / 2 == 0) v.x |= bits;
+    else if constexpr (E / 2 == 1) v.y |= bits;
+    else if constexpr (E / 2 == 2) v.z |= bits;
+    else v.w |= bits;
+}
+
+// MN-major no-swizzle descriptors: the stride between core matrices along MN
+// goes in the stride-byte-offset field, the stride along K in the
+// leading-byte-offset field
+__device__ __forceinline__ uint64_t mn_desc(uint32_t saddr, uint32_t mn_stride, uint32_t k_stride) {
+    return tc::smem_desc(saddr, k_stride, mn_stride);
+}
+
+template <int L>
+__global__ void __launch_bounds__(128) conv_bwd_weight_tc(const __grid_constant__ ConvWgtArgs a) {
+    using S = Shape<L>;
+    using W = WgtTc<L>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* As = smem;                  // [r/8][MP/8] cores of 8 r x 8 k
+    uint8_t* Bs = smem + W::A_BYTES;     // [r/8][COUT/8] cores of 8 r x 8 co
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + W::A_BYTES + W::B_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // k columns beyond the written chunks stay zero for the whole launch
+    for (int i = tid; i < (W::A_BYTES + W::B_BYTES) / 16; i += 128) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        ptx::mbar_init(mbar, 1);
+        ptx::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, W::TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t a_addr = ptx::smem_u32(As), b_addr = ptx::smem_u32(Bs);
+    constexpr uint32_t kAK = (W::MP / 8) * 128, kBK = (S::COUT / 8) * 128;  // K-direction core strides
+    constexpr uint32_t idesc = tc::idesc_bf16(128, S::COUT) | (1u << 15) | (1u << 16);  // A, B MN-major
+    // im2col arguments of the forward's staging
+    ConvFwdArgs f{};
+    f.thumbs = a.thumbs;
+    f.prev = a.prev;
+    f.cur = a.cur;
+    f.x = a.x;
     const int64_t rows = a.pairs * S::P;
-    for (int64_t r0 = static_cast<int64_t>(blockIdx.x) * R; r0 < rows; r0 += static_cast<int64_t>(gridDim.x) * R) {
+    const int64_t chunks = (rows + 127) / 128;
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+        const int64_t r = c * 128 + tid;
+        const bool live = r < rows;
+        const int64_t b = live ? r / S::P : 0;
+        const int pos = live ? static_cast<int>(r - b * S::P) : 0;
+        uint8_t* arow = As + (tid >> 3) * (W::MP / 8) * 128 + (tid & 7) * 16;
+#pragma unroll 4
+        for (int j = 0; j < S::KP / 8; ++j) {
+            uint4 v = live ? im2col_chunk<L>(f, b, pos, j) : make_uint4(0, 0, 0, 0);
+            if (j == S::K / 8 && live) set_bf16_one<S::K % 8>(v);  // the ones column k = K shares this chunk
+            *reinterpret_cast<uint4*>(arow + j * 128) = v;
+        }
+        if constexpr (S::K % 8 == 0) {
+            // the ones column starts its own chunk
+            *reinterpret_cast<uint4*>(arow + (S::K / 8) * 128) = live ? make_uint4(0x3F80u, 0, 0, 0) : make_uint4(0, 0, 0, 0);
+        }
+        uint8_t* brow = Bs + (tid >> 3) * (S::COUT / 8) * 128 + (tid & 7) * 16;
+#pragma unroll
+        for (int g = 0; g < S::COUT / 8; ++g)
+            *reinterpret_cast<uint4*>(brow + g * 128) =
+                live ? __ldg(reinterpret_cast<const uint4*>(a.du + r * S::COUT + 8 * g)) : make_uint4(0, 0, 0, 0);
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
         __syncthreads();
-        for (int e = tid; e < R * S::K; e += 256) {
-            const int rr = e / S::K, k = e % S::K;
-            const int64_t r = r0 + rr;
-            float v = 0.f;
-            if (r < rows) {
-                const int64_t b = r / S::P;
-                const int pos = static_cast<int>(r - b * S::P);
-                const int oy = pos / S::WO, ox = pos % S::WO;
-                const int tap = k / S::CIN, c = k % S::CIN;
-                const int iy = 2 * oy - 1 + tap / 3, ix = 2 * ox - 1 + tap % 3;
-                if (iy >= 0 && iy < S::HIN && ix >= 0 && ix < S::WIN) {
-                    if constexpr (L == 1) {
-                        const int fi = c == 0 ? (a.prev ? a.prev[b] : static_cast<int>(b))
-                                              : (a.cur ? a.cur[b] : static_cast<int>(b + 1));
-                        v = (static_cast<float>(a.thumbs[static_cast<int64_t>(fi) * 2304 + iy * 64 + ix]) - 128.f) *
-                            (1.f / 64.f);
-                    } else {
-                        v = __bfloat162float(a.x[((b * S::HIN + iy) * S::WIN + ix) * S::CIN + c]);
-                    }
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int t = 0; t < W::MT; ++t) {
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    tc::mma(tmem + t * S::COUT, mn_desc(a_addr + t * 16 * 128 + kk * 2 * kAK, 128, kAK),
+                            mn_desc(b_addr + kk * 2 * kBK, 128, kBK), idesc, (first && kk == 0) ? 0u : 1u);
                 }
             }
-            xs[e] = v;
+            tc::commit(mbar);
         }
-        for (int e = tid; e < R * S::COUT; e += 256) {
-            const int64_t r = r0 + e / S::COUT;
-            us[e] = r < rows ? __bfloat162float(a.du[r * S::COUT + e % S::COUT]) : 0.f;
+        first = false;
+        // the next chunk overwrites the operands: wait for these MMAs
+        if (ok && !ptx::mbar_wait_bounded(mbar, phase, kWaitNs)) {
+            ok = false;
+            atomicOr(a.status, kStatusTimeout);
         }
-        __syncthreads();
+        phase ^= 1u;
+        tc::fence_after_sync();
+    }
+    // epilogue: TMEM lane = k within the tile, column = co (every CTA has at
+    // least one chunk; the loads are warp-wide, the adds only after a complete wait)
+    if (!first) {
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int o = tid + 256 * i;
-            if (o < NOUT) {
-                const int co = o / S::K, k = o % S::K;
-                float s = acc[i];
-                for (int rr = 0; rr < R; ++rr) s = fmaf(us[rr * S::COUT + co], xs[rr * S::K + k], s);
-                acc[i] = s;
+        for (int t = 0; t < W::MT; ++t) {
+            const int k = t * 128 + tid;
+#pragma unroll
+            for (int c0 = 0; c0 < S::COUT; c0 += 16) {
+                uint32_t q[16];
+                tc::ld16(tmem + ((32u * warp) << 16) + t * S::COUT + c0, q);
+                tc::wait_ld();
+                if (!ok) continue;
+                if (k < S::K) {
+                    const int tap = k / S::CIN, ci = k % S::CIN;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        atomicAdd(a.gw + ((c0 + i) * S::CIN + ci) * 9 + tap, __uint_as_float(q[i]));
+                } else if (k == S::K) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) atomicAdd(a.gb + c0 + i, __uint_as_float(q[i]));
+                }
             }
         }
-        if (tid < S::COUT) {
-            for (int rr = 0; rr < R; ++rr) bacc += us[rr * S::COUT + tid];
-        }
     }
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int o = tid + 256 * i;
-        if (o < NOUT) {
-            const int co = o / S::K, k = o % S::K;
-            const int tap = k / S::CIN, ci = k % S::CIN;
-            atomicAdd(a.gw + (co * S::CIN + ci) * 9 + tap, acc[i]);
-        }
-    }
-    if (tid < S::COUT) atomicAdd(a.gb + tid, bacc);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, W::TMEM_COLS);
 }
 
 // Adam (bias-corrected), fp32 master weights
@@ -1197,14 +1278,13 @@ __global__ void adam_update(float* p, float* m, float* v, const float* g, int n,
 
 template <int L>
 scn_status launch_bwd_data(const ConvBwdArgs& a, cudaStream_t st) {
-    static int attr_dev = -1;
-    int dev = 0;
-    SCN_CUDA_TRY(cudaGetDevice(&dev));
-    if (attr_dev != dev) {
+    static std::atomic<uint64_t> attr_done{0};
+    const scn_status sa = once_per_device(attr_done, [] {
         SCN_CUDA_TRY(cudaFuncSetAttribute(conv_bwd_data_tc<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           BwdSmem<L>::BYTES));
-        attr_dev = dev;
-    }
+        return SCN_OK;
+    });
+    if (sa != SCN_OK) return sa;
     const int64_t tiles = (a.pairs * Shape<L>::P + 127) / 128;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
@@ -1218,19 +1298,19 @@ scn_status launch_bwd_data(const ConvBwdArgs& a, cudaStream_t st) {
 template <int L>
 scn_status launch_bwd_weight(const ConvWgtArgs& a, cudaStream_t st) {
     using S = Shape<L>;
-    constexpr int smem = (64 * S::K + 64 * S::COUT) * 4;
-    static int attr_dev = -1;
-    int dev = 0;
-    SCN_CUDA_TRY(cudaGetDevice(&dev));
-    if (attr_dev != dev) {
-        SCN_CUDA_TRY(cudaFuncSetAttribute(conv_bwd_weight<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr_dev = dev;
-    }
-    const int64_t chunks = (a.pairs * S::P + 63) / 64;
+    if (a.pairs <= 0) return SCN_OK;
+    static std::atomic<uint64_t> attr_done{0};
+    const scn_status sa = once_per_device(attr_done, [] {
+        SCN_CUDA_TRY(cudaFuncSetAttribute(conv_bwd_weight_tc<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          WgtTc<L>::BYTES));
+        return SCN_OK;
+    });
+    if (sa != SCN_OK) return sa;
+    const int64_t chunks = (a.pairs * S::P + 127) / 128;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
-    const int grid = static_cast<int>(std::min<int64_t>(chunks, static_cast<int64_t>(sms) * 2));
-    conv_bwd_weight<L><<<grid, 256, smem, st>>>(a);
+    const int grid = static_cast<int>(std::min<int64_t>(chunks, static_cast<int64_t>(sms)));
+    conv_bwd_weight_tc<L><<<grid, 128, WgtTc<L>::BYTES, st>>>(a);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }
@@ -1263,6 +1343,7 @@ scn_status gradients(Net* n, const uint8_t* thumbs, const int32_t* prev, const i
     w.prev = prev;
     w.cur = cur;
     w.pairs = pairs;
+    w.status = n->status;
     w.x = n->a2;
     w.du = n->du3;
     w.gw = n->grad + kW3;

@@ -8,6 +8,11 @@
 // 16 bytes); core matrix (i, j) (rows 8i.., columns 8j..) sits at byte
 // (i * K/8 + j) * 128.  A descriptor then has leading-byte offset 128 (the next
 // core matrix along K) and stride-byte offset K/8 * 128 (the next 8-row group).
+// MN-major operands (instruction-descriptor bits 15 / 16) use core matrices of
+// 8 K-rows x 16 bytes of 8 consecutive M (or N) values; there the stride
+// between core matrices along M/N goes in the stride-byte-offset field and the
+// stride along K in the leading-byte-offset field (checked on the B300 with a
+// one-MMA probe against a CPU product, the other reading giving wrong sums).
 #pragma once
 
 #include <cuda_runtime.h>

@@ -32,7 +32,9 @@ def test_probe_rate_is_plausible(scn, bench):
     torch.cuda.synchronize()
     c = cyc.cpu().numpy()
     assert (c > 0).all()
-    rate = 20 * 8 * iters / np.median(c)
+    warps, reds = bench.probe_geometry()
+    assert warps >= 4 and reds in (2, 3)
+    rate = warps * 8 * iters / np.median(c)
     assert 0.5 <= rate <= 1.05, rate
 
 
