@@ -173,6 +173,7 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
         b.record()
         torch.cuda.synchronize()
         tot["t_plain"] += a.elapsed_time(b) / reps
+        _check_status(src.seq, net, "plain exact path")
         for gate in gates:
             a, b = ev()
             a.record()
@@ -189,6 +190,7 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
             b.record()
             torch.cuda.synchronize()
             tot["t_" + gate] += a.elapsed_time(b) / reps
+            _check_status(src.seq, net, gate)
             p = prop.cpu().numpy()[1:].astype(bool)
             r = tot[gate]
             r["tp"] += int((p & ex).sum())
@@ -203,6 +205,15 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
                      "proposed": r["proposed"], "t_ms": tot["t_" + gate],
                      "speedup": tot["t_plain"] / max(tot["t_" + gate], 1e-9), "exact_on_proposed": r["exact_equal"]}
     return out
+
+
+def _check_status(seq, net, where: str) -> None:
+    """A bounded device wait that ran out would otherwise show only as stale
+    scores: read both status words after every timed loop."""
+    if scn.scn_seq_sync_status(seq) != scn.SCN_OK:
+        raise RuntimeError(f"device timeout in the hist kernel ({where})")
+    if scn.scn_cnn_sync_status(net) != scn.SCN_OK:
+        raise RuntimeError(f"device timeout in the proposal network ({where})")
 
 
 def run(torch, steps: int = 6000, batch: int = 256, lr: float = 1e-3, seed: int = 0, train_ids=None, val_ids=None,

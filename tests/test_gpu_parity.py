@@ -246,19 +246,38 @@ def hd_video(scn):
     torch.cuda.empty_cache()
 
 
-def test_hd_full_size_sampled_parity(scn, orc, hd_video):
+def _oracle_hists(orc, ovid, frames, W, H, batch=48):
+    """Oracle histograms of the given frame numbers (frames generated and
+    histogrammed on the host in batches, so host memory stays small)."""
+    import os
+    nt = max(1, min(32, os.cpu_count() or 1))
+    frames = np.asarray(frames, dtype=np.int64)
+    out = np.empty((len(frames), 3, 16), dtype=np.uint32)
+    for i in range(0, len(frames), batch):
+        fr = ovid.frames(frames[i:i + batch], nthreads=nt)
+        out[i:i + batch] = orc.hist_batch(fr, W, H, nthreads=nt)
+    return out
+
+
+def test_hd_full_size_parity(scn, orc, hd_video):
     """Full-size 1080p, the three sampling modes, default (bench) launch shape.
-    Sampled elements are checked against the oracle one by one; every element is
-    checked for histogram mass and for score consistency with its histograms."""
+    Every element of the stride-24 (300) and gather (1000) sequences, and every
+    24th element of the stride-1 sequence (with its predecessor for the score), is
+    compared with the oracle; every element is also checked for histogram mass
+    and for score consistency with its histograms."""
     v, buf = hd_video
     W, H, T = HD["width"], HD["height"], HD["num_frames"]
     dev = Dev(scn, buf, W, H, T)
     ovid = orc.Video(MASTER_SEED, 0, W, H, T, HD["num_shots"])
     gather = hd_gather()
+    every24 = np.arange(24, T, 24)
+    need = np.unique(np.concatenate([np.arange(0, T, 24), every24 - 1, gather]))
+    rh_all = _oracle_hists(orc, ovid, need, W, H)
+    ref = {int(f): rh_all[i] for i, f in enumerate(need)}
     try:
-        for kind, kw in [(scn.SCN_STRIDE, dict(start=0, stop=T, step=1)),
-                         (scn.SCN_STRIDE, dict(start=0, stop=T, step=24)),
-                         (scn.SCN_GATHER, dict(indices=gather.tolist()))]:
+        for kind, kw, checked in [(scn.SCN_STRIDE, dict(start=0, stop=T, step=1), every24),
+                                  (scn.SCN_STRIDE, dict(start=0, stop=T, step=24), None),
+                                  (scn.SCN_GATHER, dict(indices=gather.tolist()), None)]:
             idx = np.array(scn.scn_sample_indices(dev.table, kind, **kw))
             seq = dev.seq(kind, **kw)
             h, s, f = dev.hist_scores(seq)
@@ -268,16 +287,70 @@ def test_hd_full_size_sampled_parity(scn, orc, hd_video):
             l1 = np.abs(np.diff(hs, axis=0)).sum(axis=1)
             assert np.array_equal(s[1:], l1) and s[0] == 0
             assert np.array_equal(f, (2 * s.astype(np.int64) > W * H).astype(np.uint8))
-            pick = sorted(set([1, n // 2, n - 1] + random_indices(kind + 7, n, 5).tolist()) - {0})
-            need = sorted(set(pick) | {p - 1 for p in pick})
-            ref_frames = ovid.frames(idx[need], nthreads=8)
-            rh = orc.hist_batch(ref_frames, W, H, nthreads=8)
-            pos = {k: i for i, k in enumerate(need)}
-            for k in pick:
-                assert np.array_equal(h[k], rh[pos[k]])
-                rs, rf = orc.scores(np.stack([rh[pos[k - 1]], rh[pos[k]]]), W * H)
-                assert s[k] == rs[1] and f[k] == rf[1]
+            ks = np.arange(n) if checked is None else checked
+            rh = np.stack([ref[int(idx[k])] for k in ks])
+            assert np.array_equal(h[ks], rh)
+            for k in ks[ks > 0]:
+                rs, rf = orc.scores(np.stack([ref[int(idx[k - 1])], ref[int(idx[k])]]), W * H)
+                assert s[k] == rs[1] and f[k] == rf[1], k
+            assert s[0] == 0 and f[0] == 0
             scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+
+
+# flat single-colour frames: every pixel of a channel lands in one counter, the
+# worst case for the kernel's 16-bit lane counters; the YUV triples reach every
+# extreme of the unclamped ("extended") bins: R 30 / -14, G 27 / -11, B 33 / -18
+FLAT_YUV = [(255, 255, 255), (0, 0, 0), (255, 0, 0), (0, 255, 255), (16, 240, 16), (235, 128, 128),
+            (16, 128, 128), (255, 255, 0)]
+
+
+def _flat_frames(W, H):
+    out = np.empty((len(FLAT_YUV), W * H * 3 // 2), dtype=np.uint8)
+    for i, (y, u, v) in enumerate(FLAT_YUV):
+        out[i, :W * H] = y
+        out[i, W * H::2] = u
+        out[i, W * H + 1::2] = v
+    return out
+
+
+@pytest.mark.parametrize("W,H", [(1920, 1080), (3840, 2160)])
+def test_flat_frames_all_work_assignments(scn, orc, W, H):
+    frames = _flat_frames(W, H)
+    n = len(frames)
+    order = list(range(n)) + [n - 1, 0]  # ends with a repeat and a jump back
+    rh = np.stack([orc.hist_frame(frames[i], W, H) for i in range(n)])
+    rs, rf = orc.scores(rh[order], W * H)
+    for c in range(3):  # one bin per channel, the whole frame in it
+        assert np.all(rh[:, c].max(axis=1) == W * H)
+    buf = torch.from_numpy(frames.reshape(-1)).cuda()
+    dev = Dev(scn, buf, W, H, n)
+    try:
+        # default: contiguous row-pair ranges per CTA; then the work queue with items
+        # of about a quarter frame and of whole frames, and a one-CTA launch
+        for tune in (None, dict(item_kpx=W * H // 4000), dict(item_kpx=W * H // 1000 + 1), dict(grid=1)):
+            seq = dev.seq(scn.SCN_GATHER, indices=order)
+            h, s, f = dev.hist_scores(seq, tune=tune)
+            assert np.array_equal(h, rh[order]), tune
+            assert np.array_equal(s, rs) and np.array_equal(f, rf), tune
+            scn.scn_seq_destroy(seq)
+        # a batched plan over two sequences of the flat frames
+        seqs = [dev.seq(scn.SCN_GATHER, indices=order), dev.seq(scn.SCN_RANGE, start=0, stop=n)]
+        outs = [(torch.full((len(q), 48), -1, dtype=torch.int32, device="cuda"),
+                 torch.full((len(q),), -1, dtype=torch.int32, device="cuda"),
+                 torch.full((len(q),), 9, dtype=torch.uint8, device="cuda")) for q in (order, range(n))]
+        p = scn.scn_plan_create(seqs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+        scn.scn_plan_run(p)
+        assert scn.scn_plan_sync_status(p) == scn.SCN_OK
+        h0 = outs[0][0].cpu().numpy().view(np.uint32).reshape(-1, 3, 16)
+        h1 = outs[1][0].cpu().numpy().view(np.uint32).reshape(-1, 3, 16)
+        assert np.array_equal(h0, rh[order]) and np.array_equal(h1, rh)
+        assert np.array_equal(outs[0][1].cpu().numpy().view(np.uint32), rs)
+        assert np.array_equal(outs[0][2].cpu().numpy(), rf)
+        scn.scn_plan_destroy(p)
+        for q in seqs:
+            scn.scn_seq_destroy(q)
     finally:
         dev.close()
 
