@@ -190,10 +190,11 @@ def run_case(a) -> None:
         net = scn.scn_cnn_create(8)
         scn.scn_cnn_set_params(net, he_uniform(0))
         th = torch.empty((n, 36, 64), dtype=torch.uint8, device="cuda")
+        uv = torch.empty((n, 2, 18, 32), dtype=torch.uint8, device="cuda")
         d = torch.empty(n, dtype=torch.float32, device="cuda")
         z = torch.empty(max(n - 1, 1), dtype=torch.float32, device="cuda")
-        scn.scn_thumbs(seq, th)
-        scn.scn_thumb_diff(th, n, d)
+        scn.scn_thumbs_yuv(seq, th, uv)
+        scn.scn_thumb_diff_yuv(th, uv, n, d)
         scn.scn_cnn_forward(net, th, n - 1, z)
         tau_d = float(torch.quantile(d[1:], 0.985).item())
         tau_n = float(torch.quantile(z[:n - 1], 0.5).item())
@@ -202,7 +203,7 @@ def run_case(a) -> None:
         sc = torch.empty(n, dtype=torch.int32, device="cuda")
         fl = torch.empty(n, dtype=torch.uint8, device="cuda")
         for _ in range(a.reps):
-            scn.scn_cascade_hist_scores(seq, net, tau_d, tau_n, th, d, g, pr, sc, fl)
+            scn.scn_cascade_hist_scores(seq, net, tau_d, tau_n, th, d, g, pr, sc, fl, uv=uv)
         assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
         scn.scn_cnn_destroy(net)
     else:
@@ -567,20 +568,24 @@ def main():
     if not args.no_proposal:
         from paper_1805_07339_b300 import proposal
         torch.cuda.empty_cache()
-        res = proposal.run(torch)
+        res = proposal.run(torch, eval_sets=proposal.EVAL_SETS[1:])
         res.pop("params", None)
         C = res["cascade"]
         prop = {"workload": "train 201,572 consecutive 1080p pairs (28 videos), thresholds on 8 held-out videos, "
-                            "evaluate 100,800 fresh frames (14 videos)",
-                "path": "cascade: the thumbnail-difference gate as prefilter, the network on the pairs it passes",
+                            "evaluate 100,800 fresh frames (14 videos); recall also on two more sets of 14 fresh videos",
+                "path": "cascade: the luma + chroma thumbnail-difference gate as prefilter, the network (luma "
+                        "thumbnails) on the pairs it passes",
                 "recall": C["recall"], "precision": C["precision"], "speedup": C["speedup"],
                 "t_plain_ms": res["t_plain_ms"], "t_proposal_ms": C["t_ms"], "boundaries": res["boundaries"],
                 "proposed": C["proposed"], "exact_on_proposed": C["exact_on_proposed"],
-                "tau_diff": res["tau_pre"], "tau_network": res["tau_cascade"],
+                "tau_prefilter": res["tau_pre"], "tau_network": res["tau_cascade"],
+                "held_out": res["val_cascade"], "eval_sets": res["eval_sets"],
+                "recall_min_over_sets": min([C["recall"]] + [e["cascade"]["recall"] for e in res["eval_sets"]]),
                 "train_seconds": res["train"]["seconds"], "train_steps": res["train"]["steps"],
                 "train_pairs_per_s": res["train"]["steps"] * res["train"]["batch"] / res["train"]["seconds"],
                 "network_alone": dict(res["learned"], tau=res["tau"]),
-                "thumbnail_difference_gate": res["diff"]}
+                "thumbnail_difference_gate": dict(res["diff"], tau=res["tau_diff"]),
+                "luma_chroma_difference_gate": dict(res["diff_yuv"], tau=res["tau_yuv"])}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -444,9 +444,16 @@ scn_status scn_proposal_hist_scores(scn_seq* s, scn_cnn* net, float tau, uint8_t
 /* The non-learned gate: d_diff[k] = mean |thumb[k] - thumb[k-1]| over the
  * 2304 samples (d_diff[0] = 0); d_thumbs 4-byte aligned. */
 scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, void* stream);
+/* The same gate over luma and chroma thumbnails: d_diff[k] = mean |dY| over the
+ * 2304 luma samples + mean |dU| + mean |dV| over the 576 samples each of
+ * d_uv ([n][2][18][32], 16-byte aligned, or NULL for luma only; SCN_EINVAL when
+ * misaligned).  A boundary that changes chroma but little luma still moves it. */
+scn_status scn_thumb_diff_yuv(const uint8_t* d_thumbs, const uint8_t* d_uv, int64_t n, float* d_diff,
+                              void* stream);
 /* The cascade: the non-learned gate as a cheap prefilter, the network on what
- * it passes.  Thumbnails into d_thumbs ([n][36][64], 16-byte aligned) and
- * their differences into d_diff ([n]); every pair with d_diff[k] > tau_diff
+ * it passes.  Thumbnails into d_thumbs ([n][36][64], 16-byte aligned), chroma
+ * thumbnails into d_uv ([n][2][18][32], 16-byte aligned; NULL: a luma-only
+ * gate) and the gate (scn_thumb_diff_yuv) into d_diff ([n]); every pair with d_diff[k] > tau_diff
  * gets the network's logit in d_gate[k], every other pair -infinity; then
  * scn_gated_hist_scores with tau_net, so a pair is proposed only when both
  * thresholds pass and the exact kernel keeps the final say.  The network runs
@@ -454,8 +461,8 @@ scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, voi
  * trip).  Workspace as scn_gated_hist_scores.  d_diff, d_gate 4-byte aligned
  * (SCN_EINVAL); more than 2^31 - 1 elements: SCN_ERANGE. */
 scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, float tau_net, uint8_t* d_thumbs,
-                                   float* d_diff, float* d_gate, uint8_t* d_proposed, uint32_t* d_score,
-                                   uint8_t* d_flag, int64_t* h_nproposed, void* stream);
+                                   uint8_t* d_uv, float* d_diff, float* d_gate, uint8_t* d_proposed,
+                                   uint32_t* d_score, uint8_t* d_flag, int64_t* h_nproposed, void* stream);
 
 typedef enum { SCN_F32 = 0, SCN_BF16 = 1 } scn_dtype;
 /* Bilinear resize (half-pixel centres, no antialias, stretch) of the RGB
@@ -472,6 +479,11 @@ scn_status scn_resize_norm_both(scn_seq* s, int32_t out_h, int32_t out_w, const 
 /* Luma thumbnails: d_thumb[k][r][c] = Y[s*r][s*c], s = W/64 = H/36
  * (requires W == 64*s and H == 36*s); output uint8 [n][36][64]. */
 scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream);
+/* Luma thumbnails as scn_thumbs and, in the same launch, chroma thumbnails:
+ * d_uv[k][0][r][c] = U and d_uv[k][1][r][c] = V of chroma sample (s*c, s*r),
+ * the one under luma pixel (2*s*c, 2*s*r), r < 18, c < 32; output uint8
+ * [n][2][18][32] (NULL: luma only). */
+scn_status scn_thumbs_yuv(scn_seq* s, uint8_t* d_thumb, uint8_t* d_uv, void* stream);
 
 #ifdef __cplusplus
 }

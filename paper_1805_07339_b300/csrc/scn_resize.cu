@@ -111,13 +111,25 @@ __global__ void __launch_bounds__(256) resize_kernel(ResizeArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) thumbs_kernel(const uint8_t* nv12, int64_t stride, int W, int s,
-                                                    const int32_t* slot, uint8_t* out) {
+// One block per frame: luma thumbnail out[k][r][c] = Y[s r][s c] and, when uv is
+// given, the chroma thumbnail uv[k][p][r][c] (p = U, V) of the chroma sample
+// (s c, s r), the one under luma pixel (2 s c, 2 s r).
+__global__ void __launch_bounds__(256) thumbs_kernel(const uint8_t* nv12, int64_t stride, int W, int H, int s,
+                                                    const int32_t* slot, uint8_t* out, uint8_t* uv) {
     const int k = blockIdx.x;
     const uint8_t* f = nv12 + static_cast<int64_t>(slot[k]) * stride;
     for (int i = threadIdx.x; i < 36 * 64; i += blockDim.x) {
         const int r = i >> 6, c = i & 63;
         out[static_cast<int64_t>(k) * 2304 + i] = __ldg(f + static_cast<int64_t>(s * r) * W + s * c);
+    }
+    if (uv) {
+        const uint8_t* plane = f + static_cast<int64_t>(W) * H;
+        for (int i = threadIdx.x; i < 18 * 32; i += blockDim.x) {
+            const int r = i >> 5, c = i & 31;
+            const uint16_t w = __ldg(reinterpret_cast<const uint16_t*>(plane + static_cast<int64_t>(s * r) * W + 2 * s * c));
+            uv[static_cast<int64_t>(k) * 1152 + i] = static_cast<uint8_t>(w & 0xFF);
+            uv[static_cast<int64_t>(k) * 1152 + 576 + i] = static_cast<uint8_t>(w >> 8);
+        }
     }
 }
 
@@ -178,16 +190,18 @@ scn_status scn_resize_norm_both(scn_seq* s, int32_t oh, int32_t ow, const float*
     return scn::launch_resize(s, oh, ow, h_mean, h_std, d_out_f32, static_cast<__nv_bfloat16*>(d_out_bf16), stream);
 }
 
-scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream) {
+scn_status scn_thumbs_yuv(scn_seq* s, uint8_t* d_thumb, uint8_t* d_uv, void* stream) {
     if (!s || !d_thumb) return SCN_EINVAL;
     const int W = s->table->W, H = s->table->H;
     if (W % 64 || H % 36 || W / 64 != H / 36) return SCN_EUNSUPPORTED;
     if (s->n == 0) return SCN_OK;
     if (s->n > 0x7fffffff) return SCN_ERANGE;
     scn::thumbs_kernel<<<static_cast<unsigned>(s->n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        s->table->d_nv12, s->table->frame_stride, W, W / 64, s->d_slot, d_thumb);
+        s->table->d_nv12, s->table->frame_stride, W, H, W / 64, s->d_slot, d_thumb, d_uv);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }
+
+scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream) { return scn_thumbs_yuv(s, d_thumb, nullptr, stream); }
 
 }  // extern "C"

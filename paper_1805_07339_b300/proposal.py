@@ -22,6 +22,8 @@ HD = (1920, 1080, 7200, 60)
 TRAIN_IDS = list(range(2000, 2028))     # 28 videos: 201,572 consecutive pairs
 VAL_IDS = list(range(3000, 3008))       # threshold choice (~470 boundaries)
 EVAL_IDS = list(range(4000, 4014))      # 14 x 7200 = 100,800 fresh frames
+# two more disjoint evaluation sets of the same size: recall reported per set
+EVAL_SETS = [EVAL_IDS, list(range(5000, 5014)), list(range(6000, 6014))]
 
 
 def he_uniform(seed: int) -> np.ndarray:
@@ -63,27 +65,31 @@ class VideoSource:
         scn.scn_hist_scores(self.seq, self.hist, self.score, self.flag)
         return self.flag
 
-    def thumbs(self, out) -> None:
-        scn.scn_thumbs(self.seq, out)
+    def thumbs(self, out, uv=None) -> None:
+        scn.scn_thumbs_yuv(self.seq, out, uv)
 
     def close(self) -> None:
         scn.scn_seq_destroy(self.seq)
         scn.scn_table_destroy(self.table)
 
 
-def build_pairs(torch, src: VideoSource, ids: list[int]):
-    """Thumbnails of every frame, and (prev, cur, label) of every consecutive pair."""
+def build_pairs(torch, src: VideoSource, ids: list[int], chroma: bool = False):
+    """Thumbnails of every frame (and, with `chroma`, chroma thumbnails), and
+    (prev, cur, label) of every consecutive pair."""
     T = src.T
     thumbs = torch.empty((len(ids) * T, 36, 64), dtype=torch.uint8, device="cuda")
+    uv = torch.empty((len(ids) * T, 2, 18, 32), dtype=torch.uint8, device="cuda") if chroma else None
     labels = []
     for i, vid in enumerate(ids):
         src.load(vid)
-        src.thumbs(thumbs[i * T:(i + 1) * T])
+        src.thumbs(thumbs[i * T:(i + 1) * T], None if uv is None else uv[i * T:(i + 1) * T])
         labels.append(src.exact()[1:].float().clone())
     base = (torch.arange(len(ids), device="cuda") * T).repeat_interleave(T - 1)
     within = torch.arange(1, T, device="cuda").repeat(len(ids))
     cur = (base + within).int()
     prev = cur - 1
+    if chroma:
+        return thumbs, prev.contiguous(), cur.contiguous(), torch.cat(labels), uv
     return thumbs, prev.contiguous(), cur.contiguous(), torch.cat(labels)
 
 
@@ -142,22 +148,28 @@ def choose_tau(score: np.ndarray, labels: np.ndarray, recall: float = 0.995, fp_
 
 
 def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids: list[int], reps: int = 3,
-             tau_pre: float | None = None, tau_cascade: float | None = None):
+             tau_pre: float | None = None, tau_cascade: float | None = None, tau_yuv: float | None = None):
     """Per video: the plain exact path over all frames vs the learned gate, the
-    thumbnail-difference gate and (when tau_pre is given) the cascade, each as
-    thumbnails + gate + exact path on proposed pairs."""
+    luma thumbnail-difference gate, (when tau_yuv is given) the luma + chroma
+    thumbnail-difference gate, and (when tau_pre is given) the cascade - the
+    luma + chroma difference gate at tau_pre as prefilter, the network at
+    tau_cascade on what passes - each as thumbnails + gate + exact path on
+    proposed pairs."""
     T = src.T
     thumbs = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
+    uv = torch.empty((T, 2, 18, 32), dtype=torch.uint8, device="cuda")
     zl = torch.full((T,), -1e30, dtype=torch.float32, device="cuda")
     diff = torch.empty(T, dtype=torch.float32, device="cuda")
     prop = torch.empty(T, dtype=torch.uint8, device="cuda")
     sc = torch.empty(T, dtype=torch.int32, device="cuda")
     fl = torch.empty(T, dtype=torch.uint8, device="cuda")
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))  # noqa: E731
-    tot = dict(frames=0, boundaries=0, t_plain=0.0, t_learned=0.0, t_diff=0.0, t_cascade=0.0)
-    gates = ("learned", "diff") + (("cascade",) if tau_pre is not None else ())
+    tot = dict(frames=0, boundaries=0, t_plain=0.0)
+    gates = ("learned", "diff") + (("diff_yuv",) if tau_yuv is not None else ()) + \
+        (("cascade",) if tau_pre is not None else ())
     for gate in gates:
         tot[gate] = dict(tp=0, proposed=0, exact_equal=True)
+        tot["t_" + gate] = 0.0
     for vid in ids:
         src.load(vid)
         torch.cuda.synchronize()
@@ -182,7 +194,11 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
                     scn.scn_proposal_hist_scores(src.seq, net, tau, thumbs, zl, prop, sc, fl, count=False)
                 elif gate == "cascade":
                     scn.scn_cascade_hist_scores(src.seq, net, tau_pre, tau if tau_cascade is None else tau_cascade,
-                                                thumbs, diff, zl, prop, sc, fl, count=False)
+                                                thumbs, diff, zl, prop, sc, fl, count=False, uv=uv)
+                elif gate == "diff_yuv":
+                    src.thumbs(thumbs, uv)
+                    scn.scn_thumb_diff_yuv(thumbs, uv, T, diff)
+                    scn.scn_gated_hist_scores(src.seq, diff, tau_yuv, prop, sc, fl, count=False)
                 else:
                     src.thumbs(thumbs)
                     scn.scn_thumb_diff(thumbs, T, diff)
@@ -217,8 +233,10 @@ def _check_status(seq, net, where: str) -> None:
 
 
 def run(torch, steps: int = 6000, batch: int = 256, lr: float = 1e-3, seed: int = 0, train_ids=None, val_ids=None,
-        eval_ids=None) -> dict:
-    """Build data, train on the GPU, pick thresholds on held-out videos (choose_tau), evaluate."""
+        eval_ids=None, eval_sets=None) -> dict:
+    """Build data, train on the GPU, pick thresholds on held-out videos (choose_tau),
+    evaluate on eval_ids (the headline figures), and the cascade's recall and
+    precision on each further set of eval_sets."""
     src = VideoSource(torch)
     try:
         th, pv, cu, lab = build_pairs(torch, src, train_ids or TRAIN_IDS)
@@ -229,29 +247,45 @@ def run(torch, steps: int = 6000, batch: int = 256, lr: float = 1e-3, seed: int 
             tr = train(torch, net, th, pv, cu, lab, steps=steps, batch=batch, lr=lr, seed=seed)
             scn.scn_cnn_set_params(fwd, scn.scn_cnn_get_params(net))
             del th, pv, cu
-            vth, vp, vc, vl = build_pairs(torch, src, val_ids or VAL_IDS)
+            vth, vp, vc, vl, vuv = build_pairs(torch, src, val_ids or VAL_IDS, chroma=True)
             z = logits(torch, fwd, vth, vp, vc).cpu().numpy()
             vlab = vl.cpu().numpy()
             tau = choose_tau(z, vlab)
             d = torch.empty(vth.shape[0], dtype=torch.float32, device="cuda")
+            # gate of pair (k-1, k) sits at thumbnail k; pairs never span two videos
             scn.scn_thumb_diff(vth, vth.shape[0], d)
-            dd = d.cpu().numpy()
-            # diff of pair (k-1, k) sits at thumbnail k; pairs never span two videos
-            dv = dd[vc.cpu().numpy()]
+            dv = d.cpu().numpy()[vc.cpu().numpy()]
             tau_d = choose_tau(dv, vlab)
-            # cascade: the difference gate's own threshold as the prefilter (non-boundary pairs
-            # crowd just below it, so a looser one would pass most pairs), then the network as a
-            # precision filter on what passes, with a threshold 2 logits below the lowest held-out
-            # boundary there (and never stricter than the network's own): recall is the prefilter's
-            tau_pre = tau_d
-            pas = dv > tau_pre
+            scn.scn_thumb_diff_yuv(vth, vuv, vth.shape[0], d)
+            dyv = d.cpu().numpy()[vc.cpu().numpy()]
+            tau_yuv = choose_tau(dyv, vlab)
+            # cascade: the luma + chroma difference gate as the prefilter (a boundary moves luma or
+            # chroma, so boundaries and non-boundaries separate there, where the luma gate's
+            # non-boundaries crowd just below the boundaries of chroma-dominant cuts), then the
+            # network as a precision filter on what passes, with a threshold 2 logits below the
+            # lowest held-out boundary there (and never stricter than the network's own)
+            tau_pre = tau_yuv
+            pas = dyv > tau_pre
             tau_c = min(tau_for_recall(z[pas], vlab[pas], recall=1.0) - 2.0, tau) if pas.any() else tau
             pos = vlab > 0.5
+            neg = ~pos
             val_cascade = {"recall": float(np.mean(pas[pos] & (z[pos] > tau_c))), "prefilter_pass": float(np.mean(pas)),
-                           "proposed_fraction": float(np.mean(pas & (z > tau_c)))}
-            res = evaluate(torch, fwd, tau, tau_d, src, eval_ids or EVAL_IDS, tau_pre=tau_pre, tau_cascade=tau_c)
+                           "proposed_fraction": float(np.mean(pas & (z > tau_c))),
+                           "prefilter_recall": float(np.mean(pas[pos])),
+                           # the margin between the classes on the held-out gate values
+                           "gate_lowest_boundary": float(dyv[pos].min()) if pos.any() else None,
+                           "gate_highest_non_boundary": float(dyv[neg].max()) if neg.any() else None}
+            res = evaluate(torch, fwd, tau, tau_d, src, eval_ids or EVAL_IDS, tau_pre=tau_pre, tau_cascade=tau_c,
+                           tau_yuv=tau_yuv)
+            sets = []
+            for ids in (eval_sets or []):
+                r2 = evaluate(torch, fwd, tau, tau_d, src, ids, reps=1, tau_pre=tau_pre, tau_cascade=tau_c,
+                              tau_yuv=tau_yuv)
+                sets.append({"videos": [ids[0], ids[-1]], "boundaries": r2["boundaries"],
+                             **{g: {k: r2[g][k] for k in ("recall", "precision", "speedup")}
+                                for g in ("cascade", "learned", "diff", "diff_yuv")}})
             res.update({"train": tr, "tau": tau, "tau_diff": tau_d, "tau_pre": tau_pre, "tau_cascade": tau_c,
-                        "val_cascade": val_cascade,
+                        "tau_yuv": tau_yuv, "val_cascade": val_cascade, "eval_sets": sets,
                         "train_pairs": int(lab.numel()),
                         "train_positives": int(lab.sum().item()), "val_pairs": int(vl.numel()),
                         "params": scn.scn_cnn_get_params(fwd)})
