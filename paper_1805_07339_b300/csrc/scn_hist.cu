@@ -35,9 +35,10 @@
 //    region (two column halves x two 16-bit counter halves), so the reductions
 //    never conflict on a bank and 20 warps fit in shared memory.
 //  * After each item the table is flushed (lane columns and counter halves
-//    summed, extended bins folded) and published: directly to hist[k] when the
-//    item is the whole frame, else through an accumulator that the CTA
-//    completing the frame turns into hist[k].  The CTA completing the second
+//    summed, extended bins folded) into one of two accumulators and handed to a
+//    publisher warp, which publishes it while the consumers go on counting:
+//    directly to hist[k] when the item is the whole frame, else through a global
+//    accumulator that the CTA completing the frame turns into hist[k].  The CTA completing the second
 //    frame of a consecutive pair computes that pair's score.  Completion uses
 //    counters; no CTA waits for another.
 #include <cuda_runtime.h>
@@ -78,13 +79,22 @@ struct ChunkMeta {
     int32_t job, k, rows, seg_end, seg_rp, r0, pad[2];
 };
 
+// What the publisher warp needs to publish one flushed item: its job, element
+// and row pairs (job < 0: the consumers are done).
+struct PubMeta {
+    int32_t job, k, seg_rp, pad;
+};
+
 struct Smem {
     uint8_t* tab;
     ChunkMeta* meta;    // [kStages]
-    uint32_t* acc;      // [48]
+    uint32_t* acc;      // [2][64]: flushed counts of an item, double-buffered for the publisher
+    PubMeta* pmeta;     // [2]
     uint64_t* full;     // [kStages]
     uint64_t* empty;    // [kStages]
     uint64_t* cbar;     // consumers' CTA barrier (every consumer thread arrives)
+    uint64_t* accfull;  // [2] acc[b] holds an item's counts (the consumers' thread 0 arrives)
+    uint64_t* accfree;  // [2] the publisher has taken acc[b] (its 32 lanes arrive)
     int* abort_flag;
 };
 
@@ -93,13 +103,17 @@ __device__ __forceinline__ Smem carve(uint8_t* smem) {
     s.tab = smem;
     s.meta = reinterpret_cast<ChunkMeta*>(smem + kTabBytes);
     s.acc = reinterpret_cast<uint32_t*>(s.meta + kStages);
-    s.full = reinterpret_cast<uint64_t*>(s.acc + 64);
+    s.pmeta = reinterpret_cast<PubMeta*>(s.acc + 128);
+    s.full = reinterpret_cast<uint64_t*>(s.pmeta + 2);
     s.empty = s.full + kStages;
     s.cbar = s.empty + kStages;
-    s.abort_flag = reinterpret_cast<int*>(s.cbar + 1);
+    s.accfull = s.cbar + 1;
+    s.accfree = s.accfull + 2;
+    s.abort_flag = reinterpret_cast<int*>(s.accfree + 2);
     return s;
 }
-static_assert(kStages * sizeof(ChunkMeta) + 64 * 4 + (2 * kStages + 1) * 8 + 16 <= kSmemMisc, "misc smem");
+static_assert(kStages * sizeof(ChunkMeta) + 128 * 4 + 2 * sizeof(PubMeta) + (2 * kStages + 5) * 8 + 16 <= kSmemMisc,
+              "misc smem");
 
 __device__ __forceinline__ const Job& job_of(const Launch& L, int j) { return L.jobs ? L.jobs[j] : L.job0; }
 
@@ -347,13 +361,10 @@ __device__ __forceinline__ void write_score(const Job& J, int64_t k, uint32_t h0
     }
 }
 
-// One warp, after the flush: publish an item's counts of element k (seg_rp
-// row pairs), complete the frame and the scores it unblocks.
-__device__ void publish(const Job& J, int64_t n, int64_t k, int seg_rp, uint32_t* acc, int lane) {
-    uint32_t h0 = acc[lane];
-    uint32_t h1 = lane < 16 ? acc[32 + lane] : 0u;
-    acc[lane] = 0;
-    if (lane < 16) acc[32 + lane] = 0;
+// The publisher warp: publish an item's counts of element k (seg_rp row pairs;
+// lane holds bins lane and 32 + lane), complete the frame and the scores it
+// unblocks.
+__device__ void publish(const Job& J, int64_t n, int64_t k, int seg_rp, uint32_t h0, uint32_t h1, int lane) {
     const int hp = J.H / 2;
     if (seg_rp != hp) {
         // part of the frame: accumulate; the CTA completing the frame finishes it
@@ -422,7 +433,6 @@ __device__ __forceinline__ bool consumer_sync(const Launch& L, const Smem& s, ui
 
 __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
     const int ctid = warp * 32 + lane;
-    const int64_t n_dev = device_elems(L);
     const int region = warp / kGroupWarps;
     const uint32_t lanereg = static_cast<uint32_t>(lane * 4 + (warp & 1) * 128);
     const uint32_t inc = (warp & 2) ? 65536u : 1u;
@@ -433,6 +443,7 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
     const uint32_t cB = static_cast<uint32_t>(kCB) + rowbase + (static_cast<uint32_t>(kBaseB) << 16);
     uint32_t it = 0;
     uint32_t cphase = 0;  // completed phases of the consumer barrier
+    uint32_t seg = 0;     // items flushed so far (acc buffer seg & 1)
     int rot = 0;
     // geometry of the current job, kept in registers: reloaded only when a chunk
     // belongs to another job (global loads at every chunk start stall all warps)
@@ -503,11 +514,56 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&s.empty[st]);
         if (m.seg_end) {
+            const uint32_t b = seg & 1u;
             if (!consumer_sync(L, s, cphase)) break;  // every consumer has counted the item
-            flush_table(s.tab, s.acc, ctid);
-            if (!consumer_sync(L, s, cphase)) break;  // table zeroed, acc complete
-            if (warp == 0) publish(J, L.d_count ? n_dev : J.n, m.k, m.seg_rp, s.acc, lane);
+            // acc[b] was last filled two items ago: the publisher has taken it
+            if (seg >= 2 && !ptx::mbar_wait_bounded(&s.accfree[b], ((seg >> 1) - 1) & 1u, wait_limit(L))) {
+                fail(L, s);
+                break;
+            }
+            flush_table(s.tab, s.acc + 64 * b, ctid);
+            if (!consumer_sync(L, s, cphase)) break;  // table zeroed, acc[b] complete
+            if (ctid == 0) {
+                s.pmeta[b] = PubMeta{m.job, m.k, m.seg_rp, 0};
+                ptx::mbar_arrive(&s.accfull[b]);  // release: the counts and their item
+            }
+            ++seg;
         }
+    }
+    // tell the publisher that no item follows (not after a failure: it then gives up by itself)
+    if (!aborted(s) && ctid == 0) {
+        const uint32_t b = seg & 1u;
+        if (seg < 2 || ptx::mbar_wait_bounded(&s.accfree[b], ((seg >> 1) - 1) & 1u, wait_limit(L))) {
+            s.pmeta[b] = PubMeta{-1, 0, 0, 0};
+            ptx::mbar_arrive(&s.accfull[b]);
+        } else {
+            fail(L, s);
+        }
+    }
+}
+
+// The publisher warp: takes each flushed item's counts off acc[b] (freeing the
+// buffer for the consumers at once) and publishes them - global atomics, frame
+// completion, the score of each completed pair - so that the latency of those
+// global round trips is not on the consumers' path.
+__device__ void publisher(const Launch& L, const Smem& s, int lane) {
+    const int64_t n_dev = device_elems(L);
+    for (uint32_t pseg = 0;; ++pseg) {
+        const uint32_t b = pseg & 1u;
+        if (!ptx::mbar_wait_bounded(&s.accfull[b], (pseg >> 1) & 1u, wait_limit(L))) {
+            fail(L, s);
+            return;
+        }
+        const PubMeta pm = s.pmeta[b];
+        if (pm.job < 0) return;
+        uint32_t* acc = s.acc + 64 * b;
+        const uint32_t h0 = acc[lane];
+        const uint32_t h1 = lane < 16 ? acc[32 + lane] : 0u;
+        acc[lane] = 0;
+        if (lane < 16) acc[32 + lane] = 0;
+        ptx::mbar_arrive(&s.accfree[b]);  // release: acc[b] read and zeroed
+        const Job& J = job_of(L, pm.job);
+        publish(J, L.d_count ? n_dev : J.n, pm.k, pm.seg_rp, h0, h1, lane);
     }
 }
 
@@ -517,19 +573,27 @@ __global__ void __launch_bounds__(kHistThreads, 1) hist_kernel(const __grid_cons
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kTabBytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
-    if (tid < 64) s.acc[tid] = 0;
+    if (tid < 128) s.acc[tid] = 0;
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
             ptx::mbar_init(&s.full[i], 1);
             ptx::mbar_init(&s.empty[i], kConsumerWarps);
         }
         ptx::mbar_init(s.cbar, kNT);
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&s.accfull[i], 1);
+            ptx::mbar_init(&s.accfree[i], 32);
+        }
         *s.abort_flag = 0;
         ptx::fence_mbar_init();
     }
     __syncthreads();
     if (warp == kConsumerWarps) {
         if (lane == 0) produce(L, s);
+        return;
+    }
+    if (warp == kConsumerWarps + 1) {
+        publisher(L, s, lane);
         return;
     }
     consume(L, s, warp, lane);

@@ -59,7 +59,7 @@ constexpr int kStatusTimeout = 1;
 
 // Histogram kernel geometry (fixed at compile time).
 constexpr int kConsumerWarps = 20;                        // warps that load, convert + count
-constexpr int kHistThreads = (kConsumerWarps + 1) * 32;  // + one producer warp (work descriptors)
+constexpr int kHistThreads = (kConsumerWarps + 2) * 32;  // + a producer warp (work descriptors) + a publisher warp
 constexpr int kStages = 2;                                // chunk descriptors in flight
 constexpr int kGroupWarps = 4;                            // warps sharing one table region
 constexpr int kRegions = kConsumerWarps / kGroupWarps;
