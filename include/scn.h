@@ -444,16 +444,17 @@ scn_status scn_proposal_hist_scores(scn_seq* s, scn_cnn* net, float tau, uint8_t
 /* The non-learned gate: d_diff[k] = mean |thumb[k] - thumb[k-1]| over the
  * 2304 samples (d_diff[0] = 0); d_thumbs 4-byte aligned. */
 scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, void* stream);
-/* The same gate over luma and chroma thumbnails: d_diff[k] = mean |dY| over the
- * 2304 luma samples + mean |dU| + mean |dV| over the 576 samples each of
- * d_uv ([n][2][18][32], 16-byte aligned, or NULL for luma only; SCN_EINVAL when
- * misaligned).  A boundary that changes chroma but little luma still moves it. */
-scn_status scn_thumb_diff_yuv(const uint8_t* d_thumbs, const uint8_t* d_uv, int64_t n, float* d_diff,
-                              void* stream);
-/* The cascade: the non-learned gate as a cheap prefilter, the network on what
- * it passes.  Thumbnails into d_thumbs ([n][36][64], 16-byte aligned), chroma
- * thumbnails into d_uv ([n][2][18][32], 16-byte aligned; NULL: a luma-only
- * gate) and the gate (scn_thumb_diff_yuv) into d_diff ([n]); every pair with d_diff[k] > tau_diff
+/* The luma + chroma gate over coarse YUV thumbnails (scn_thumbs_yuv): d_diff[k]
+ * = mean |dY| + mean |dU| + mean |dV| between elements k-1 and k, 192 samples
+ * per plane (d_diff[0] = 0).  d_yuv [n][3][6][32], 16-byte aligned, else
+ * SCN_EINVAL.  A boundary that changes chroma but little luma still moves it. */
+scn_status scn_thumb_diff_yuv(const uint8_t* d_yuv, int64_t n, float* d_diff, void* stream);
+/* The cascade: the luma + chroma gate as a cheap prefilter, the network on what
+ * it passes.  Coarse YUV thumbnails of every element into d_yuv
+ * ([n][3][6][32], 16-byte aligned) and the gate (scn_thumb_diff_yuv) into
+ * d_diff ([n]); the network's luma thumbnails into d_thumbs ([n][36][64],
+ * 16-byte aligned) for the two elements of each pair whose gate passes
+ * tau_diff only (other entries are not written); every pair with d_diff[k] > tau_diff
  * gets the network's logit in d_gate[k], every other pair -infinity; then
  * scn_gated_hist_scores with tau_net, so a pair is proposed only when both
  * thresholds pass and the exact kernel keeps the final say.  The network runs
@@ -479,11 +480,12 @@ scn_status scn_resize_norm_both(scn_seq* s, int32_t out_h, int32_t out_w, const 
 /* Luma thumbnails: d_thumb[k][r][c] = Y[s*r][s*c], s = W/64 = H/36
  * (requires W == 64*s and H == 36*s); output uint8 [n][36][64]. */
 scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream);
-/* Luma thumbnails as scn_thumbs and, in the same launch, chroma thumbnails:
- * d_uv[k][0][r][c] = U and d_uv[k][1][r][c] = V of chroma sample (s*c, s*r),
- * the one under luma pixel (2*s*c, 2*s*r), r < 18, c < 32; output uint8
- * [n][2][18][32] (NULL: luma only). */
-scn_status scn_thumbs_yuv(scn_seq* s, uint8_t* d_thumb, uint8_t* d_uv, void* stream);
+/* Coarse YUV thumbnails and, in the same launch when d_thumb is not NULL, the
+ * luma thumbnails of scn_thumbs: d_yuv[k][0][r][c] = Y[6*s*r][2*s*c] and
+ * d_yuv[k][1][r][c], d_yuv[k][2][r][c] = U, V of chroma sample (s*c, 3*s*r),
+ * the one under that luma pixel, r < 6, c < 32; output uint8 [n][3][6][32]
+ * (NULL: luma thumbnails only; both NULL: SCN_EINVAL). */
+scn_status scn_thumbs_yuv(scn_seq* s, uint8_t* d_thumb, uint8_t* d_yuv, void* stream);
 
 #ifdef __cplusplus
 }

@@ -82,10 +82,12 @@ def lib():
         _lib.orc_resize_norm_frame.restype = None
         _lib.orc_thumb_frame.argtypes = [p, i32, i32, p]
         _lib.orc_thumb_frame.restype = None
-        _lib.orc_thumb_uv_frame.argtypes = [p, i32, i32, p]
-        _lib.orc_thumb_uv_frame.restype = None
-        _lib.orc_thumb_diff.argtypes = [p, p, p, p]
+        _lib.orc_thumb_yuv_frame.argtypes = [p, i32, i32, p]
+        _lib.orc_thumb_yuv_frame.restype = None
+        _lib.orc_thumb_diff.argtypes = [p, p]
         _lib.orc_thumb_diff.restype = ctypes.c_double
+        _lib.orc_thumb_diff_yuv.argtypes = [p, p]
+        _lib.orc_thumb_diff_yuv.restype = ctypes.c_double
         _lib.orc_hist_batch.argtypes = [p, i64, i32, i32, p, i64, i32, p]
         _lib.orc_hist_batch.restype = None
         _lib.orc_gen_batch.argtypes = [ctypes.POINTER(GenParams), ctypes.POINTER(Shot), i64, p, i64,
@@ -247,21 +249,23 @@ def thumb_frame(frame: np.ndarray, W: int, H: int) -> np.ndarray:
     return out
 
 
-def thumb_uv_frame(frame: np.ndarray, W: int, H: int) -> np.ndarray:
-    """[2][18][32]: U and V of the chroma sample under luma pixel (2 s c, 2 s r)."""
+def thumb_yuv_frame(frame: np.ndarray, W: int, H: int) -> np.ndarray:
+    """[3][6][32]: Y at luma pixel (2 s c, 6 s r), and U, V of the chroma sample it uses."""
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
-    out = np.empty((2, 18, 32), dtype=np.uint8)
-    lib().orc_thumb_uv_frame(_ptr(frame), W, H, _ptr(out))
+    out = np.empty((3, 6, 32), dtype=np.uint8)
+    lib().orc_thumb_yuv_frame(_ptr(frame), W, H, _ptr(out))
     return out
 
 
-def thumb_diff(ta: np.ndarray, tb: np.ndarray, uva=None, uvb=None) -> float:
-    """Mean |luma thumbnail difference|, plus the mean |U| and |V| differences of the
-    chroma thumbnails when given (the difference gate between two frames)."""
+def thumb_diff(ta: np.ndarray, tb: np.ndarray) -> float:
+    """Mean |luma thumbnail difference| (the luma gate between two frames)."""
     ta = np.ascontiguousarray(ta, dtype=np.uint8)
     tb = np.ascontiguousarray(tb, dtype=np.uint8)
-    if uva is None:
-        return float(lib().orc_thumb_diff(_ptr(ta), _ptr(tb), None, None))
-    uva = np.ascontiguousarray(uva, dtype=np.uint8)
-    uvb = np.ascontiguousarray(uvb, dtype=np.uint8)
-    return float(lib().orc_thumb_diff(_ptr(ta), _ptr(tb), _ptr(uva), _ptr(uvb)))
+    return float(lib().orc_thumb_diff(_ptr(ta), _ptr(tb)))
+
+
+def thumb_diff_yuv(ya: np.ndarray, yb: np.ndarray) -> float:
+    """Mean |dY| + mean |dU| + mean |dV| of two coarse YUV thumbnails (the luma + chroma gate)."""
+    ya = np.ascontiguousarray(ya, dtype=np.uint8)
+    yb = np.ascontiguousarray(yb, dtype=np.uint8)
+    return float(lib().orc_thumb_diff_yuv(_ptr(ya), _ptr(yb)))

@@ -332,32 +332,40 @@ void orc_thumb_frame(const uint8_t* f, int32_t W, int32_t H, uint8_t* thumb) {
             thumb[r * 64 + c] = f[(s * r) * W + s * c];
 }
 
-/* Chroma thumbnails: the chroma sample under every second luma thumbnail
- * position, i.e. under luma pixel (2 s c, 2 s r): uv[0][r][c] = U and
- * uv[1][r][c] = V of chroma sample (s c, s r), r < 18, c < 32.  In the NV12
- * chroma plane (H/2 rows of W bytes, U and V interleaved) that sample's U is
- * byte 2 s c of row s r and its V the next byte. */
-void orc_thumb_uv_frame(const uint8_t* f, int32_t W, int32_t H, uint8_t* uv) {
+/* Coarse YUV thumbnails: every sixth row and every second column of the luma
+ * thumbnail grid, and the chroma sample under each of those pixels.
+ * yuv[0][r][c] = Y at luma pixel (2 s c, 6 s r); yuv[1][r][c] and yuv[2][r][c]
+ * = U and V of chroma sample (s c, 3 s r), the one that pixel uses; r < 6,
+ * c < 32.  In the NV12 chroma plane (H/2 rows of W bytes, U and V interleaved)
+ * that sample's U is byte 2 s c of row 3 s r and its V the next byte. */
+void orc_thumb_yuv_frame(const uint8_t* f, int32_t W, int32_t H, uint8_t* yuv) {
     int64_t s = W / 64;
     const uint8_t* plane = f + (int64_t)W * H;
-    for (int64_t p = 0; p < 2; p++)
-        for (int64_t r = 0; r < 18; r++)
-            for (int64_t c = 0; c < 32; c++)
-                uv[(p * 18 + r) * 32 + c] = plane[(s * r) * W + 2 * (s * c) + p];
+    for (int64_t r = 0; r < 6; r++)
+        for (int64_t c = 0; c < 32; c++) {
+            yuv[(0 * 6 + r) * 32 + c] = f[(6 * s * r) * W + 2 * s * c];
+            yuv[(1 * 6 + r) * 32 + c] = plane[(3 * s * r) * W + 2 * (s * c)];
+            yuv[(2 * 6 + r) * 32 + c] = plane[(3 * s * r) * W + 2 * (s * c) + 1];
+        }
 }
 
-/* The thumbnail-difference gate between frames k-1 and k: the mean absolute
- * difference of their luma thumbnails (2304 samples), plus, when chroma
- * thumbnails are given, the mean absolute difference of their U samples and of
- * their V samples (576 each); in double precision. */
-double orc_thumb_diff(const uint8_t* ta, const uint8_t* tb, const uint8_t* uva, const uint8_t* uvb) {
-    int64_t sy = 0, su = 0, sv = 0;
+/* The luma thumbnail-difference gate between frames k-1 and k: the mean
+ * absolute difference of their 36 x 64 luma thumbnails. */
+double orc_thumb_diff(const uint8_t* ta, const uint8_t* tb) {
+    int64_t sy = 0;
     for (int64_t i = 0; i < 2304; i++) sy += labs((long)ta[i] - (long)tb[i]);
-    double d = (double)sy / 2304.0;
-    if (uva && uvb) {
-        for (int64_t i = 0; i < 576; i++) su += labs((long)uva[i] - (long)uvb[i]);
-        for (int64_t i = 576; i < 1152; i++) sv += labs((long)uva[i] - (long)uvb[i]);
-        d += (double)su / 576.0 + (double)sv / 576.0;
+    return (double)sy / 2304.0;
+}
+
+/* The luma + chroma gate: over two coarse YUV thumbnails, the mean absolute
+ * difference of the Y samples plus that of the U samples plus that of the V
+ * samples (192 each). */
+double orc_thumb_diff_yuv(const uint8_t* ya, const uint8_t* yb) {
+    double d = 0.0;
+    for (int64_t p = 0; p < 3; p++) {
+        int64_t sp = 0;
+        for (int64_t i = 0; i < 192; i++) sp += labs((long)ya[p * 192 + i] - (long)yb[p * 192 + i]);
+        d += (double)sp / 192.0;
     }
     return d;
 }

@@ -195,6 +195,10 @@ int device_sm_count();
 scn_status cnn_forward_counted(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
                                int64_t max_pairs, const int* d_pairs, float* d_logits, cudaStream_t st,
                                const int32_t* d_out_index);
+// Luma thumbnails of both frames of listed pairs i < *count (sequence elements
+// prev[i], cur[i]) into out[element] (scn_resize.cu); max_pairs bounds *count.
+scn_status launch_thumbs_listed(const scn_seq* s, const int32_t* prev, const int32_t* cur, const int* count,
+                                int64_t max_pairs, uint8_t* out, cudaStream_t st);
 // Release a sequence's gated-path workspace (scn_proposal.cu).
 void free_gate_workspace(scn_seq* s);
 // Zero the gated-path workspace's kernel scratch after a device timeout, on st.

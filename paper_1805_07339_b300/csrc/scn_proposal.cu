@@ -93,53 +93,47 @@ __device__ __forceinline__ unsigned thumb_l1(const uint8_t* thumbs, int64_t k, i
     return __reduce_add_sync(0xffffffffu, s);
 }
 
-// Sum of |uv[k] - uv[k-1]| over the 1152 chroma-thumbnail samples (U then V),
-// 0 for k = 0, by one warp (16-byte pieces; uv is 16-byte aligned); in every lane.
-__device__ __forceinline__ unsigned uv_l1(const uint8_t* uv, int64_t k, int lane) {
+// The luma + chroma gate of element k (0 for k = 0) by one warp: mean |dY| +
+// mean |dU| + mean |dV| over two coarse YUV thumbnails (192 samples per plane,
+// 576 bytes, 16-byte aligned), i.e. the sum of all 576 differences / 192.
+__device__ __forceinline__ float yuv_gate(const uint8_t* yuv, int64_t k, int lane) {
     unsigned s = 0;
-    if (k > 0) {
-        const uint4* a = reinterpret_cast<const uint4*>(uv + k * 1152);
-        const uint4* b = reinterpret_cast<const uint4*>(uv + (k - 1) * 1152);
-#pragma unroll
-        for (int i = lane; i < 72; i += 32) {
-            const uint4 x = a[i], y = b[i];
-            s = __vsadu4(x.x, y.x) + __vsadu4(x.y, y.y) + __vsadu4(x.z, y.z) + __vsadu4(x.w, y.w) + s;
-        }
+    if (k > 0 && lane < 36) {
+        const uint4 x = reinterpret_cast<const uint4*>(yuv + k * 576)[lane];
+        const uint4 y = reinterpret_cast<const uint4*>(yuv + (k - 1) * 576)[lane];
+        s = __vsadu4(x.x, y.x) + __vsadu4(x.y, y.y) + __vsadu4(x.z, y.z) + __vsadu4(x.w, y.w);
     }
-    return __reduce_add_sync(0xffffffffu, s);
-}
-
-// The difference gate: mean |dY| over the 2304 luma samples, plus (uv given) the
-// mean |dU| and |dV| over 576 samples each.
-__device__ __forceinline__ float gate_diff(const uint8_t* thumbs, const uint8_t* uv, int64_t k, int lane) {
-    const unsigned t = thumb_l1(thumbs, k, lane);
-    float d = static_cast<float>(t) / 2304.f;
-    if (uv) d += static_cast<float>(uv_l1(uv, k, lane)) / 576.f;
-    return d;
+    if (k > 0 && lane < 4) {
+        const uint4 x = reinterpret_cast<const uint4*>(yuv + k * 576)[32 + lane];
+        const uint4 y = reinterpret_cast<const uint4*>(yuv + (k - 1) * 576)[32 + lane];
+        s += __vsadu4(x.x, y.x) + __vsadu4(x.y, y.y) + __vsadu4(x.z, y.z) + __vsadu4(x.w, y.w);
+    }
+    return static_cast<float>(__reduce_add_sync(0xffffffffu, s)) / 192.f;
 }
 
 constexpr int kDiffWarps = 8;  // frames per 256-thread block, one warp each
 
-// the difference gate of every element (0 for k = 0)
-__global__ void __launch_bounds__(32 * kDiffWarps) thumb_diff_kernel(const uint8_t* thumbs, const uint8_t* uv,
+// the luma gate (thumbs given) or the luma + chroma gate (yuv given) of every element (0 for k = 0)
+__global__ void __launch_bounds__(32 * kDiffWarps) thumb_diff_kernel(const uint8_t* thumbs, const uint8_t* yuv,
                                                                      int64_t n, float* diff) {
     const int64_t k = blockIdx.x * static_cast<int64_t>(kDiffWarps) + (threadIdx.x >> 5);
     if (k >= n) return;
-    const float d = gate_diff(thumbs, uv, k, threadIdx.x & 31);
-    if ((threadIdx.x & 31) == 0) diff[k] = d;
+    const int lane = threadIdx.x & 31;
+    const float d = yuv ? yuv_gate(yuv, k, lane) : static_cast<float>(thumb_l1(thumbs, k, lane)) / 2304.f;
+    if (lane == 0) diff[k] = d;
 }
 
 // Cascade prefilter, in the thumbnail-difference launch: d_diff[k] as
 // thumb_diff_kernel writes it, every gate value set below any threshold, and
 // each pair whose difference exceeds tau_diff listed for the network
 // (thumbnail indices k-1, k, whose logit goes to gate element k).
-__global__ void __launch_bounds__(32 * kDiffWarps) diff_prefilter_kernel(const uint8_t* thumbs, const uint8_t* uv,
-                                                                         int64_t n, float tau_diff, float* diff,
-                                                                         float* gate, int32_t* prev, int32_t* cur,
-                                                                         int32_t* elem, int* count) {
+__global__ void __launch_bounds__(32 * kDiffWarps) diff_prefilter_kernel(const uint8_t* yuv, int64_t n,
+                                                                         float tau_diff, float* diff, float* gate,
+                                                                         int32_t* prev, int32_t* cur, int32_t* elem,
+                                                                         int* count) {
     const int64_t k = blockIdx.x * static_cast<int64_t>(kDiffWarps) + (threadIdx.x >> 5);
     if (k >= n) return;
-    const float dk = gate_diff(thumbs, uv, k, threadIdx.x & 31);
+    const float dk = yuv_gate(yuv, k, threadIdx.x & 31);
     if ((threadIdx.x & 31) == 0) {
         diff[k] = dk;
         gate[k] = -INFINITY;
@@ -222,21 +216,26 @@ using namespace scn;
 
 extern "C" {
 
-scn_status scn_thumb_diff_yuv(const uint8_t* d_thumbs, const uint8_t* d_uv, int64_t n, float* d_diff,
-                              void* stream) {
+scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, void* stream) {
     if (n < 0) return SCN_EINVAL;
     if (n == 0) return SCN_OK;
     if (!d_thumbs || !d_diff || (reinterpret_cast<uintptr_t>(d_thumbs) & 3u)) return SCN_EINVAL;
-    if (d_uv && (reinterpret_cast<uintptr_t>(d_uv) & 15u)) return SCN_EINVAL;
     if (n > 0x7fffffff) return SCN_ERANGE;
     thumb_diff_kernel<<<static_cast<unsigned>((n + kDiffWarps - 1) / kDiffWarps), 32 * kDiffWarps, 0,
-                        static_cast<cudaStream_t>(stream)>>>(d_thumbs, d_uv, n, d_diff);
+                        static_cast<cudaStream_t>(stream)>>>(d_thumbs, nullptr, n, d_diff);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }
 
-scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, void* stream) {
-    return scn_thumb_diff_yuv(d_thumbs, nullptr, n, d_diff, stream);
+scn_status scn_thumb_diff_yuv(const uint8_t* d_yuv, int64_t n, float* d_diff, void* stream) {
+    if (n < 0) return SCN_EINVAL;
+    if (n == 0) return SCN_OK;
+    if (!d_yuv || !d_diff || (reinterpret_cast<uintptr_t>(d_yuv) & 15u)) return SCN_EINVAL;
+    if (n > 0x7fffffff) return SCN_ERANGE;
+    thumb_diff_kernel<<<static_cast<unsigned>((n + kDiffWarps - 1) / kDiffWarps), 32 * kDiffWarps, 0,
+                        static_cast<cudaStream_t>(stream)>>>(nullptr, d_yuv, n, d_diff);
+    SCN_CUDA_TRY(cudaGetLastError());
+    return SCN_OK;
 }
 
 scn_status scn_gated_hist_scores(scn_seq* s, const float* d_gate, float tau, uint8_t* d_proposed, uint32_t* d_score,
@@ -313,10 +312,11 @@ scn_status scn_proposal_hist_scores(scn_seq* s, scn_cnn* net, float tau, uint8_t
 
 
 scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, float tau_net, uint8_t* d_thumbs,
-                                   uint8_t* d_uv, float* d_diff, float* d_gate, uint8_t* d_proposed,
+                                   uint8_t* d_yuv, float* d_diff, float* d_gate, uint8_t* d_proposed,
                                    uint32_t* d_score, uint8_t* d_flag, int64_t* h_nproposed, void* stream) {
-    if (!s || !net || !d_thumbs || !d_diff || !d_gate || !d_proposed || !d_score || !d_flag) return SCN_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(d_thumbs) & 15u) || (reinterpret_cast<uintptr_t>(d_uv) & 15u)) return SCN_EINVAL;
+    if (!s || !net || !d_thumbs || !d_yuv || !d_diff || !d_gate || !d_proposed || !d_score || !d_flag)
+        return SCN_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_thumbs) & 15u) || (reinterpret_cast<uintptr_t>(d_yuv) & 15u)) return SCN_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_diff) | reinterpret_cast<uintptr_t>(d_gate)) & 3u) return SCN_EINVAL;
     if (h_nproposed) *h_nproposed = 0;
     if (s->n == 0) return SCN_OK;
@@ -325,13 +325,17 @@ scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, flo
     scn_status st = ensure_ws(s, ws);
     if (st != SCN_OK) return st;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    st = scn_thumbs_yuv(s, d_thumbs, d_uv, stream);
+    // coarse YUV thumbnails of every frame (the gate's input), not the luma thumbnails
+    st = scn_thumbs_yuv(s, nullptr, d_yuv, stream);
     if (st != SCN_OK) return st;
     SCN_CUDA_TRY(cudaMemsetAsync(ws->pre_count, 0, sizeof(int), cs));
     diff_prefilter_kernel<<<static_cast<unsigned>((s->n + kDiffWarps - 1) / kDiffWarps), 32 * kDiffWarps, 0, cs>>>(
-        d_thumbs, d_uv, s->n, tau_diff, d_diff, d_gate, ws->pre_prev, ws->pre_cur, ws->pre_elem, ws->pre_count);
+        d_yuv, s->n, tau_diff, d_diff, d_gate, ws->pre_prev, ws->pre_cur, ws->pre_elem, ws->pre_count);
     SCN_CUDA_TRY(cudaGetLastError());
     if (s->n > 1) {
+        // luma thumbnails only for the frames of the listed pairs: what the network reads
+        st = launch_thumbs_listed(s, ws->pre_prev, ws->pre_cur, ws->pre_count, s->n - 1, d_thumbs, cs);
+        if (st != SCN_OK) return st;
         // the network only on the listed pairs (the launch is sized for all n-1 and reads the
         // count); the logit of listed pair i goes straight to d_gate[elem[i]]
         st = cnn_forward_counted(net, d_thumbs, ws->pre_prev, ws->pre_cur, s->n - 1, ws->pre_count, d_gate, cs,

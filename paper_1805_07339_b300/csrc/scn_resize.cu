@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "scn_internal.h"
 
 namespace scn {
@@ -111,25 +113,62 @@ __global__ void __launch_bounds__(256) resize_kernel(ResizeArgs a) {
     }
 }
 
-// One block per frame: luma thumbnail out[k][r][c] = Y[s r][s c] and, when uv is
-// given, the chroma thumbnail uv[k][p][r][c] (p = U, V) of the chroma sample
-// (s c, s r), the one under luma pixel (2 s c, 2 s r).
-__global__ void __launch_bounds__(256) thumbs_kernel(const uint8_t* nv12, int64_t stride, int W, int H, int s,
-                                                    const int32_t* slot, uint8_t* out, uint8_t* uv) {
+// Thumbnail gathers: every sample is its own 32-byte sector request, so a
+// thread issues all of its loads before its first store (byte pointers may
+// alias, which would otherwise keep each load behind the previous store).
+constexpr int kThumbThreads = 192;  // 2304 = 12 x 192 luma samples; 192 coarse samples per plane
+
+// Luma thumbnail of one frame f into o: o[r][c] = Y[s r][s c], 12 samples per thread.
+__device__ __forceinline__ void luma_thumb(const uint8_t* __restrict__ f, int W, int s, uint8_t* __restrict__ o) {
+    uint8_t v[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        const int i = threadIdx.x + q * kThumbThreads, r = i >> 6, c = i & 63;
+        v[q] = __ldg(f + static_cast<int64_t>(s * r) * W + s * c);
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) o[threadIdx.x + q * kThumbThreads] = v[q];
+}
+
+// One block per frame: the luma thumbnail out[k] (when out is given) and the
+// coarse YUV thumbnail (when yuv is given): yuv[k][0][r][c] = Y[6 s r][2 s c],
+// yuv[k][1..2][r][c] = U, V of chroma sample (s c, 3 s r), the one under that
+// luma pixel (one 16-bit load for both), r < 6, c < 32.  The gather's cost is
+// the 128-byte lines it touches, so the coarse thumbnail samples 6 luma rows
+// and 6 chroma rows (180 lines of a 1080p frame against 540 for the luma
+// thumbnail).
+__global__ void __launch_bounds__(kThumbThreads) thumbs_kernel(const uint8_t* __restrict__ nv12, int64_t stride, int W,
+                                                              int H, int s, const int32_t* __restrict__ slot,
+                                                              uint8_t* __restrict__ out, uint8_t* __restrict__ yuv) {
     const int k = blockIdx.x;
     const uint8_t* f = nv12 + static_cast<int64_t>(slot[k]) * stride;
-    for (int i = threadIdx.x; i < 36 * 64; i += blockDim.x) {
-        const int r = i >> 6, c = i & 63;
-        out[static_cast<int64_t>(k) * 2304 + i] = __ldg(f + static_cast<int64_t>(s * r) * W + s * c);
-    }
-    if (uv) {
+    if (out) luma_thumb(f, W, s, out + static_cast<int64_t>(k) * 2304);
+    if (yuv) {
         const uint8_t* plane = f + static_cast<int64_t>(W) * H;
-        for (int i = threadIdx.x; i < 18 * 32; i += blockDim.x) {
-            const int r = i >> 5, c = i & 31;
-            const uint16_t w = __ldg(reinterpret_cast<const uint16_t*>(plane + static_cast<int64_t>(s * r) * W + 2 * s * c));
-            uv[static_cast<int64_t>(k) * 1152 + i] = static_cast<uint8_t>(w & 0xFF);
-            uv[static_cast<int64_t>(k) * 1152 + 576 + i] = static_cast<uint8_t>(w >> 8);
-        }
+        const int i = threadIdx.x, r = i >> 5, c = i & 31;  // 192 threads = 6 x 32 samples
+        const uint8_t y = __ldg(f + static_cast<int64_t>(6 * s * r) * W + 2 * s * c);
+        const uint16_t w = __ldg(reinterpret_cast<const uint16_t*>(plane + static_cast<int64_t>(3 * s * r) * W + 2 * s * c));
+        uint8_t* o = yuv + static_cast<int64_t>(k) * 576;
+        o[i] = y;
+        o[192 + i] = static_cast<uint8_t>(w & 0xFF);
+        o[384 + i] = static_cast<uint8_t>(w >> 8);
+    }
+}
+
+// Luma thumbnails of the two frames of each listed pair i < *count (elements
+// prev[i] and cur[i] of the sequence) into out[element]; a frame shared by two
+// listed pairs is written twice with the same bytes.  One block per frame of a
+// listed pair (block 2i + q), grid-stride over them.
+__global__ void __launch_bounds__(kThumbThreads) thumbs_listed_kernel(const uint8_t* __restrict__ nv12, int64_t stride,
+                                                                     int W, int s, const int32_t* __restrict__ slot,
+                                                                     const int32_t* __restrict__ prev,
+                                                                     const int32_t* __restrict__ cur,
+                                                                     const int* __restrict__ count,
+                                                                     uint8_t* __restrict__ out) {
+    const int64_t m2 = 2 * static_cast<int64_t>(*count);
+    for (int64_t j = blockIdx.x; j < m2; j += gridDim.x) {
+        const int32_t k = (j & 1) ? cur[j >> 1] : prev[j >> 1];
+        luma_thumb(nv12 + static_cast<int64_t>(slot[k]) * stride, W, s, out + static_cast<int64_t>(k) * 2304);
     }
 }
 
@@ -170,6 +209,24 @@ scn_status launch_resize(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean
 }  // namespace
 }  // namespace scn
 
+namespace scn {
+scn_status launch_thumbs_listed(const scn_seq* s, const int32_t* prev, const int32_t* cur, const int* count,
+                                int64_t max_pairs, uint8_t* out, cudaStream_t st) {
+    const int W = s->table->W, H = s->table->H;
+    if (W % 64 || H % 36 || W / 64 != H / 36) return SCN_EUNSUPPORTED;
+    if (max_pairs <= 0) return SCN_OK;
+    // one block per listed frame, sized for the common case (a prefilter that passes a few
+    // percent of the pairs); more listed frames loop over the same blocks
+    int sms = device_sm_count();
+    if (sms <= 0) sms = 148;
+    const unsigned grid = static_cast<unsigned>(std::min<int64_t>(2 * max_pairs, 4LL * sms));
+    thumbs_listed_kernel<<<grid, kThumbThreads, 0, st>>>(s->table->d_nv12, s->table->frame_stride, W, W / 64,
+                                                         s->d_slot, prev, cur, count, out);
+    SCN_CUDA_TRY(cudaGetLastError());
+    return SCN_OK;
+}
+}  // namespace scn
+
 extern "C" {
 
 scn_status scn_resize_norm(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean, const float* h_std, int32_t dtype,
@@ -190,18 +247,21 @@ scn_status scn_resize_norm_both(scn_seq* s, int32_t oh, int32_t ow, const float*
     return scn::launch_resize(s, oh, ow, h_mean, h_std, d_out_f32, static_cast<__nv_bfloat16*>(d_out_bf16), stream);
 }
 
-scn_status scn_thumbs_yuv(scn_seq* s, uint8_t* d_thumb, uint8_t* d_uv, void* stream) {
-    if (!s || !d_thumb) return SCN_EINVAL;
+scn_status scn_thumbs_yuv(scn_seq* s, uint8_t* d_thumb, uint8_t* d_yuv, void* stream) {
+    if (!s || (!d_thumb && !d_yuv)) return SCN_EINVAL;
     const int W = s->table->W, H = s->table->H;
     if (W % 64 || H % 36 || W / 64 != H / 36) return SCN_EUNSUPPORTED;
     if (s->n == 0) return SCN_OK;
     if (s->n > 0x7fffffff) return SCN_ERANGE;
-    scn::thumbs_kernel<<<static_cast<unsigned>(s->n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        s->table->d_nv12, s->table->frame_stride, W, H, W / 64, s->d_slot, d_thumb, d_uv);
+    scn::thumbs_kernel<<<static_cast<unsigned>(s->n), scn::kThumbThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        s->table->d_nv12, s->table->frame_stride, W, H, W / 64, s->d_slot, d_thumb, d_yuv);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }
 
-scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream) { return scn_thumbs_yuv(s, d_thumb, nullptr, stream); }
+scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream) {
+    if (!d_thumb) return SCN_EINVAL;
+    return scn_thumbs_yuv(s, d_thumb, nullptr, stream);
+}
 
 }  // extern "C"

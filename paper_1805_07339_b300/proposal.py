@@ -65,8 +65,8 @@ class VideoSource:
         scn.scn_hist_scores(self.seq, self.hist, self.score, self.flag)
         return self.flag
 
-    def thumbs(self, out, uv=None) -> None:
-        scn.scn_thumbs_yuv(self.seq, out, uv)
+    def thumbs(self, out, yuv=None) -> None:
+        scn.scn_thumbs_yuv(self.seq, out, yuv)
 
     def close(self) -> None:
         scn.scn_seq_destroy(self.seq)
@@ -74,11 +74,11 @@ class VideoSource:
 
 
 def build_pairs(torch, src: VideoSource, ids: list[int], chroma: bool = False):
-    """Thumbnails of every frame (and, with `chroma`, chroma thumbnails), and
+    """Thumbnails of every frame (and, with `chroma`, coarse YUV thumbnails), and
     (prev, cur, label) of every consecutive pair."""
     T = src.T
     thumbs = torch.empty((len(ids) * T, 36, 64), dtype=torch.uint8, device="cuda")
-    uv = torch.empty((len(ids) * T, 2, 18, 32), dtype=torch.uint8, device="cuda") if chroma else None
+    uv = torch.empty((len(ids) * T, 3, 6, 32), dtype=torch.uint8, device="cuda") if chroma else None
     labels = []
     for i, vid in enumerate(ids):
         src.load(vid)
@@ -157,7 +157,7 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
     proposed pairs."""
     T = src.T
     thumbs = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
-    uv = torch.empty((T, 2, 18, 32), dtype=torch.uint8, device="cuda")
+    yuv = torch.empty((T, 3, 6, 32), dtype=torch.uint8, device="cuda")
     zl = torch.full((T,), -1e30, dtype=torch.float32, device="cuda")
     diff = torch.empty(T, dtype=torch.float32, device="cuda")
     prop = torch.empty(T, dtype=torch.uint8, device="cuda")
@@ -194,10 +194,10 @@ def evaluate(torch, net: int, tau: float, tau_diff: float, src: VideoSource, ids
                     scn.scn_proposal_hist_scores(src.seq, net, tau, thumbs, zl, prop, sc, fl, count=False)
                 elif gate == "cascade":
                     scn.scn_cascade_hist_scores(src.seq, net, tau_pre, tau if tau_cascade is None else tau_cascade,
-                                                thumbs, diff, zl, prop, sc, fl, count=False, uv=uv)
+                                                thumbs, yuv, diff, zl, prop, sc, fl, count=False)
                 elif gate == "diff_yuv":
-                    src.thumbs(thumbs, uv)
-                    scn.scn_thumb_diff_yuv(thumbs, uv, T, diff)
+                    src.thumbs(None, yuv)
+                    scn.scn_thumb_diff_yuv(yuv, T, diff)
                     scn.scn_gated_hist_scores(src.seq, diff, tau_yuv, prop, sc, fl, count=False)
                 else:
                     src.thumbs(thumbs)
@@ -256,7 +256,7 @@ def run(torch, steps: int = 6000, batch: int = 256, lr: float = 1e-3, seed: int 
             scn.scn_thumb_diff(vth, vth.shape[0], d)
             dv = d.cpu().numpy()[vc.cpu().numpy()]
             tau_d = choose_tau(dv, vlab)
-            scn.scn_thumb_diff_yuv(vth, vuv, vth.shape[0], d)
+            scn.scn_thumb_diff_yuv(vuv, vth.shape[0], d)
             dyv = d.cpu().numpy()[vc.cpu().numpy()]
             tau_yuv = choose_tau(dyv, vlab)
             # cascade: the luma + chroma difference gate as the prefilter (a boundary moves luma or

@@ -108,7 +108,7 @@ SIGNATURES = [
     ("scn_thumb_diff", c_i32, [c_vp, c_i64, c_vp, c_vp]),
     ("scn_cascade_hist_scores", c_i32, [c_vp, c_vp, ctypes.c_float, ctypes.c_float, c_vp, c_vp, c_vp, c_vp, c_vp,
                                         c_vp, c_vp, _P(c_i64), c_vp]),
-    ("scn_thumb_diff_yuv", c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    ("scn_thumb_diff_yuv", c_i32, [c_vp, c_i64, c_vp, c_vp]),
     ("scn_thumbs_yuv", c_i32, [c_vp, c_vp, c_vp, c_vp]),
     ("scn_resize_norm", c_i32, [c_vp, c_i32, c_i32, _P(ctypes.c_float), _P(ctypes.c_float), c_i32, c_vp, c_vp]),
     ("scn_thumbs", c_i32, [c_vp, c_vp, c_vp]),
@@ -457,13 +457,13 @@ def scn_proposal_hist_scores(s: int, net: int, tau: float, thumbs, logits, propo
     return m.value if count else None
 
 
-def scn_cascade_hist_scores(s: int, net: int, tau_diff: float, tau_net: float, thumbs, diff, gate, proposed, score,
-                            flag, stream=None, count: bool = True, uv=None):
-    """The difference gate (over luma and, when `uv` is given, chroma thumbnails) as a
-    prefilter, the network on what passes, the exact kernel on pairs that pass both
-    (see include/scn.h)."""
+def scn_cascade_hist_scores(s: int, net: int, tau_diff: float, tau_net: float, thumbs, yuv, diff, gate, proposed,
+                            score, flag, stream=None, count: bool = True):
+    """The luma + chroma difference gate over coarse YUV thumbnails as a prefilter, the
+    network on what passes (luma thumbnails gathered for those pairs only), the exact
+    kernel on pairs that pass both (see include/scn.h)."""
     m = c_i64()
-    _check(_lib.scn_cascade_hist_scores(s, net, tau_diff, tau_net, _ptr(thumbs), _ptr(uv), _ptr(diff), _ptr(gate),
+    _check(_lib.scn_cascade_hist_scores(s, net, tau_diff, tau_net, _ptr(thumbs), _ptr(yuv), _ptr(diff), _ptr(gate),
                                         _ptr(proposed), _ptr(score), _ptr(flag), ctypes.byref(m) if count else None,
                                         _stream(stream)),
            "scn_cascade_hist_scores")
@@ -474,8 +474,8 @@ def scn_thumb_diff(thumbs, n: int, diff, stream=None) -> None:
     _check(_lib.scn_thumb_diff(_ptr(thumbs), n, _ptr(diff), _stream(stream)), "scn_thumb_diff")
 
 
-def scn_thumb_diff_yuv(thumbs, uv, n: int, diff, stream=None) -> None:
-    _check(_lib.scn_thumb_diff_yuv(_ptr(thumbs), _ptr(uv), n, _ptr(diff), _stream(stream)), "scn_thumb_diff_yuv")
+def scn_thumb_diff_yuv(yuv, n: int, diff, stream=None) -> None:
+    _check(_lib.scn_thumb_diff_yuv(_ptr(yuv), n, _ptr(diff), _stream(stream)), "scn_thumb_diff_yuv")
 
 
 def scn_resize_norm(s: int, oh: int, ow: int, mean, std, dtype: int, out, stream=None) -> None:
@@ -495,8 +495,9 @@ def scn_thumbs(s: int, thumb, stream=None) -> None:
     _check(_lib.scn_thumbs(s, _ptr(thumb), _stream(stream)), "scn_thumbs")
 
 
-def scn_thumbs_yuv(s: int, thumb, uv, stream=None) -> None:
-    _check(_lib.scn_thumbs_yuv(s, _ptr(thumb), _ptr(uv), _stream(stream)), "scn_thumbs_yuv")
+def scn_thumbs_yuv(s: int, thumb, yuv, stream=None) -> None:
+    """thumb: [n][36][64] luma thumbnails or None; yuv: [n][3][6][32] coarse YUV thumbnails or None."""
+    _check(_lib.scn_thumbs_yuv(s, _ptr(thumb), _ptr(yuv), _stream(stream)), "scn_thumbs_yuv")
 
 
 def scn_space(s: int, values, elem_bytes: int, out, fill_mode: int = SCN_FILL_VALUE, fill: bytes | None = None,

@@ -446,14 +446,18 @@ def test_thumbs_parity(scn, orc, W, H):
         got = out.cpu().numpy()
         for j, k in enumerate([2, 0, 1]):
             assert np.array_equal(got[j], orc.thumb_frame(frames[k], W, H))
-        # luma and chroma thumbnails in one launch: the same luma, chroma equal to the oracle's
+        # luma and coarse YUV thumbnails in one launch: the same luma, YUV equal to the oracle's
         out2 = torch.zeros((n, 36, 64), dtype=torch.uint8, device="cuda")
-        uv = torch.zeros((n, 2, 18, 32), dtype=torch.uint8, device="cuda")
-        scn.scn_thumbs_yuv(seq, out2, uv)
+        yuv = torch.zeros((n, 3, 6, 32), dtype=torch.uint8, device="cuda")
+        scn.scn_thumbs_yuv(seq, out2, yuv)
         assert torch.equal(out2, out)
-        guv = uv.cpu().numpy()
+        gy = yuv.cpu().numpy()
         for j, k in enumerate([2, 0, 1]):
-            assert np.array_equal(guv[j], orc.thumb_uv_frame(frames[k], W, H))
+            assert np.array_equal(gy[j], orc.thumb_yuv_frame(frames[k], W, H))
+        # YUV only
+        yuv2 = torch.zeros_like(yuv)
+        scn.scn_thumbs_yuv(seq, None, yuv2)
+        assert torch.equal(yuv2, yuv)
         scn.scn_seq_destroy(seq)
     finally:
         dev.close()

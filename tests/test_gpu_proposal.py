@@ -106,29 +106,22 @@ def test_thumb_diff(scn, orc, tiny):
 
 
 def test_thumb_diff_yuv_matches_oracle(scn, orc, tiny):
-    """The luma + chroma difference gate against the oracle's, on the generated video and on
-    random bytes (every sample difference up to 255)."""
+    """The luma + chroma difference gate over coarse YUV thumbnails against the oracle's, on the
+    generated video and on random bytes (every sample difference up to 255)."""
     T = tiny["T"]
-    th = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
-    uv = torch.empty((T, 2, 18, 32), dtype=torch.uint8, device="cuda")
-    scn.scn_thumbs_yuv(tiny["seq"], th, uv)
+    yuv = torch.empty((T, 3, 6, 32), dtype=torch.uint8, device="cuda")
+    scn.scn_thumbs_yuv(tiny["seq"], None, yuv)
     rng = np.random.default_rng(5)
-    rth = rng.integers(0, 256, (8, 36, 64), dtype=np.uint8)
-    ruv = rng.integers(0, 256, (8, 2, 18, 32), dtype=np.uint8)
-    for t_np, uv_np in ((th.cpu().numpy(), uv.cpu().numpy()), (rth, ruv)):
-        n = len(t_np)
+    ryuv = rng.integers(0, 256, (8, 3, 6, 32), dtype=np.uint8)
+    for y_np in (yuv.cpu().numpy(), ryuv):
+        n = len(y_np)
         d = torch.empty(n, dtype=torch.float32, device="cuda")
-        scn.scn_thumb_diff_yuv(torch.from_numpy(t_np).cuda(), torch.from_numpy(uv_np).cuda(), n, d)
-        ref = [0.0] + [orc.thumb_diff(t_np[k - 1], t_np[k], uv_np[k - 1], uv_np[k]) for k in range(1, n)]
+        scn.scn_thumb_diff_yuv(torch.from_numpy(y_np).cuda(), n, d)
+        ref = [0.0] + [orc.thumb_diff_yuv(y_np[k - 1], y_np[k]) for k in range(1, n)]
         assert np.allclose(d.cpu().numpy(), ref, rtol=1e-6, atol=1e-5)
-        # without chroma: the luma gate, as scn_thumb_diff
-        d0 = torch.empty(n, dtype=torch.float32, device="cuda")
-        scn.scn_thumb_diff_yuv(torch.from_numpy(t_np).cuda(), None, n, d0)
-        ref0 = [0.0] + [orc.thumb_diff(t_np[k - 1], t_np[k]) for k in range(1, n)]
-        assert np.allclose(d0.cpu().numpy(), ref0, rtol=1e-6, atol=1e-6)
-    with pytest.raises(scn.ScnError):  # chroma thumbnails must be 16-byte aligned
-        raw = torch.zeros(2 * 1152 + 16, dtype=torch.uint8, device="cuda")
-        scn.scn_thumb_diff_yuv(th[:2], raw[4:4 + 2 * 1152], 2, torch.empty(2, device="cuda"))
+    with pytest.raises(scn.ScnError):  # coarse thumbnails must be 16-byte aligned
+        raw = torch.zeros(2 * 576 + 16, dtype=torch.uint8, device="cuda")
+        scn.scn_thumb_diff_yuv(raw[4:4 + 2 * 576], 2, torch.empty(2, device="cuda"))
 
 
 def test_learned_proposal_path_consistent(scn, tiny):
@@ -152,9 +145,8 @@ def test_learned_proposal_path_consistent(scn, tiny):
         scn.scn_cnn_destroy(net)
 
 
-@pytest.mark.parametrize("q_diff,q_net,chroma", [(0.5, 0.5, False), (0.0, 0.0, False), (1.1, 0.5, False),
-                                                 (0.2, 0.9, False), (0.5, 0.5, True), (0.9, 0.2, True)])
-def test_cascade_matches_its_two_thresholds(scn, tiny, q_diff, q_net, chroma):
+@pytest.mark.parametrize("q_diff,q_net", [(0.5, 0.5), (0.0, 0.0), (1.1, 0.5), (0.2, 0.9), (0.9, 0.2)])
+def test_cascade_matches_its_two_thresholds(scn, tiny, q_diff, q_net):
     """The cascade proposes exactly the pairs whose thumbnail difference and network
     logit both pass (thresholds at quantiles of the tiny video's own scores; 1.1 lists
     no pair at all); its gate holds the full forward's logits bit for bit on the listed
@@ -167,9 +159,9 @@ def test_cascade_matches_its_two_thresholds(scn, tiny, q_diff, q_net, chroma):
         th = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
         d = torch.empty(T, dtype=torch.float32, device="cuda")
         zz = torch.empty(T - 1, dtype=torch.float32, device="cuda")
-        uv = torch.empty((T, 2, 18, 32), dtype=torch.uint8, device="cuda") if chroma else None
-        scn.scn_thumbs_yuv(tiny["seq"], th, uv)
-        scn.scn_thumb_diff_yuv(th, uv, T, d)
+        yuv = torch.empty((T, 3, 6, 32), dtype=torch.uint8, device="cuda")
+        scn.scn_thumbs_yuv(tiny["seq"], th, yuv)
+        scn.scn_thumb_diff_yuv(yuv, T, d)
         scn.scn_cnn_forward(net, th, T - 1, zz)
         dh, zh = d.cpu().numpy(), zz.cpu().numpy()
         tau_d = float(np.quantile(dh[1:], min(q_diff, 1.0))) + (1.0 if q_diff > 1.0 else 0.0)
@@ -178,15 +170,20 @@ def test_cascade_matches_its_two_thresholds(scn, tiny, q_diff, q_net, chroma):
         d2 = torch.zeros_like(d)
         gate = torch.zeros(T, dtype=torch.float32, device="cuda")
         prop, sc, fl = _outs(T)
-        uv2 = torch.zeros_like(uv) if chroma else None
-        m = scn.scn_cascade_hist_scores(tiny["seq"], net, tau_d, tau_n, th2, d2, gate, prop, sc, fl, uv=uv2)
+        yuv2 = torch.zeros_like(yuv)
+        m = scn.scn_cascade_hist_scores(tiny["seq"], net, tau_d, tau_n, th2, yuv2, d2, gate, prop, sc, fl)
         p = _check(prop, sc, fl, tiny["exact"])
-        if chroma:
-            assert torch.equal(uv2, uv)
+        assert torch.equal(yuv2, yuv)
         listed = np.concatenate([[False], dh[1:] > tau_d])
         want = listed & np.concatenate([[False], zh > tau_n])
         assert np.array_equal(p, want) and m == int(want.sum())
-        assert torch.equal(th2, th) and np.array_equal(d2.cpu().numpy(), dh)
+        assert np.array_equal(d2.cpu().numpy(), dh)
+        # luma thumbnails written for both frames of every listed pair, nothing else
+        frames = np.zeros(T, dtype=bool)
+        frames[1:] |= dh[1:] > tau_d
+        frames[:-1] |= dh[1:] > tau_d
+        t2, t1 = th2.cpu().numpy(), th.cpu().numpy()
+        assert np.array_equal(t2[frames], t1[frames]) and not t2[~frames].any()
         g = gate.cpu().numpy()
         assert np.array_equal(g[listed].view(np.uint32), np.concatenate([[0.0], zh]).astype(np.float32)[listed].view(np.uint32))
         assert np.all(np.isneginf(g[~listed]))
@@ -210,11 +207,12 @@ def test_cascade_short_sequences(scn, tiny, n):
         scn.scn_cnn_set_params(net, he_uniform(4))
         m = max(n, 1)
         th = torch.full((m, 36, 64), 7, dtype=torch.uint8, device="cuda")
+        yuv = torch.full((m, 3, 6, 32), 7, dtype=torch.uint8, device="cuda")
         d = torch.full((m,), 5.0, dtype=torch.float32, device="cuda")
         gate = torch.full((m,), 5.0, dtype=torch.float32, device="cuda")
         prop, sc, fl = (torch.full((m,), 9, dtype=torch.uint8, device="cuda"), torch.full((m,), 9, dtype=torch.int32, device="cuda"),
                         torch.full((m,), 9, dtype=torch.uint8, device="cuda"))
-        cnt = scn.scn_cascade_hist_scores(seq, net, -1.0, -1e30, th, d, gate, prop, sc, fl)
+        cnt = scn.scn_cascade_hist_scores(seq, net, -1.0, -1e30, th, yuv, d, gate, prop, sc, fl)
         torch.cuda.synchronize()
         assert scn.scn_seq_sync_status(seq) == scn.SCN_OK
         assert scn.scn_cnn_sync_status(net) == scn.SCN_OK

@@ -238,22 +238,25 @@ def test_thumbnails(orc):
         assert np.array_equal(t, Yp[0: 36 * s: s, 0: 64 * s: s])
 
 
-def test_chroma_thumbnails(orc):
-    # the chroma sample under luma pixel (2 s c, 2 s r): U, V at chroma (s c, s r)
+def test_coarse_yuv_thumbnails(orc):
+    # Y at luma pixel (2 s c, 6 s r), U and V of the chroma sample (s c, 3 s r) that pixel uses
     for W, H in [(320, 180), (640, 360), (1920, 1080)]:
         rng = np.random.default_rng(W + 1)
         fr = rng.integers(0, 256, W * H * 3 // 2, dtype=np.uint8)
-        uv = orc.thumb_uv_frame(fr, W, H)
+        yuv = orc.thumb_yuv_frame(fr, W, H)
         s = W // 64
+        Yp = fr[: W * H].reshape(H, W)
         Up = fr[W * H:].reshape(H // 2, W)[:, 0::2]
         Vp = fr[W * H:].reshape(H // 2, W)[:, 1::2]
-        assert np.array_equal(uv[0], Up[0: 18 * s: s, 0: 32 * s: s])
-        assert np.array_equal(uv[1], Vp[0: 18 * s: s, 0: 32 * s: s])
+        assert np.array_equal(yuv[0], Yp[0: 36 * s: 6 * s, 0: 64 * s: 2 * s])
+        assert np.array_equal(yuv[0], orc.thumb_frame(fr, W, H)[0::6, 0::2])
+        assert np.array_equal(yuv[1], Up[0: 18 * s: 3 * s, 0: 32 * s: s])
+        assert np.array_equal(yuv[2], Vp[0: 18 * s: 3 * s, 0: 32 * s: s])
         # and it is the chroma that the conversion uses at those luma pixels
-        for r, c in [(0, 0), (17, 31), (5, 9)]:
-            y, x = 2 * s * r, 2 * s * c
-            assert uv[0, r, c] == fr[W * H + (y >> 1) * W + 2 * (x >> 1)]
-            assert uv[1, r, c] == fr[W * H + (y >> 1) * W + 2 * (x >> 1) + 1]
+        for r, c in [(0, 0), (5, 31), (3, 9)]:
+            y, x = 6 * s * r, 2 * s * c
+            assert yuv[1, r, c] == fr[W * H + (y >> 1) * W + 2 * (x >> 1)]
+            assert yuv[2, r, c] == fr[W * H + (y >> 1) * W + 2 * (x >> 1) + 1]
 
 
 def test_thumb_diff_hand_values(orc):
@@ -263,8 +266,10 @@ def test_thumb_diff_hand_values(orc):
     b[35, 63] = 255         # and one by 255
     assert orc.thumb_diff(a, b) == (320 + 255) / 2304
     assert orc.thumb_diff(b, a) == orc.thumb_diff(a, b) and orc.thumb_diff(a, a) == 0.0
-    ua = np.full((2, 18, 32), 128, dtype=np.uint8)
-    ub = ua.copy()
-    ub[0] = 160             # every U sample +32: mean 32
-    ub[1, :9] = 100         # half the V samples -28: mean 14
-    assert orc.thumb_diff(a, b, ua, ub) == (320 + 255) / 2304 + 32.0 + 14.0
+    ya = np.full((3, 6, 32), 128, dtype=np.uint8)
+    yb = ya.copy()
+    yb[0, 0, :] = 152       # 32 Y samples +24: 768 / 192 = 4
+    yb[1] = 160             # every U sample +32: mean 32
+    yb[2, :3] = 100         # half the V samples -28: mean 14
+    assert orc.thumb_diff_yuv(ya, yb) == 4.0 + 32.0 + 14.0
+    assert orc.thumb_diff_yuv(yb, ya) == orc.thumb_diff_yuv(ya, yb) and orc.thumb_diff_yuv(ya, ya) == 0.0
