@@ -92,8 +92,8 @@ struct Smem {
     PubMeta* pmeta;     // [2]
     uint64_t* full;     // [kStages]
     uint64_t* empty;    // [kStages]
-    uint64_t* cbar;     // consumers' CTA barrier (every consumer thread arrives)
-    uint64_t* accfull;  // [2] acc[b] holds an item's counts (the consumers' thread 0 arrives)
+    uint64_t* cbar;     // [kRegions] barrier of one table region's consumer warps
+    uint64_t* accfull;  // [2] acc[b] holds an item's counts (each region's first thread arrives)
     uint64_t* accfree;  // [2] the publisher has taken acc[b] (its 32 lanes arrive)
     int* abort_flag;
 };
@@ -107,12 +107,13 @@ __device__ __forceinline__ Smem carve(uint8_t* smem) {
     s.full = reinterpret_cast<uint64_t*>(s.pmeta + 2);
     s.empty = s.full + kStages;
     s.cbar = s.empty + kStages;
-    s.accfull = s.cbar + 1;
+    s.accfull = s.cbar + kRegions;
     s.accfree = s.accfull + 2;
     s.abort_flag = reinterpret_cast<int*>(s.accfree + 2);
     return s;
 }
-static_assert(kStages * sizeof(ChunkMeta) + 128 * 4 + 2 * sizeof(PubMeta) + (2 * kStages + 5) * 8 + 16 <= kSmemMisc,
+static_assert(kStages * sizeof(ChunkMeta) + 128 * 4 + 2 * sizeof(PubMeta) + (2 * kStages + kRegions + 4) * 8 + 16 <=
+                  kSmemMisc,
               "misc smem");
 
 __device__ __forceinline__ const Job& job_of(const Launch& L, int j) { return L.jobs ? L.jobs[j] : L.job0; }
@@ -319,12 +320,14 @@ __device__ __forceinline__ void count_unit(uint32_t lanereg, uint32_t inc, uint3
     }
 }
 
-// Cooperative flush by all consumer threads: every table row summed over its
-// 64 words and both 16-bit halves, extended bin folded into the final bin,
-// added into acc[48]; the table is left zeroed.
-__device__ __forceinline__ void flush_table(uint8_t* tab, uint32_t* acc, int ctid) {
-    const int lane = ctid & 31;
-    for (int row = ctid; row < kRegions * kTabRowsPerRegion; row += kNT) {
+// Flush of one table region by its own consumer threads (rt = thread within
+// the region): every row summed over its 64 words and both 16-bit halves,
+// extended bin folded into the final bin, added into acc[48]; the region's
+// rows are left zeroed.
+constexpr int kRegionThreads = kGroupWarps * 32;
+__device__ __forceinline__ void flush_region(uint8_t* tab, uint32_t* acc, int region, int rt) {
+    const int lane = rt & 31;
+    for (int row = region * kTabRowsPerRegion + rt; row < (region + 1) * kTabRowsPerRegion; row += kRegionThreads) {
         uint8_t* p = tab + row * 256;
         uint32_t lo = 0, hi = 0;
 #pragma unroll
@@ -418,13 +421,13 @@ __device__ void publish(const Job& J, int64_t n, int64_t k, int seg_rp, uint32_t
 
 __device__ __forceinline__ uint4 ldg128(const uint8_t* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
 
-// Barrier of the consumer threads, bounded: every consumer thread arrives
-// (release) and waits (acquire) for the phase.  A consumer that gave up earlier
-// has left the loop, so the others would wait for it forever on a named
+// Barrier of one table region's consumer threads, bounded: every one of them
+// arrives (release) and waits (acquire) for the phase.  A consumer that gave up
+// earlier has left the loop, so the others would wait for it forever on a named
 // barrier; here they give up too, after the launch's wait limit.
-__device__ __forceinline__ bool consumer_sync(const Launch& L, const Smem& s, uint32_t& phase) {
-    ptx::mbar_arrive(s.cbar);
-    const bool ok = ptx::mbar_wait_bounded(s.cbar, phase & 1u, wait_limit(L));
+__device__ __forceinline__ bool consumer_sync(const Launch& L, const Smem& s, int region, uint32_t& phase) {
+    ptx::mbar_arrive(&s.cbar[region]);
+    const bool ok = ptx::mbar_wait_bounded(&s.cbar[region], phase & 1u, wait_limit(L));
     ++phase;
     if (!ok) fail(L, s);
     return ok;
@@ -434,6 +437,7 @@ __device__ __forceinline__ bool consumer_sync(const Launch& L, const Smem& s, ui
 __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
     const int ctid = warp * 32 + lane;
     const int region = warp / kGroupWarps;
+    const int rt = ctid - region * kRegionThreads;  // thread within the region
     const uint32_t lanereg = static_cast<uint32_t>(lane * 4 + (warp & 1) * 128);
     const uint32_t inc = (warp & 2) ? 65536u : 1u;
     // table row of x = (x >> 16): shared base / 256 + region rows + channel rows + extended bin
@@ -514,27 +518,29 @@ __device__ void consume(const Launch& L, const Smem& s, int warp, int lane) {
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&s.empty[st]);
         if (m.seg_end) {
+            // each table region flushes on its own as soon as its four warps have counted
+            // the item; the other regions may still be counting it or already be on the next
             const uint32_t b = seg & 1u;
-            if (!consumer_sync(L, s, cphase)) break;  // every consumer has counted the item
+            if (!consumer_sync(L, s, region, cphase)) break;  // the region has counted the item
             // acc[b] was last filled two items ago: the publisher has taken it
             if (seg >= 2 && !ptx::mbar_wait_bounded(&s.accfree[b], ((seg >> 1) - 1) & 1u, wait_limit(L))) {
                 fail(L, s);
                 break;
             }
-            flush_table(s.tab, s.acc + 64 * b, ctid);
-            if (!consumer_sync(L, s, cphase)) break;  // table zeroed, acc[b] complete
-            if (ctid == 0) {
-                s.pmeta[b] = PubMeta{m.job, m.k, m.seg_rp, 0};
-                ptx::mbar_arrive(&s.accfull[b]);  // release: the counts and their item
+            flush_region(s.tab, s.acc + 64 * b, region, rt);
+            if (!consumer_sync(L, s, region, cphase)) break;  // region rows zeroed, its part of acc[b] added
+            if (rt == 0) {
+                if (region == 0) s.pmeta[b] = PubMeta{m.job, m.k, m.seg_rp, 0};
+                ptx::mbar_arrive(&s.accfull[b]);  // release; the phase completes with the last region
             }
             ++seg;
         }
     }
     // tell the publisher that no item follows (not after a failure: it then gives up by itself)
-    if (!aborted(s) && ctid == 0) {
+    if (!aborted(s) && rt == 0) {
         const uint32_t b = seg & 1u;
         if (seg < 2 || ptx::mbar_wait_bounded(&s.accfree[b], ((seg >> 1) - 1) & 1u, wait_limit(L))) {
-            s.pmeta[b] = PubMeta{-1, 0, 0, 0};
+            if (region == 0) s.pmeta[b] = PubMeta{-1, 0, 0, 0};
             ptx::mbar_arrive(&s.accfull[b]);
         } else {
             fail(L, s);
@@ -579,9 +585,9 @@ __global__ void __launch_bounds__(kHistThreads, 1) hist_kernel(const __grid_cons
             ptx::mbar_init(&s.full[i], 1);
             ptx::mbar_init(&s.empty[i], kConsumerWarps);
         }
-        ptx::mbar_init(s.cbar, kNT);
+        for (int r = 0; r < kRegions; ++r) ptx::mbar_init(&s.cbar[r], kRegionThreads);
         for (int i = 0; i < 2; ++i) {
-            ptx::mbar_init(&s.accfull[i], 1);
+            ptx::mbar_init(&s.accfull[i], kRegions);
             ptx::mbar_init(&s.accfree[i], 32);
         }
         *s.abort_flag = 0;
