@@ -71,9 +71,11 @@ constexpr int kSmemMisc = 1024;                           // accumulators + barr
 static_assert(kTabBytes + kSmemMisc <= kSmemLimit, "tables fit in shared memory");
 constexpr int kConsumerThreads = kConsumerWarps * 32;
 // Pixels of one work item at most: the table is flushed after every item, and
-// this keeps every 16-bit lane counter below 2^16 (each of the 512 consumer
-// threads counts at most 1/512 of an item's pixels, plus one unit).
+// this keeps every 16-bit lane counter below 2^16 (each counter belongs to one
+// consumer thread, which counts at most 1/kConsumerThreads of an item's
+// pixels plus one unit of 32).
 constexpr int64_t kItemPixelsMax = int64_t(1) << 24;
+static_assert(kItemPixelsMax / kConsumerThreads + 2 * 32 < 65536, "16-bit lane counters");
 
 }  // namespace scn
 
