@@ -859,13 +859,480 @@ __global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_
     if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+// ---------------------------------------------------------------------------
+// inference: warp-specialised pipeline over batches, one CTA per SM
+// ---------------------------------------------------------------------------
+// Four warp groups of four warps work on different batches at the same time,
+// each on buffers of its own, and hand each batch on through mbarriers:
+//   group 0 (warps 0-3):  X1 of batch j and its conv1 MMAs;
+//   group 1 (warps 4-7):  conv1 epilogue of batch j into A1[j & 1];
+//   group 2 (warps 8-11): conv2 of batch j into A2[j & 1];
+//   group 3 (warps 12-15): conv3 of batch j (warp 15 issues its MMAs), pooling
+//                         and the head (FC1, FC2).
+// The batch's time is then that of the slowest group rather than the sum of
+// the phases.  Each layer's MMAs are issued by the group that produced its
+// input (conv1) or by the group that consumes its output (conv2, conv3), lane
+// 0 of each of its warps, so no layer waits behind another's in an issue
+// queue, and the issuing is
+// spread: a thread issues one accumulating tcgen05.mma per ~145 cycles (the
+// next one waits for the one before, whatever accumulator it writes), while
+// 2 and 4 issuing threads reach 74 and 41 cycles per MMA of 128 x 32 x 16
+// (measured on the B300).  The per-batch buffer layouts and MMA operand
+// addresses are those of the two-CTA form above; X1 is single, A1 and A2
+// double-buffered, and their padding is written once.  Differences in
+// arithmetic: conv1's bias enters through the MMA (every X1 entry carries 1.0
+// in its two spare K slots, W1 holds the bias split into two BF16 parts
+// there, so the epilogue is one conversion with ReLU per two values), conv2
+// accumulates all 9 taps in one accumulator per tile, and conv3 its two K
+// halves in two.  Each group owns the four TMEM lane quadrants through its
+// four warps; TMEM holds conv1's accumulators twice (columns 0-159 and
+// 160-319, batch parity), conv2's at 320-447, conv3's at 448-511.  Every wait
+// is bounded (2 s), after which the thread records a timeout and stops
+// waiting; no thread leaves its loop early, so every barrier is still reached.
+constexpr int kPpThreads = 512;
+constexpr int kPpW1 = 0;                                   // [16][32]
+constexpr int kPpW2 = kPpW1 + 16 * 32 * 2;                 // 9 x [32][16]
+constexpr int kPpW3 = kPpW2 + 9 * 32 * 16 * 2;             // 9 x [32][32]
+constexpr int kPpBias = kPpW3 + 9 * 32 * 32 * 2;           // same float layout as the two-CTA form
+// mbarriers (count): X1 built (128 builder threads), X1 read by conv1 (4
+// issuers), conv1 tile done (2 TMEM buffers x 10 tiles, 1 each), conv1 TMEM
+// buffer read by group 1 (2, 4 warps each), A1[b] written
+// (128), A1[b] read by conv2 (4 issuers), conv2 tile done (4, 1 each), A2[b]
+// written (128), A2[b] read by conv3 (1 issuer), conv3 done (1 issuer).  A
+// group's TMEM accumulators are reused only after its own warps have read them
+// (groups 2 and 3 issue their layer's MMAs themselves, after a group barrier;
+// group 0 issues conv1's into a buffer that group 1 has released)
+constexpr int kBX1Full = 0, kBX1Free = 1, kBT1Full = 2, kBT1Free = kBT1Full + 2 * kFzT1, kBA1Full = kBT1Free + 2,
+              kBA1Free = kBA1Full + 2,
+              kBT2Full = kBA1Free + 2, kBA2Full = kBT2Full + 4, kBA2Free = kBA2Full + 2, kBT3Full = kBA2Free + 2,
+              kPpNBar = kBT3Full + 1;
+constexpr int kPpT1 = 0, kPpT2 = 2 * kFzT1 * 16, kPpT3 = kPpT2 + 4 * 32;  // TMEM columns (conv3: 2 x 32)
+constexpr int kPpBar = kPpBias + 1024;
+constexpr int kPpX1 = (kPpBar + kPpNBar * 8 + 16 + 1023) / 1024 * 1024;  // O1, E1 planes
+constexpr int kPpA1 = kPpX1 + kFzReg0Bytes;                               // 2 x A1
+constexpr int kPpA2Bytes = kFzF1T;  // A2 and what its dropped groups read beyond it
+constexpr int kPpA2 = kPpA1 + 2 * kFzReg1Bytes;                           // 2 x A2
+constexpr int kPpPart = kPpA2 + 2 * kPpA2Bytes;                           // 2 x [pair][5][32] fp32
+constexpr int kPpF1 = kPpPart + 2 * kFzPairs * 5 * 32 * 4;                // F1 transposed, [32][64] fp32
+constexpr int kPpSmem = kPpF1 + 32 * 64 * 4;
+constexpr int kPpTmemCols = 512;
+constexpr uint32_t kPpOnes = 0x3F803F80u;  // BF16 1.0 in both halves: X1's bias slots
+static_assert(kPpT3 + 64 <= kPpTmemCols, "TMEM columns");
+static_assert(kPpSmem <= 232448, "one CTA per SM");
+static_assert(kFzReg1Bytes % 16 == 0 && kPpA2Bytes % 16 == 0 && kFzReg0Bytes % 16 == 0, "16-byte buffers");
+static_assert(kFzPairs * 36 % 4 == 0, "build rows split evenly over the four builder warps");
+
+// bounded wait by one thread (no warp-wide step: callers may be a single lane)
+__device__ __forceinline__ bool pp_wait1(uint64_t* bar, uint32_t par, bool ok, int* status) {
+    if (ok && !ptx::mbar_wait_bounded(bar, par, kWaitNs)) {
+        atomicOr(status, kStatusTimeout);
+        ok = false;
+    }
+    return ok;
+}
+
+__device__ __forceinline__ void pp_group_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void pp_group_sync96(int id) { asm volatile("bar.sync %0, 96;" ::"r"(id) : "memory"); }
+
+// max(lo, 0) and max(hi, 0) rounded to BF16 (round to nearest even), packed lo | hi << 16
+__device__ __forceinline__ uint32_t relu_pack(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+__global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_constant__ FusedArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = warp >> 2, quad = warp & 3;
+    const int r = 32 * quad + lane;  // TMEM lane = tile row of this thread in the epilogues
+    float* bias = reinterpret_cast<float*>(smem + kPpBias);  // b1 @0, b2 @16, b3 @48, c1 @80, f2 @144, c2 @208
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kPpBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kPpBar + kPpNBar * 8);
+    uint8_t* X1 = smem + kPpX1;
+    const uint32_t sbase = ptx::smem_u32(smem);
+
+    // ---- once: weights, biases, zeroed activation buffers, barriers, TMEM
+    for (int e = tid; e < 16 * 4; e += kPpThreads) {  // W1: 16 rows x 4 entries
+        const int n = e >> 2, j = e & 3;
+        uint32_t w[4];
+        // conv1's bias in the K slots 6 and 7 of the first filter row, as two BF16
+        // parts whose sum is the fp32 bias to 16 significant bits; X1 carries 1.0 there
+        const float b1 = a.master[kB1 + n];
+        const __nv_bfloat16 bhi = __float2bfloat16_rn(b1);
+        const __nv_bfloat16 blo = __float2bfloat16_rn(b1 - __bfloat162float(bhi));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint16_t h[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int k = 8 * j + 2 * q + s, dy = k >> 3, rem = k & 7, dx = rem >> 1, c = rem & 1;
+                h[s] = (dy < 3 && rem < 6) ? __bfloat16_as_ushort(a.w1b[n * 32 + (dy * 3 + dx) * 2 + c])
+                       : k == 6           ? __bfloat16_as_ushort(bhi)
+                       : k == 7           ? __bfloat16_as_ushort(blo)
+                                          : 0;
+            }
+            w[q] = static_cast<uint32_t>(h[0]) | (static_cast<uint32_t>(h[1]) << 16);
+        }
+        *reinterpret_cast<uint4*>(smem + kPpW1 + tc::core_offset(n, 8 * j, 32)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    for (int e = tid; e < 9 * 32 * 2; e += kPpThreads) {  // W2: tap x 32 rows x 2 entries
+        const int t = e / 64, n = (e >> 1) & 31, j = e & 1;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w2b + n * 144 + t * 16 + 8 * j));
+        *reinterpret_cast<uint4*>(smem + kPpW2 + t * 1024 + tc::core_offset(n, 8 * j, 16)) = v;
+    }
+    for (int e = tid; e < 9 * 32 * 4; e += kPpThreads) {  // W3: tap x 32 rows x 4 entries
+        const int t = e / 128, n = (e >> 2) & 31, j = e & 3;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w3b + n * 288 + t * 32 + 8 * j));
+        *reinterpret_cast<uint4*>(smem + kPpW3 + t * 2048 + tc::core_offset(n, 8 * j, 32)) = v;
+    }
+    if (tid < 16) bias[tid] = a.master[kB1 + tid];
+    if (tid < 32) {
+        bias[16 + tid] = a.master[kB2 + tid];
+        bias[48 + tid] = a.master[kB3 + tid];
+    }
+    if (tid < 64) {
+        bias[80 + tid] = a.master[kC1 + tid];
+        bias[144 + tid] = __bfloat162float(a.f2b[tid]);
+    }
+    if (tid == 0) bias[208] = a.master[kC2];
+    for (int e = tid; e < 32 * 64; e += kPpThreads) reinterpret_cast<float*>(smem + kPpF1)[e] = a.f1t[e];
+    // X1: every entry 0 with 1.0 in the two bias slots (the padding rows keep it: the
+    // build writes the image rows only); both A1 and both A2 buffers zero (the
+    // epilogues write the live entries only)
+    for (int e = tid; e < kFzReg0Bytes / 16; e += kPpThreads)
+        reinterpret_cast<uint4*>(X1)[e] = make_uint4(0, 0, 0, kPpOnes);
+    for (int e = tid; e < (kPpPart - kPpA1) / 16; e += kPpThreads)
+        reinterpret_cast<uint4*>(smem + kPpA1)[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int i = 0; i < kPpNBar; ++i) {
+            uint32_t cnt = 1;  // tcgen05.commit of one issuer
+            if (i == kBX1Full || i == kBA1Full || i == kBA1Full + 1 || i == kBA2Full || i == kBA2Full + 1)
+                cnt = 128;  // every thread of the writing group
+            else if (i == kBX1Free || i == kBA1Free || i == kBA1Free + 1 || i == kBT1Free || i == kBT1Free + 1)
+                cnt = 4;  // the four conv1 (X1) or conv2 (A1) issuers, or group 1's four readers
+            ptx::mbar_init(bar + i, cnt);
+        }
+        ptx::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, kPpTmemCols);
+    fz_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t tlane = static_cast<uint32_t>(32 * quad) << 16;
+    bool ok = true;
+
+    const int64_t npairs = a.d_pairs ? min(static_cast<int64_t>(max(*a.d_pairs, 0)), a.pairs) : a.pairs;
+    const int64_t nbatch = (npairs + kFzPairs - 1) / kFzPairs;
+    // batches of this CTA: blockIdx.x + j * gridDim.x, j < nb
+    const int nb = blockIdx.x < nbatch ? static_cast<int>((nbatch - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+
+    if (grp == 0) {
+        // ---- group 0: X1 of batch j (warp w builds input rows w, w + 4, ...: lane = output
+        //      column, one 512-byte plane row per store)
+        constexpr int kRows = kFzPairs * 36 / 4;
+        const int64_t b0 = blockIdx.x;
+        int64_t ip0 = 0, ic0 = 0, ip1 = 0, ic1 = 0;
+        auto pair_thumbs = [&](int64_t batch, int p, int64_t& ip, int64_t& ic) {
+            int64_t b = batch * kFzPairs + p;
+            if (b >= npairs) b = npairs - 1;
+            ip = a.prev ? a.prev[b] : b;
+            ic = a.cur ? a.cur[b] : b + 1;
+        };
+        if (nb > 0) {
+            pair_thumbs(b0, 0, ip0, ic0);
+            pair_thumbs(b0, 1, ip1, ic1);
+        }
+        for (int j = 0; j < nb; ++j) {
+            const int64_t batch = b0 + static_cast<int64_t>(j) * gridDim.x;
+            uint32_t vps[kRows], vqs[kRows];
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {  // every load in flight before the first store
+                const int task = warp + 4 * q, p = task / 36, iy = task - 36 * p;
+                const int64_t ip = p ? ip1 : ip0, ic = p ? ic1 : ic0;
+                vps[q] = __ldg(reinterpret_cast<const uint16_t*>(a.thumbs + ip * 2304 + iy * 64) + lane);
+                vqs[q] = __ldg(reinterpret_cast<const uint16_t*>(a.thumbs + ic * 2304 + iy * 64) + lane);
+            }
+            if (j + 1 < nb) {  // the next batch's thumbnail indices
+                pair_thumbs(batch + gridDim.x, 0, ip0, ic0);
+                pair_thumbs(batch + gridDim.x, 1, ip1, ic1);
+            }
+            // X1 is free once the conv1 MMAs of batch j-1 have completed
+            if (j > 0) ok = pp_wait1(&bar[kBX1Free], (j - 1) & 1, ok, a.status);
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                const int task = warp + 4 * q, p = task / 36, iy = task - 36 * p;
+                const uint32_t vp = vps[q], vq = vqs[q];
+                const uint32_t up = __shfl_up_sync(0xffffffffu, vp, 1), uq = __shfl_up_sync(0xffffffffu, vq, 1);
+                const uint32_t w[8] = {vp, vq, up, uq, 0, 0, 0, 0};
+                const uint32_t w0 = lane ? bf16x2(thumb_at<9>(w), thumb_at<13>(w)) : 0u;  // column -1 is padding
+                const uint32_t w1 = bf16x2(thumb_at<0>(w), thumb_at<4>(w));
+                const uint32_t w2 = bf16x2(thumb_at<1>(w), thumb_at<5>(w));
+                uint8_t* row = (iy & 1) ? X1 + (p * kFzR1 + ((iy + 1) >> 1)) * 512
+                                        : X1 + kFzX1Plane + (p * kFzR1 + (iy >> 1)) * 512;
+                *reinterpret_cast<uint4*>(row + lane * 16) = make_uint4(w0, w1, w2, kPpOnes);
+            }
+            tc::fence_proxy_async();
+            ptx::mbar_arrive(&bar[kBX1Full]);
+            // conv1 of batch j into TMEM buffer j & 1: lane 0 of warp w issues tiles w, w + 4,
+            // w + 8 once every builder is done and group 1 has read the buffer (batch j-2)
+            if (lane == 0) {
+                const int cb = j & 1;
+                ok = pp_wait1(&bar[kBX1Full], j & 1, ok, a.status);
+                if (j >= 2) ok = pp_wait1(&bar[kBT1Free + cb], ((j >> 1) + 1) & 1, ok, a.status);
+                tc::fence_after_sync();
+                constexpr uint32_t idesc = tc::idesc_bf16(128, 16);
+                for (int t = warp; t < kFzT1; t += 4) {
+                    const uint32_t g0 = static_cast<uint32_t>(min(16 * t, kFzG1 - 16));
+                    const uint32_t acc = tmem + kPpT1 + 16 * (kFzT1 * cb + t);
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+                        tc::mma(acc, tc::smem_desc(sbase + kPpX1 + 512 * k + g0 * 128, kFzX1Plane, 128),
+                                tc::smem_desc(sbase + kPpW1 + 256 * k, 128, 512), idesc, k ? 1u : 0u);
+                    tc::commit(&bar[kBT1Full + kFzT1 * cb + t]);
+                }
+                tc::commit(&bar[kBX1Free]);
+            }
+            __syncwarp();
+        }
+    } else if (grp == 1) {
+        // ---- group 1: conv1 epilogue of batch j (ReLU, BF16; the bias is in the
+        //      accumulator) into A1[j & 1], four tiles (64 columns) per TMEM load
+        for (int j = 0; j < nb; ++j) {
+            const int b = j & 1;
+            uint8_t* E2 = smem + kPpA1 + b * kFzReg1Bytes;
+            uint8_t* O2 = E2 + 2 * kFzE2Plane;
+            // A1[b] is free once the conv2 MMAs of batch j-2 have completed
+            if (j >= 2) ok = pp_wait1(&bar[kBA1Free + b], ((j >> 1) + 1) & 1, ok, a.status);
+            const uint32_t t1 = tmem + tlane + kPpT1 + 16 * kFzT1 * b;  // the batch's conv1 accumulators
+            for (int t0 = 0; t0 < kFzT1; t0 += 4) {
+                const int nt = min(4, kFzT1 - t0);
+                for (int u = 0; u < nt; ++u)
+                    ok = pp_wait1(&bar[kBT1Full + kFzT1 * b + t0 + u], (j >> 1) & 1, ok, a.status);
+                __syncwarp();
+                tc::fence_after_sync();
+                uint32_t accs[64];
+                if (nt == 4) {
+                    tc::ld64(t1 + 16 * t0, accs);
+                } else {
+                    tc::ld32(t1 + 16 * t0, *reinterpret_cast<uint32_t(*)[32]>(accs));
+                }
+                tc::wait_ld();
+                if (t0 + nt == kFzT1) {  // the batch's conv1 accumulators are read
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&bar[kBT1Free + b]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (u >= nt) break;
+                    const int t = t0 + u;
+                    const uint32_t* acc = accs + 16 * u;
+                    const int g0 = min(16 * t, kFzG1 - 16);
+                    const int g = g0 + (r >> 3);
+                    const int p = g / (kFzR1 * 4), rem = g - p * (kFzR1 * 4), oy = rem >> 2;
+                    if (g >= 16 * t && oy < 18) {
+                        const int ox = 8 * (rem & 3) + (r & 7);
+                        uint32_t o[8];
+#pragma unroll
+                        for (int c = 0; c < 16; c += 2)
+                            o[c / 2] = relu_pack(__uint_as_float(acc[c]), __uint_as_float(acc[c + 1]));
+                        const int row = p * kFzR2 + oy + 1;
+                        uint8_t* dst = (ox & 1) ? O2 + row * kFzO2Pitch + ((ox + 1) >> 1) * 16
+                                                : E2 + row * kFzE2Pitch + (ox >> 1) * 16;
+                        const int cs = (ox & 1) ? kFzO2Plane : kFzE2Plane;
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(o[0], o[1], o[2], o[3]);
+                        *reinterpret_cast<uint4*>(dst + cs) = make_uint4(o[4], o[5], o[6], o[7]);
+                    }
+                }
+            }
+            tc::fence_proxy_async();
+            ptx::mbar_arrive(&bar[kBA1Full + b]);
+        }
+    } else if (grp == 2) {
+        // ---- group 2: conv2 of batch j (lane 0 of warp 8 + q issues tile q, all 9 taps),
+        //      then its epilogue (bias, ReLU, BF16) into A2[j & 1]
+        float b2[32];  // in registers: a broadcast 16-byte shared load costs four wavefronts
+#pragma unroll
+        for (int c = 0; c < 32; ++c) b2[c] = bias[16 + c];
+        for (int j = 0; j < nb; ++j) {
+            const int b = j & 1;
+            if (j > 0) {  // every warp of the group has read batch j-1's conv2 accumulators
+                tc::fence_before_sync();
+                pp_group_sync(2);
+                tc::fence_after_sync();
+            }
+            if (lane == 0) {
+                ok = pp_wait1(&bar[kBA1Full + b], (j >> 1) & 1, ok, a.status);
+                tc::fence_after_sync();
+                constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
+                // tile quad: column half h, first group g0; tap (dy, dx) reads the even-
+                // column plane (dx = 1) or the odd one, shifted by one entry for dx = 2
+                const int h = quad >> 1, g0 = (quad & 1) ? kFzG2 - 16 : 0;
+                const uint32_t s_e2 = sbase + kPpA1 + b * kFzReg1Bytes, s_o2 = s_e2 + 2 * kFzE2Plane;
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+                    const uint32_t rp = dx == 1 ? kFzE2Pitch : kFzO2Pitch;
+                    const uint32_t cs = dx == 1 ? kFzE2Plane : kFzO2Plane;
+                    const uint32_t ad = (dx == 1 ? s_e2 : s_o2) + (2 * g0 + dy) * rp + (8 * h + (dx == 2 ? 1 : 0)) * 16;
+                    tc::mma(tmem + kPpT2 + 32 * quad, tc::smem_desc(ad, cs, 2 * rp),
+                            tc::smem_desc(sbase + kPpW2 + tap * 1024, 128, 256), idesc, tap > 0 ? 1u : 0u);
+                }
+                tc::commit(&bar[kBT2Full + quad]);
+                tc::commit(&bar[kBA1Free + b]);
+            }
+            __syncwarp();
+            uint8_t* E3 = smem + kPpA2 + b * kPpA2Bytes;
+            uint8_t* O3 = E3 + 4 * kFzE3Plane;
+            if (j >= 2) ok = pp_wait1(&bar[kBA2Free + b], ((j >> 1) + 1) & 1, ok, a.status);
+            for (int tt = 0; tt < 4; ++tt) {
+                ok = pp_wait1(&bar[kBT2Full + tt], j & 1, ok, a.status);
+                __syncwarp();
+                tc::fence_after_sync();
+                const int h = tt >> 1, first = (tt & 1) ? 16 : 0, g0 = (tt & 1) ? kFzG2 - 16 : 0;
+                const int g = g0 + (r >> 3), p = g / 10, oy = g - 10 * p;
+                const bool live = g >= first && oy < 9;
+                const int ox = 8 * h + (r & 7);
+                const int row = p * kFzR3 + oy + 1;
+                uint8_t* dst = (ox & 1) ? O3 + row * kFzO3Pitch + ((ox + 1) >> 1) * 16
+                                        : E3 + row * kFzE3Pitch + (ox >> 1) * 16;
+                const int cs = (ox & 1) ? kFzO3Plane : kFzE3Plane;
+                uint32_t us[32];
+                tc::ld32(tmem + tlane + kPpT2 + 32 * tt, us);
+                tc::wait_ld();
+#pragma unroll
+                for (int c0 = 0; c0 < 32; c0 += 16) {
+                    const uint32_t* u0 = us + c0;
+                    if (live) {
+                        uint32_t o[8];
+#pragma unroll
+                        for (int c = 0; c < 16; c += 2)
+                            o[c / 2] = relu_pack(__uint_as_float(u0[c]) + b2[c0 + c],
+                                                 __uint_as_float(u0[c + 1]) + b2[c0 + c + 1]);
+                        const int q = c0 / 8;
+                        *reinterpret_cast<uint4*>(dst + q * cs) = make_uint4(o[0], o[1], o[2], o[3]);
+                        *reinterpret_cast<uint4*>(dst + (q + 1) * cs) = make_uint4(o[4], o[5], o[6], o[7]);
+                    }
+                }
+            }
+            tc::fence_proxy_async();
+            ptx::mbar_arrive(&bar[kBA2Full + b]);
+        }
+    } else {
+        // ---- group 3: conv3 of batch j, its epilogue (bias, ReLU, BF16 rounding), each
+        //      output row's 8 positions summed by shuffles into part[j & 1], and the head
+        //      (warp 12 + p: pair p's logit: mean, FC1, ReLU, FC2).  Warp 15 (its lanes hold
+        //      dropped rows only) issues conv3 (both K halves, one accumulator each): batch
+        //      j + 1's as soon as the group has read batch j's accumulators, so that the MMAs
+        //      run while the other three warps pool and compute the head of batch j.
+        auto issue_conv3 = [&](int jj) {  // lane 0 of warp 15
+            const int bb = jj & 1;
+            ok = pp_wait1(&bar[kBA2Full + bb], (jj >> 1) & 1, ok, a.status);
+            tc::fence_after_sync();
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
+            const uint32_t s_e3 = sbase + kPpA2 + bb * kPpA2Bytes, s_o3 = s_e3 + 4 * kFzE3Plane;
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap % 3;
+                const uint32_t rp = dx == 1 ? kFzE3Pitch : kFzO3Pitch;
+                const uint32_t cs = dx == 1 ? kFzE3Plane : kFzO3Plane;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const uint32_t ad = (dx == 1 ? s_e3 : s_o3) + 2 * kk * cs + dy * rp + (dx == 2 ? 16 : 0);
+                    tc::mma(tmem + kPpT3 + 32 * kk, tc::smem_desc(ad, cs, 2 * rp),
+                            tc::smem_desc(sbase + kPpW3 + tap * 2048 + kk * 256, 128, 512), idesc, tap > 0 ? 1u : 0u);
+                }
+            }
+            tc::commit(&bar[kBT3Full]);
+            tc::commit(&bar[kBA2Free + bb]);
+        };
+        float b3r[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) b3r[c] = bias[48 + c];
+        const float c1a = bias[80 + lane], c1b = bias[80 + 32 + lane];
+        const float f2a = bias[144 + lane], f2b = bias[144 + 32 + lane], c2 = bias[208];
+        if (quad == 3 && lane == 0 && nb > 0) issue_conv3(0);
+        __syncwarp();
+        for (int j = 0; j < nb; ++j) {
+            const int b = j & 1;
+            float* part = reinterpret_cast<float*>(smem + kPpPart) + b * (kFzPairs * 5 * 32);
+            ok = pp_wait1(&bar[kBT3Full], j & 1, ok, a.status);
+            __syncwarp();
+            tc::fence_after_sync();
+            uint32_t acc2[64];  // the two accumulators (K halves), 32 channels each
+            tc::ld64(tmem + tlane + kPpT3, acc2);
+            tc::wait_ld();
+            tc::fence_before_sync();
+            pp_group_sync(1);  // every warp has read batch j's conv3 accumulators
+            tc::fence_after_sync();
+            if (quad == 3) {
+                if (lane == 0 && j + 1 < nb) issue_conv3(j + 1);
+                __syncwarp();
+                continue;
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t acc[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    acc[c] = __float_as_uint(__uint_as_float(acc2[16 * half + c]) + __uint_as_float(acc2[32 + 16 * half + c]));
+                const int g = r >> 3;
+                float v[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    v[c] = g < kFzG3 ? __bfloat162float(__float2bfloat16_rn(
+                                           fmaxf(__uint_as_float(acc[c]) + b3r[16 * half + c], 0.f)))
+                                     : 0.f;
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+                if (g < kFzG3 && (lane & 7) == 0) {
+                    const int p = g / 5, oy = g - 5 * p;
+                    float4* dst = reinterpret_cast<float4*>(part + (p * 5 + oy) * 32 + 16 * half);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+            pp_group_sync96(3);  // part[b] complete (warps 12-14; part[b] of batch j-2 no longer read)
+            if (quad < kFzPairs) {
+                const int p = quad;
+                const float* q = part + p * 160 + lane;
+                const float gl = (q[0] + q[32] + q[64] + q[96] + q[128]) * (1.f / 40.f);
+                const float* f1 = reinterpret_cast<const float*>(smem + kPpF1);
+                float v0 = c1a, v1 = c1b;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const float gc = __shfl_sync(0xffffffffu, gl, c);
+                    v0 = fmaf(f1[c * 64 + lane], gc, v0);
+                    v1 = fmaf(f1[c * 64 + 32 + lane], gc, v1);
+                }
+                float z0 = f2a * fmaxf(v0, 0.f), z1 = f2b * fmaxf(v1, 0.f);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    z0 += __shfl_xor_sync(0xffffffffu, z0, o);
+                    z1 += __shfl_xor_sync(0xffffffffu, z1, o);
+                }
+                const int64_t pb = (static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(j) * gridDim.x) * kFzPairs + p;
+                if (lane == 0 && pb < npairs) a.logits[a.out_index ? a.out_index[pb] : pb] = z0 + z1 + c2;
+            }
+        }
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, kPpTmemCols);
+}
+
 scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* prev, const int32_t* cur, int64_t pairs,
                                 float* logits, cudaStream_t st, const int* d_pairs = nullptr,
                                 const int32_t* out_index = nullptr) {
     static std::atomic<uint64_t> attr_done{0};
     const scn_status sa = once_per_device(attr_done, [] {
-        SCN_CUDA_TRY(cudaFuncSetAttribute(cnn_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFzSmem));
-        SCN_CUDA_TRY(cudaFuncSetAttribute(cnn_forward_fused, cudaFuncAttributePreferredSharedMemoryCarveout,
+        SCN_CUDA_TRY(cudaFuncSetAttribute(cnn_forward_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, kPpSmem));
+        SCN_CUDA_TRY(cudaFuncSetAttribute(cnn_forward_pipe, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           cudaSharedmemCarveoutMaxShared));
         return SCN_OK;
     });
@@ -889,8 +1356,8 @@ scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* pr
     const int64_t nbatch = (pairs + kFzPairs - 1) / kFzPairs;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
-    const int grid = static_cast<int>(std::min<int64_t>(nbatch, static_cast<int64_t>(sms) * 2));
-    cnn_forward_fused<<<grid, kFzThreads, kFzSmem, st>>>(a);
+    const int grid = static_cast<int>(std::min<int64_t>(nbatch, static_cast<int64_t>(sms)));
+    cnn_forward_pipe<<<grid, kPpThreads, kPpSmem, st>>>(a);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }
