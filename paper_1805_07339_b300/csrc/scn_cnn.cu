@@ -123,14 +123,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return static_cast<uint32_t>(__bfloat16_as_ushort(a)) | (static_cast<uint32_t>(__bfloat16_as_ushort(b)) << 16);
 }
 
-// BF16 pair (lo, hi) of relu(lo), relu(hi): one paired conversion, then the ReLU on
-// the packed pair; rounding keeps the sign, so this equals rounding relu(x)
-__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    v = __hmax2(v, __float2bfloat162_rn(0.f));
-    return *reinterpret_cast<const uint32_t*>(&v);
-}
-
 // 8 consecutive im2col values (columns 8j..8j+7) of output row (pair b, position pos)
 template <int L>
 __device__ __forceinline__ uint4 im2col_chunk(const ConvFwdArgs& a, int64_t b, int pos, int j) {
@@ -370,10 +362,10 @@ scn_status forward_chunk(Net* n, const uint8_t* thumbs, const int32_t* prev, con
 }
 
 // ---------------------------------------------------------------------------
-// fused forward (inference): the whole network in one persistent kernel
+// fused forward (inference): per-batch activation layouts in shared memory
 // ---------------------------------------------------------------------------
-// A CTA takes kFzPairs pairs at a time and keeps every activation in shared
-// memory.  Each convolution is an implicit GEMM whose A operand the tensor core
+// The inference kernel below takes kFzPairs pairs (a batch) at a time and keeps
+// every activation in shared memory.  Each convolution is an implicit GEMM whose A operand the tensor core
 // reads straight out of the activation buffer, one filter tap per MMA (no
 // im2col copy): the buffers are laid out so that, for a fixed tap, the 8-row
 // core matrices of the output positions sit at one constant stride.  Stride 2
@@ -387,8 +379,7 @@ scn_status forward_chunk(Net* n, const uint8_t* thumbs, const int32_t* prev, con
 // so that consecutive groups are consecutive output rows (layer 1: 4 groups per
 // row); the last tile of a layer starts at G - 16 and keeps only the groups it
 // adds, and group slots past a pair's last output row are computed and dropped.
-constexpr int kFzPairs = 2;  // the zero-row lists of phases 0 and 2 are written for two pairs
-constexpr int kFzThreads = 256;
+constexpr int kFzPairs = 2;
 // layer 1 input X1: planes O1 (odd input rows; row 0 of a pair = zero padding
 // above the image) and E1 (even input rows; row 18 of a pair = zeros); a plane
 // row holds the 32 output columns ox, entry ox = [prev, cur] at input columns
@@ -410,43 +401,23 @@ constexpr int kFzG2 = kFzPairs * 10;  // groups per column half (9 output rows +
 // layer 3 input A2 (a2, 32 channels = 4 chunks): even plane 8 entries, odd plane
 // 9 entries; row 0 of each pair and row kFzPairs*10 = zero padding (row 10 of a
 // pair is row 0 of the next).  Dropped groups read past a plane into the next
-// one or into the head's scratch that follows; every such read stays in region 0.
+// one or past the last one; every such read stays inside the A2 buffer (kFzF1T).
 constexpr int kFzR3 = 10;
 constexpr int kFzA2Rows = kFzPairs * kFzR3 + 1;
 constexpr int kFzE3Pitch = 8 * 16, kFzO3Pitch = 9 * 16;
 constexpr int kFzE3Plane = kFzA2Rows * kFzE3Pitch, kFzO3Plane = kFzA2Rows * kFzO3Pitch;
 constexpr int kFzA2Bytes = 4 * (kFzE3Plane + kFzO3Plane);
 constexpr int kFzG3 = kFzPairs * 5;
-constexpr int kFzF1T = 24576;  // end of what layer-3 reads of region 0
-// MMA descriptor table: conv1 2 per tile, conv2 9 per tile, conv3 18
-constexpr int kFzD1 = 0, kFzD2 = kFzD1 + 2 * kFzT1, kFzD3 = kFzD2 + 4 * 9, kFzNDesc = kFzD3 + 18;
-// shared-memory map (bytes)
-constexpr int kFzW1 = 0;                           // [16][32]  core layout, k = dy*8 + dx*2 + c
-constexpr int kFzW2 = kFzW1 + 16 * 32 * 2;         // 9 x [32][16]
-constexpr int kFzW3 = kFzW2 + 9 * 32 * 16 * 2;     // 9 x [32][32]
-constexpr int kFzBias = kFzW3 + 9 * 32 * 32 * 2;   // floats: b1 16, b2 32, b3 32, c1 64, f2 64, c2 1
-constexpr int kFzDesc = kFzBias + 1024;            // kFzNDesc x (A, B) descriptors
-constexpr int kFzBar = kFzDesc + kFzNDesc * 16;    // mbarriers, TMEM address
-constexpr int kFzNBar = kFzT1 + 8 + 3;  // conv1 tiles, conv2 tile x tap range, conv3 tap range
-constexpr int kFzReg0 = kFzBar + 256;              // X1, later a2 + head scratch
-constexpr int kFzReg0Bytes = 2 * kFzX1Plane;
-constexpr int kFzReg1 = kFzReg0 + kFzReg0Bytes;    // A1
-constexpr int kFzReg1Bytes = 2 * kFzE2Plane + 2 * kFzO2Plane;
-// head scratch, outside the activation regions so that the head of a batch runs
-// during the next batch's phases 0-2: per pair the 5 row sums of a3 (fp32 [5][32];
-// row 0 later holds the pooled g), then the FC2 partial sum of each of 4 warps
-constexpr int kFzPart = kFzReg1 + kFzReg1Bytes;
-constexpr int kFzWsum = kFzPart + kFzPairs * 5 * 32 * 4;
-constexpr int kFzSmem = kFzWsum + 4 * 4;
-static_assert(kFzNBar * 8 + 4 <= 256, "barrier area");
-static_assert(kFzSmem <= 115712, "two CTAs per SM");
+constexpr int kFzF1T = 24576;  // end of what layer 3's dropped groups read of the A2 buffer
+constexpr int kFzReg0Bytes = 2 * kFzX1Plane;                    // X1
+constexpr int kFzReg1Bytes = 2 * kFzE2Plane + 2 * kFzO2Plane;   // A1
 static_assert(kFzG1 >= 16 && kFzG2 >= 16, "every layer-1/2 tile lies inside the buffers");
-// every row the MMAs read lies inside its plane (layers 1, 2) or inside region 0 (layer 3)
+// every row the MMAs read lies inside its plane (layers 1, 2) or inside the A2 buffer (layer 3)
 static_assert((kFzG1 - 1) / 4 + 1 < kFzX1Rows, "layer-1 reads");
 static_assert(2 * (kFzG2 - 1) + 2 < kFzA1Rows, "layer-2 reads");
 static_assert(4 * kFzE3Plane + 3 * kFzO3Plane + (2 * 15 + 2 + 1) * kFzO3Pitch <= kFzF1T, "layer-3 reads");
-static_assert(kFzA2Bytes <= kFzF1T && kFzF1T <= kFzReg0Bytes, "region 0 in phases 2-3");
-static_assert(kFzPairs == 2, "the head's warp split (warp w: pair w / 2, units 32 (w % 2) ..) assumes two pairs");
+static_assert(kFzA2Bytes <= kFzF1T, "A2 buffer");
+static_assert(kFzPairs == 2, "the head's warp split (warp 12 + p: pair p) and the zero-row layout assume two pairs");
 
 struct FusedArgs {
     const uint8_t* thumbs;
@@ -480,16 +451,6 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ bool fz_wait(uint64_t* bar, uint32_t par, bool ok, int* status) {
-    if (ok && !ptx::mbar_wait_bounded(bar, par, kWaitNs)) {
-        atomicOr(status, kStatusTimeout);
-        ok = false;
-    }
-    __syncwarp();
-    tc::fence_after_sync();
-    return ok;
-}
-
 __device__ __forceinline__ void fz_sync() {
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -497,395 +458,30 @@ __device__ __forceinline__ void fz_sync() {
     tc::fence_after_sync();
 }
 
-__global__ void __launch_bounds__(kFzThreads, 2) cnn_forward_fused(const __grid_constant__ FusedArgs a) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, half = warp >> 2;
-    const int r = 32 * quad + lane;  // TMEM lane = tile row of this thread in epilogues
-    float* bias = reinterpret_cast<float*>(smem + kFzBias);  // b1 @0, b2 @16, b3 @48, c1 @80, f2 @144, c2 @208
-    uint64_t* desc = reinterpret_cast<uint64_t*>(smem + kFzDesc);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kFzBar);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kFzBar + kFzNBar * 8);
-    uint8_t* reg0 = smem + kFzReg0;
-    uint8_t* reg1 = smem + kFzReg1;
-    uint8_t* O1 = reg0;
-    uint8_t* E1 = reg0 + kFzX1Plane;
-    uint8_t* E3 = reg0;
-    uint8_t* O3 = reg0 + 4 * kFzE3Plane;
-    float* part = reinterpret_cast<float*>(smem + kFzPart);  // [pair][5][32]; [pair][0][c] = g after step A
-    float* wsum = reinterpret_cast<float*>(smem + kFzWsum);  // [4]
-    uint8_t* E2 = reg1;
-    uint8_t* O2 = reg1 + 2 * kFzE2Plane;
-    const uint32_t sbase = ptx::smem_u32(smem);
-
-    // ---- once: weights in tensor-core layouts, biases, descriptors, zeroed A1, barriers, TMEM
-    for (int e = tid; e < 16 * 4; e += kFzThreads) {  // W1: 16 rows x 4 entries
-        const int n = e >> 2, j = e & 3;
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint16_t h[2];
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int k = 8 * j + 2 * q + s, dy = k >> 3, rem = k & 7, dx = rem >> 1, c = rem & 1;
-                h[s] = (dy < 3 && rem < 6) ? __bfloat16_as_ushort(a.w1b[n * 32 + (dy * 3 + dx) * 2 + c]) : 0;
-            }
-            w[q] = static_cast<uint32_t>(h[0]) | (static_cast<uint32_t>(h[1]) << 16);
-        }
-        *reinterpret_cast<uint4*>(smem + kFzW1 + tc::core_offset(n, 8 * j, 32)) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    for (int e = tid; e < 9 * 32 * 2; e += kFzThreads) {  // W2: tap x 32 rows x 2 entries
-        const int t = e / 64, n = (e >> 1) & 31, j = e & 1;
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w2b + n * 144 + t * 16 + 8 * j));
-        *reinterpret_cast<uint4*>(smem + kFzW2 + t * 1024 + tc::core_offset(n, 8 * j, 16)) = v;
-    }
-    for (int e = tid; e < 9 * 32 * 4; e += kFzThreads) {  // W3: tap x 32 rows x 4 entries
-        const int t = e / 128, n = (e >> 2) & 31, j = e & 3;
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w3b + n * 288 + t * 32 + 8 * j));
-        *reinterpret_cast<uint4*>(smem + kFzW3 + t * 2048 + tc::core_offset(n, 8 * j, 32)) = v;
-    }
-    if (tid < 16) bias[tid] = a.master[kB1 + tid];
-    if (tid < 32) {
-        bias[16 + tid] = a.master[kB2 + tid];
-        bias[48 + tid] = a.master[kB3 + tid];
-    }
-    if (tid < 64) {
-        bias[80 + tid] = a.master[kC1 + tid];
-        bias[144 + tid] = __bfloat162float(a.f2b[tid]);
-    }
-    if (tid == 0) bias[208] = a.master[kC2];
-    if (tid < kFzNDesc) {
-        // the operand addresses are the same for every batch
-        uint64_t ad, bd;
-        const int i = tid;
-        const uint32_t s_o1 = sbase + kFzReg0, s_e2 = sbase + kFzReg1, s_o2 = s_e2 + 2 * kFzE2Plane;
-        const uint32_t s_e3 = sbase + kFzReg0, s_o3 = s_e3 + 4 * kFzE3Plane;
-        if (i < kFzD2) {  // conv1: tile t, K half k
-            const int t = i >> 1, k = i & 1, g0 = min(16 * t, kFzG1 - 16);
-            ad = tc::smem_desc(s_o1 + 512 * k + g0 * 128, kFzX1Plane, 128);
-            bd = tc::smem_desc(sbase + kFzW1 + 256 * k, 128, 512);
-        } else if (i < kFzD3) {  // conv2: tile tt (column half h, first group g0), tap
-            const int tt = (i - kFzD2) / 9, tap = (i - kFzD2) % 9, dy = tap / 3, dx = tap % 3;
-            const int h = tt >> 1, g0 = (tt & 1) ? kFzG2 - 16 : 0;
-            const uint32_t plane = dx == 1 ? s_e2 : s_o2;
-            const uint32_t rp = dx == 1 ? kFzE2Pitch : kFzO2Pitch;
-            const uint32_t cs = dx == 1 ? kFzE2Plane : kFzO2Plane;
-            ad = tc::smem_desc(plane + (2 * g0 + dy) * rp + (8 * h + (dx == 2 ? 1 : 0)) * 16, cs, 2 * rp);
-            bd = tc::smem_desc(sbase + kFzW2 + tap * 1024, 128, 256);
-        } else {  // conv3: tap, K half kk
-            const int j = i - kFzD3, tap = j >> 1, kk = j & 1, dy = tap / 3, dx = tap % 3;
-            const uint32_t plane = dx == 1 ? s_e3 : s_o3;
-            const uint32_t rp = dx == 1 ? kFzE3Pitch : kFzO3Pitch;
-            const uint32_t cs = dx == 1 ? kFzE3Plane : kFzO3Plane;
-            ad = tc::smem_desc(plane + 2 * kk * cs + dy * rp + (dx == 2 ? 16 : 0), cs, 2 * rp);
-            bd = tc::smem_desc(sbase + kFzW3 + tap * 2048 + kk * 256, 128, 512);
-        }
-        desc[2 * i] = ad;
-        desc[2 * i + 1] = bd;
-    }
-    for (int e = tid; e < kFzReg1Bytes / 16; e += kFzThreads)
-        reinterpret_cast<uint4*>(reg1)[e] = make_uint4(0, 0, 0, 0);
-    if (tid == 0) {
-        for (int i = 0; i < kFzNBar; ++i) ptx::mbar_init(bar + i, 1);
-        ptx::fence_mbar_init();
-    }
-    if (warp == 0) tc::tmem_alloc(tslot, 256);
-    fz_sync();
-    const uint32_t tmem = *tslot;
-    const uint32_t tlane = static_cast<uint32_t>(32 * quad) << 16;
-    bool ok = true;
-
-    // thumbnail indices of the batch's two pairs (every thread keeps them; fetched a batch ahead)
-    const int64_t npairs = a.d_pairs ? min(static_cast<int64_t>(max(*a.d_pairs, 0)), a.pairs) : a.pairs;
-    const int64_t nbatch = (npairs + kFzPairs - 1) / kFzPairs;
-    auto pair_thumbs = [&](int64_t batch, int p, int64_t& ip, int64_t& ic) {
-        int64_t b = batch * kFzPairs + p;
-        if (b >= npairs) b = npairs - 1;
-        ip = a.prev ? a.prev[b] : b;
-        ic = a.cur ? a.cur[b] : b + 1;
-    };
-    int64_t ip0 = 0, ic0 = 0, ip1 = 0, ic1 = 0;
-    if (blockIdx.x < nbatch) {
-        pair_thumbs(blockIdx.x, 0, ip0, ic0);
-        pair_thumbs(blockIdx.x, 1, ip1, ic1);
-    }
-    // The head of a batch runs in three steps during the next batch's phases 0, 1 and 2
-    // (after the last batch, on its own): A pools a3 from its row sums (64 threads), B
-    // computes FC1 and each warp's share of FC2 (128 threads), C adds the shares.
-    auto head_a = [&]() {
-        if (tid < kFzPairs * 32) {
-            float* q = part + (tid >> 5) * 160 + (tid & 31);
-            q[0] = (q[0] + q[32] + q[64] + q[96] + q[128]) * (1.f / 40.f);
-        }
-    };
-    auto head_b = [&]() {
-        if (tid < kFzPairs * 64) {
-            const int p = tid >> 6, j = tid & 63;
-            const float* g = part + p * 160;
-            float v = bias[80 + j];
-            float f[32];  // every load in flight before the first fma
-#pragma unroll
-            for (int c = 0; c < 32; ++c) f[c] = __ldg(a.f1t + c * 64 + j);
-#pragma unroll
-            for (int c = 0; c < 32; ++c) v = fmaf(f[c], g[c], v);
-            float zz = bias[144 + j] * fmaxf(v, 0.f);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
-            if (lane == 0) wsum[warp] = zz;
-        }
-    };
-    auto head_c = [&](int64_t hb) {
-        if (tid < kFzPairs) {
-            const int64_t b = hb * kFzPairs + tid;
-            if (b < npairs) a.logits[a.out_index ? a.out_index[b] : b] = wsum[2 * tid] + wsum[2 * tid + 1] + bias[208];
-        }
-    };
-    int64_t prev = -1;  // the batch whose head is pending
-    uint32_t it = 0;
-    for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x, ++it) {
-        const uint32_t par = it & 1u;
-        // ---- phase 0: layer-1 input planes, one warp per input row of a pair (lane = output
-        //      column, so each store writes one contiguous 512-byte plane row); zero rows;
-        //      head step A of the previous batch
-        constexpr int kRowsPerWarp = kFzPairs * 36 / (kFzThreads / 32);
-        static_assert(kRowsPerWarp * (kFzThreads / 32) == kFzPairs * 36, "rows split evenly over warps");
-        uint32_t vps[kRowsPerWarp], vqs[kRowsPerWarp];
-#pragma unroll
-        for (int q = 0; q < kRowsPerWarp; ++q) {  // every load in flight before the first store
-            const int task = warp + q * (kFzThreads / 32), p = task / 36, iy = task - 36 * p;
-            const int64_t ip = p ? ip1 : ip0, ic = p ? ic1 : ic0;
-            // bytes 2 lane, 2 lane + 1 of the row; column 2 lane - 1 comes from the lane below
-            vps[q] = __ldg(reinterpret_cast<const uint16_t*>(a.thumbs + ip * 2304 + iy * 64) + lane);
-            vqs[q] = __ldg(reinterpret_cast<const uint16_t*>(a.thumbs + ic * 2304 + iy * 64) + lane);
-        }
-#pragma unroll
-        for (int q = 0; q < kRowsPerWarp; ++q) {
-            const int task = warp + q * (kFzThreads / 32), p = task / 36, iy = task - 36 * p;
-            const uint32_t vp = vps[q], vq = vqs[q];
-            const uint32_t up = __shfl_up_sync(0xffffffffu, vp, 1), uq = __shfl_up_sync(0xffffffffu, vq, 1);
-            const uint32_t w[8] = {vp, vq, up, uq, 0, 0, 0, 0};
-            // w as bytes: 0,1 = prev cols 2l, 2l+1; 4,5 = cur; 9 = prev col 2l-1; 13 = cur col 2l-1
-            const uint32_t w0 = lane ? bf16x2(thumb_at<9>(w), thumb_at<13>(w)) : 0u;  // column -1 is padding
-            const uint32_t w1 = bf16x2(thumb_at<0>(w), thumb_at<4>(w));
-            const uint32_t w2 = bf16x2(thumb_at<1>(w), thumb_at<5>(w));
-            uint8_t* row = (iy & 1) ? O1 + (p * kFzR1 + ((iy + 1) >> 1)) * 512 : E1 + (p * kFzR1 + (iy >> 1)) * 512;
-            *reinterpret_cast<uint4*>(row + lane * 16) = make_uint4(w0, w1, w2, 0u);
-        }
-        for (int z = tid; z < 6 * 32; z += kFzThreads) {  // zero rows: O1 {0, 19, 38}, E1 {18, 37, 38}
-            const int which = z >> 5, ox = z & 31;
-            const int zr = which == 0 ? 0 : which == 1 ? kFzR1 : which == 2 ? 2 * kFzR1
-                         : which == 3 ? kFzR1 - 1 : which == 4 ? 2 * kFzR1 - 1 : 2 * kFzR1;
-            *reinterpret_cast<uint4*>((which < 3 ? O1 : E1) + zr * 512 + ox * 16) = make_uint4(0, 0, 0, 0);
-        }
-        if (prev >= 0) head_a();
-        fz_sync();
-
-        // the next batch's thumbnail indices: loads in flight through phases 1-4
-        if (batch + gridDim.x < nbatch) {
-            pair_thumbs(batch + gridDim.x, 0, ip0, ic0);
-            pair_thumbs(batch + gridDim.x, 1, ip1, ic1);
-        }
-
-        // ---- phase 1: conv1, kFzT1 tiles of 128 x 16, issued by lane 0 of warp t % 8 (one
-        //      issuing thread is slower: each MMA waits for the tensor core to take it)
-        if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_bf16(128, 16);
-            for (int t = warp; t < kFzT1; t += kFzThreads / 32) {
-                tc::mma(tmem + 16 * t, desc[4 * t], desc[4 * t + 1], idesc, 0u);
-                tc::mma(tmem + 16 * t, desc[4 * t + 2], desc[4 * t + 3], idesc, 1u);
-                tc::commit(bar + t);
-            }
-        }
-        __syncwarp();
-        if (prev >= 0) head_b();  // FC1 of the previous batch while the tensor core runs conv1
-        for (int t2 = half; t2 < kFzT1; t2 += 6) {
-            // up to three tiles of this warp's parity per TMEM round trip (each tcgen05.ld
-            // round trip costs hundreds of cycles; loads in flight together share it)
-            const int nt = min(3, (kFzT1 - t2 + 1) / 2);
-            for (int u = 0; u < nt; ++u) ok = fz_wait(bar + t2 + 2 * u, par, ok, a.status);
-            uint32_t accs[3][16];
-            tc::ld16(tmem + tlane + 16 * t2, accs[0]);
-            if (nt > 1) tc::ld16(tmem + tlane + 16 * (t2 + 2), accs[1]);
-            if (nt > 2) tc::ld16(tmem + tlane + 16 * (t2 + 4), accs[2]);
-            tc::wait_ld();
-#pragma unroll
-            for (int u = 0; u < 3; ++u) {
-            if (u >= nt) break;
-            const int t = t2 + 2 * u;
-            const uint32_t (&acc)[16] = accs[u];
-            const int g0 = min(16 * t, kFzG1 - 16);
-            const int g = g0 + (r >> 3);
-            const int p = g / (kFzR1 * 4), rem = g - p * (kFzR1 * 4), oy = rem >> 2;
-            if (g >= 16 * t && oy < 18) {
-                const int ox = 8 * (rem & 3) + (r & 7);
-                uint32_t o[8];
-#pragma unroll
-                for (int c = 0; c < 16; c += 2)
-                    o[c / 2] = relu_bf16x2(__uint_as_float(acc[c]) + bias[c], __uint_as_float(acc[c + 1]) + bias[c + 1]);
-                const int row = p * kFzR2 + oy + 1;
-                uint8_t* dst = (ox & 1) ? O2 + row * kFzO2Pitch + ((ox + 1) >> 1) * 16 : E2 + row * kFzE2Pitch + (ox >> 1) * 16;
-                const int cs = (ox & 1) ? kFzO2Plane : kFzE2Plane;
-                *reinterpret_cast<uint4*>(dst) = make_uint4(o[0], o[1], o[2], o[3]);
-                *reinterpret_cast<uint4*>(dst + cs) = make_uint4(o[4], o[5], o[6], o[7]);
-            }
-            }
-        }
-        fz_sync();
-
-        // ---- phase 2: conv2, 2 column halves x 2 tiles of 128 x 32; each tile accumulates
-        //      taps 0-4 and taps 5-8 in two TMEM blocks, issued by lane 0 of 8 warps (short
-        //      chains: each MMA waits for the tensor core to take it); zero padding of A2
-        if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
-            const int tt = warp >> 1, k = warp & 1, t0 = 5 * k, t1 = k ? 9 : 5;
-            const uint64_t* d = desc + 2 * (kFzD2 + 9 * tt);
-            for (int tap = t0; tap < t1; ++tap)
-                tc::mma(tmem + 64 * tt + 32 * k, d[2 * tap], d[2 * tap + 1], idesc, tap > t0 ? 1u : 0u);
-            tc::commit(bar + kFzT1 + warp);
-        }
-        __syncwarp();
-        for (int e = tid; e < 3 * 4 * (8 + 9) + 2 * 9 * 4; e += kFzThreads) {
-            uint8_t* dst;
-            if (e < 3 * 4 * 17) {
-                const int rz = e / 68, c = (e / 17) & 3, k = e % 17;  // rows 0, 10, 20
-                dst = k < 8 ? E3 + c * kFzE3Plane + (rz * kFzR3) * kFzE3Pitch + k * 16
-                            : O3 + c * kFzO3Plane + (rz * kFzR3) * kFzO3Pitch + (k - 8) * 16;
-            } else {
-                const int z = e - 3 * 4 * 17, c = z & 3, rr = z >> 2, row = (rr / 9) * kFzR3 + 1 + rr % 9;
-                dst = O3 + c * kFzO3Plane + row * kFzO3Pitch;  // entry 0: column -1
-            }
-            *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
-        }
-        if (prev >= 0) head_c(prev);
-        for (int tt = half; tt < 4; tt += 2) {
-            ok = fz_wait(bar + kFzT1 + 2 * tt, par, ok, a.status);
-            ok = fz_wait(bar + kFzT1 + 2 * tt + 1, par, ok, a.status);
-            const int h = tt >> 1, first = (tt & 1) ? 16 : 0, g0 = (tt & 1) ? kFzG2 - 16 : 0;
-            const int g = g0 + (r >> 3), p = g / 10, oy = g - 10 * p;
-            const bool live = g >= first && oy < 9;
-            const int ox = 8 * h + (r & 7);
-            const int row = p * kFzR3 + oy + 1;
-            uint8_t* dst = (ox & 1) ? O3 + row * kFzO3Pitch + ((ox + 1) >> 1) * 16 : E3 + row * kFzE3Pitch + (ox >> 1) * 16;
-            const int cs = (ox & 1) ? kFzO3Plane : kFzE3Plane;
-            // the tile's 64 accumulator columns (two tap ranges x 32 channels) in one round trip
-            uint32_t us[4][16];
-            tc::ld16(tmem + tlane + 64 * tt, us[0]);
-            tc::ld16(tmem + tlane + 64 * tt + 32, us[1]);
-            tc::ld16(tmem + tlane + 64 * tt + 16, us[2]);
-            tc::ld16(tmem + tlane + 64 * tt + 48, us[3]);
-            tc::wait_ld();
-#pragma unroll
-            for (int c0 = 0; c0 < 32; c0 += 16) {
-                const uint32_t (&u0)[16] = us[c0 / 8];
-                const uint32_t (&u1)[16] = us[c0 / 8 + 1];
-                if (live) {
-                    uint32_t o[8];
-#pragma unroll
-                    for (int c = 0; c < 16; c += 2)
-                        o[c / 2] = relu_bf16x2(__uint_as_float(u0[c]) + __uint_as_float(u1[c]) + bias[16 + c0 + c],
-                                               __uint_as_float(u0[c + 1]) + __uint_as_float(u1[c + 1]) +
-                                                   bias[16 + c0 + c + 1]);
-                    const int q = c0 / 8;
-                    *reinterpret_cast<uint4*>(dst + q * cs) = make_uint4(o[0], o[1], o[2], o[3]);
-                    *reinterpret_cast<uint4*>(dst + (q + 1) * cs) = make_uint4(o[4], o[5], o[6], o[7]);
-                }
-            }
-        }
-        fz_sync();
-
-        // ---- phase 3: conv3, one tile of 128 x 32 (groups past kFzG3 are dropped); taps
-        //      0-2, 3-5, 6-8 accumulate in three TMEM blocks, issued by lane 0 of warps 0-2
-        if (lane == 0 && warp < 3) {
-            constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
-            const uint64_t* d = desc + 2 * (kFzD3 + 6 * warp);
-#pragma unroll
-            for (int m = 0; m < 6; ++m) tc::mma(tmem + 32 * warp, d[2 * m], d[2 * m + 1], idesc, m > 0 ? 1u : 0u);
-            tc::commit(bar + kFzT1 + 8 + warp);
-        }
-        __syncwarp();
-        {
-            ok = fz_wait(bar + kFzT1 + 8, par, ok, a.status);
-            ok = fz_wait(bar + kFzT1 + 9, par, ok, a.status);
-            ok = fz_wait(bar + kFzT1 + 10, par, ok, a.status);
-            uint32_t acc[16];
-            {
-                uint32_t u0[16], u1[16], u2[16];
-                tc::ld16(tmem + tlane + 16 * half, u0);
-                tc::ld16(tmem + tlane + 32 + 16 * half, u1);
-                tc::ld16(tmem + tlane + 64 + 16 * half, u2);
-                tc::wait_ld();
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    acc[c] = __float_as_uint(__uint_as_float(u0[c]) + __uint_as_float(u1[c]) + __uint_as_float(u2[c]));
-            }
-            // a3 (BF16-rounded) summed over the 8 positions of each output row: the 8 lanes
-            // of a group hold one row of one pair; groups past kFzG3 are dropped
-            const int g = r >> 3;
-            if (4 * quad < kFzG3) {  // warps of quad 3 hold dropped groups only
-                const float* b3 = bias + 48 + 16 * half;
-                float v[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    v[c] = g < kFzG3 ? __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(acc[c]) + b3[c], 0.f)))
-                                     : 0.f;
-#pragma unroll
-                for (int o = 1; o < 8; o <<= 1)
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
-                if (g < kFzG3 && (lane & 7) == 0) {
-                    const int p = g / 5, oy = g - 5 * p;
-                    float4* dst = reinterpret_cast<float4*>(part + (p * 5 + oy) * 32 + 16 * half);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                }
-            }
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        prev = batch;
-    }
-    if (prev >= 0) {  // the last batch's head
-        head_a();
-        __syncthreads();
-        head_b();
-        __syncthreads();
-        head_c(prev);
-    }
-
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 256);
-}
-
 // ---------------------------------------------------------------------------
 // inference: warp-specialised pipeline over batches, one CTA per SM
 // ---------------------------------------------------------------------------
 // Four warp groups of four warps work on different batches at the same time,
 // each on buffers of its own, and hand each batch on through mbarriers:
-//   group 0 (warps 0-3):  X1 of batch j and its conv1 MMAs;
-//   group 1 (warps 4-7):  conv1 epilogue of batch j into A1[j & 1];
-//   group 2 (warps 8-11): conv2 of batch j into A2[j & 1];
-//   group 3 (warps 12-15): conv3 of batch j (warp 15 issues its MMAs), pooling
-//                         and the head (FC1, FC2).
-// The batch's time is then that of the slowest group rather than the sum of
-// the phases.  Each layer's MMAs are issued by the group that produced its
-// input (conv1) or by the group that consumes its output (conv2, conv3), lane
-// 0 of each of its warps, so no layer waits behind another's in an issue
-// queue, and the issuing is
-// spread: a thread issues one accumulating tcgen05.mma per ~145 cycles (the
-// next one waits for the one before, whatever accumulator it writes), while
-// 2 and 4 issuing threads reach 74 and 41 cycles per MMA of 128 x 32 x 16
-// (measured on the B300).  The per-batch buffer layouts and MMA operand
-// addresses are those of the two-CTA form above; X1 is single, A1 and A2
-// double-buffered, and their padding is written once.  Differences in
-// arithmetic: conv1's bias enters through the MMA (every X1 entry carries 1.0
-// in its two spare K slots, W1 holds the bias split into two BF16 parts
-// there, so the epilogue is one conversion with ReLU per two values), conv2
-// accumulates all 9 taps in one accumulator per tile, and conv3 its two K
-// halves in two.  Each group owns the four TMEM lane quadrants through its
-// four warps; TMEM holds conv1's accumulators twice (columns 0-159 and
+//   group 0 (warps 0-3):   X1 of batch j and its conv1 MMAs;
+//   group 1 (warps 4-7):   conv1 epilogue of batch j into A1[j & 1];
+//   group 2 (warps 8-11):  conv2 of batch j (MMAs and epilogue) into A2[j & 1];
+//   group 3 (warps 12-15): conv3 of batch j (warp 15 issues its MMAs, one batch
+//                          ahead), pooling and the head (FC1, FC2).
+// A batch then takes the time of the slowest group, not the sum of the phases.
+// Each layer's MMAs are issued by lane 0 of several warps of the group that
+// produces its input (conv1) or consumes its output (conv2, conv3), so no
+// layer waits behind another's in an issue queue: one thread issues one
+// accumulating tcgen05.mma per ~145 cycles (each waits for the one before,
+// whatever accumulator it writes), while 2 and 4 issuing threads reach 74 and
+// 41 cycles per MMA of 128 x 32 x 16 (measured on the B300).  The per-batch
+// layouts are those above; X1 is single, A1 and A2 double-buffered, and their
+// padding is written once.  conv1's bias enters through the MMA (every X1
+// entry carries 1.0 in its two spare K slots, W1 holds the bias split into two
+// BF16 parts there, so the epilogue is one conversion with ReLU per two
+// values); conv2 accumulates all 9 taps in one accumulator per tile, conv3 its
+// two K halves in two.  Each group owns the four TMEM lane quadrants through
+// its four warps; TMEM holds conv1's accumulators twice (columns 0-159 and
 // 160-319, batch parity), conv2's at 320-447, conv3's at 448-511.  Every wait
 // is bounded (2 s), after which the thread records a timeout and stops
 // waiting; no thread leaves its loop early, so every barrier is still reached.
@@ -893,15 +489,14 @@ constexpr int kPpThreads = 512;
 constexpr int kPpW1 = 0;                                   // [16][32]
 constexpr int kPpW2 = kPpW1 + 16 * 32 * 2;                 // 9 x [32][16]
 constexpr int kPpW3 = kPpW2 + 9 * 32 * 16 * 2;             // 9 x [32][32]
-constexpr int kPpBias = kPpW3 + 9 * 32 * 32 * 2;           // same float layout as the two-CTA form
+constexpr int kPpBias = kPpW3 + 9 * 32 * 32 * 2;           // floats: b1 16, b2 32, b3 32, c1 64, f2 64, c2 1
 // mbarriers (count): X1 built (128 builder threads), X1 read by conv1 (4
 // issuers), conv1 tile done (2 TMEM buffers x 10 tiles, 1 each), conv1 TMEM
-// buffer read by group 1 (2, 4 warps each), A1[b] written
-// (128), A1[b] read by conv2 (4 issuers), conv2 tile done (4, 1 each), A2[b]
-// written (128), A2[b] read by conv3 (1 issuer), conv3 done (1 issuer).  A
-// group's TMEM accumulators are reused only after its own warps have read them
-// (groups 2 and 3 issue their layer's MMAs themselves, after a group barrier;
-// group 0 issues conv1's into a buffer that group 1 has released)
+// buffer read by group 1 (2, 4 warps each), A1[b] written (128), A1[b] read by
+// conv2 (4 issuers), conv2 tile done (4, 1 each), A2[b] written (128), A2[b]
+// read by conv3 (1 issuer), conv3 done (1 issuer).  Groups 2 and 3 reuse their
+// TMEM accumulators after a group barrier that follows their warps' reads;
+// group 0 issues conv1 into a buffer that group 1 has released.
 constexpr int kBX1Full = 0, kBX1Free = 1, kBT1Full = 2, kBT1Free = kBT1Full + 2 * kFzT1, kBA1Full = kBT1Free + 2,
               kBA1Free = kBA1Full + 2,
               kBT2Full = kBA1Free + 2, kBA2Full = kBT2Full + 4, kBA2Free = kBA2Full + 2, kBT3Full = kBA2Free + 2,
