@@ -320,8 +320,21 @@ scn_status scn_cnn_train_step(scn_cnn* c, const uint8_t* d_thumbs, const int32_t
 /* Device pointer to the BF16 NHWC output of conv layer 1, 2 or 3 of the last
  * scn_cnn_gradients / scn_cnn_train_step batch ([pairs][positions][channels]). */
 scn_status scn_cnn_activation(const scn_cnn* c, int32_t layer, const void** d_ptr);
-/* Synchronise stream, read and clear the network's device status word. */
+/* Synchronise stream, read and clear the network's device status word.
+ * Returns SCN_OK or SCN_ETIMEOUT (a bounded wait of a launch ran out; that
+ * launch's outputs are undefined; the network keeps no scratch between
+ * launches, so the next call is unaffected). */
 scn_status scn_cnn_sync_status(scn_cnn* c, void* stream);
+/* Test hook for the inference kernel's bounded waits (no counterpart in the
+ * paper; it exercises the status-word path without faulting or hanging the
+ * GPU).  Later scn_cnn_forward launches (and the learned / cascade paths that
+ * run them) wait at most wait_limit_ns at each bounded wait (0 restores the
+ * default 2 s; otherwise it must lie in [1e5, 1e10] ns, else SCN_EINVAL), and
+ * with withhold_batch = k >= 0 every CTA's builder warps withhold the "input
+ * built" signal of their k-th batch, so the waits on it run out: the launch
+ * ends by itself with SCN_ETIMEOUT in the status word and undefined logits.
+ * withhold_batch < 0 restores normal operation.  Host-only setter. */
+scn_status scn_cnn_set_wait_test(scn_cnn* c, uint64_t wait_limit_ns, int32_t withhold_batch);
 
 /* ------------------------------------------------------------------------ */
 /* Spacing and slicing (Sec. 3.2) and the per-shot montage (Sec. 5.2)       */

@@ -94,6 +94,8 @@ struct Net {
     int64_t max_batch;
     int64_t step;
     void* block;
+    uint64_t test_wait_ns;      // test hook (scn_cnn_set_wait_test): bounded-wait limit of the inference kernel
+    int32_t test_withhold;      //   (0: default) and the batch whose X1 the builders withhold (< 0: none)
 };
 
 // ---------------------------------------------------------------------------
@@ -435,6 +437,8 @@ struct FusedArgs {
     int* status;
     const int* d_pairs;        // non-null: the pair count, read on the device (at most pairs)
     const int32_t* out_index;  // non-null: pair b's logit goes to logits[out_index[b]]
+    uint64_t wait_ns;          // bounded-wait limit (test hook; 0 = kWaitNs)
+    int32_t withhold;          // test hook: the builders withhold X1 of this local batch (< 0: none)
 };
 
 // (byte k of w - 128) / 64 as fp32: the byte placed in the mantissa of 2^23
@@ -518,8 +522,8 @@ static_assert(kFzReg1Bytes % 16 == 0 && kPpA2Bytes % 16 == 0 && kFzReg0Bytes % 1
 static_assert(kFzPairs * 36 % 4 == 0, "build rows split evenly over the four builder warps");
 
 // bounded wait by one thread (no warp-wide step: callers may be a single lane)
-__device__ __forceinline__ bool pp_wait1(uint64_t* bar, uint32_t par, bool ok, int* status) {
-    if (ok && !ptx::mbar_wait_bounded(bar, par, kWaitNs)) {
+__device__ __forceinline__ bool pp_wait1(uint64_t* bar, uint32_t par, bool ok, int* status, uint64_t limit) {
+    if (ok && !ptx::mbar_wait_bounded(bar, par, limit)) {
         atomicOr(status, kStatusTimeout);
         ok = false;
     }
@@ -615,6 +619,7 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
     const uint32_t tmem = *tslot;
     const uint32_t tlane = static_cast<uint32_t>(32 * quad) << 16;
     bool ok = true;
+    const uint64_t wlim = a.wait_ns ? a.wait_ns : kWaitNs;
 
     const int64_t npairs = a.d_pairs ? min(static_cast<int64_t>(max(*a.d_pairs, 0)), a.pairs) : a.pairs;
     const int64_t nbatch = (npairs + kFzPairs - 1) / kFzPairs;
@@ -652,7 +657,7 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
                 pair_thumbs(batch + gridDim.x, 1, ip1, ic1);
             }
             // X1 is free once the conv1 MMAs of batch j-1 have completed
-            if (j > 0) ok = pp_wait1(&bar[kBX1Free], (j - 1) & 1, ok, a.status);
+            if (j > 0) ok = pp_wait1(&bar[kBX1Free], (j - 1) & 1, ok, a.status, wlim);
 #pragma unroll
             for (int q = 0; q < kRows; ++q) {
                 const int task = warp + 4 * q, p = task / 36, iy = task - 36 * p;
@@ -667,13 +672,13 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
                 *reinterpret_cast<uint4*>(row + lane * 16) = make_uint4(w0, w1, w2, kPpOnes);
             }
             tc::fence_proxy_async();
-            ptx::mbar_arrive(&bar[kBX1Full]);
+            if (j != a.withhold) ptx::mbar_arrive(&bar[kBX1Full]);  // test hook: a withheld batch times out
             // conv1 of batch j into TMEM buffer j & 1: lane 0 of warp w issues tiles w, w + 4,
             // w + 8 once every builder is done and group 1 has read the buffer (batch j-2)
             if (lane == 0) {
                 const int cb = j & 1;
-                ok = pp_wait1(&bar[kBX1Full], j & 1, ok, a.status);
-                if (j >= 2) ok = pp_wait1(&bar[kBT1Free + cb], ((j >> 1) + 1) & 1, ok, a.status);
+                ok = pp_wait1(&bar[kBX1Full], j & 1, ok, a.status, wlim);
+                if (j >= 2) ok = pp_wait1(&bar[kBT1Free + cb], ((j >> 1) + 1) & 1, ok, a.status, wlim);
                 tc::fence_after_sync();
                 constexpr uint32_t idesc = tc::idesc_bf16(128, 16);
                 for (int t = warp; t < kFzT1; t += 4) {
@@ -697,12 +702,12 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
             uint8_t* E2 = smem + kPpA1 + b * kFzReg1Bytes;
             uint8_t* O2 = E2 + 2 * kFzE2Plane;
             // A1[b] is free once the conv2 MMAs of batch j-2 have completed
-            if (j >= 2) ok = pp_wait1(&bar[kBA1Free + b], ((j >> 1) + 1) & 1, ok, a.status);
+            if (j >= 2) ok = pp_wait1(&bar[kBA1Free + b], ((j >> 1) + 1) & 1, ok, a.status, wlim);
             const uint32_t t1 = tmem + tlane + kPpT1 + 16 * kFzT1 * b;  // the batch's conv1 accumulators
             for (int t0 = 0; t0 < kFzT1; t0 += 4) {
                 const int nt = min(4, kFzT1 - t0);
                 for (int u = 0; u < nt; ++u)
-                    ok = pp_wait1(&bar[kBT1Full + kFzT1 * b + t0 + u], (j >> 1) & 1, ok, a.status);
+                    ok = pp_wait1(&bar[kBT1Full + kFzT1 * b + t0 + u], (j >> 1) & 1, ok, a.status, wlim);
                 __syncwarp();
                 tc::fence_after_sync();
                 uint32_t accs[64];
@@ -757,7 +762,7 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
                 tc::fence_after_sync();
             }
             if (lane == 0) {
-                ok = pp_wait1(&bar[kBA1Full + b], (j >> 1) & 1, ok, a.status);
+                ok = pp_wait1(&bar[kBA1Full + b], (j >> 1) & 1, ok, a.status, wlim);
                 tc::fence_after_sync();
                 constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
                 // tile quad: column half h, first group g0; tap (dy, dx) reads the even-
@@ -779,9 +784,9 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
             __syncwarp();
             uint8_t* E3 = smem + kPpA2 + b * kPpA2Bytes;
             uint8_t* O3 = E3 + 4 * kFzE3Plane;
-            if (j >= 2) ok = pp_wait1(&bar[kBA2Free + b], ((j >> 1) + 1) & 1, ok, a.status);
+            if (j >= 2) ok = pp_wait1(&bar[kBA2Free + b], ((j >> 1) + 1) & 1, ok, a.status, wlim);
             for (int tt = 0; tt < 4; ++tt) {
-                ok = pp_wait1(&bar[kBT2Full + tt], j & 1, ok, a.status);
+                ok = pp_wait1(&bar[kBT2Full + tt], j & 1, ok, a.status, wlim);
                 __syncwarp();
                 tc::fence_after_sync();
                 const int h = tt >> 1, first = (tt & 1) ? 16 : 0, g0 = (tt & 1) ? kFzG2 - 16 : 0;
@@ -822,7 +827,7 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
         //      run while the other three warps pool and compute the head of batch j.
         auto issue_conv3 = [&](int jj) {  // lane 0 of warp 15
             const int bb = jj & 1;
-            ok = pp_wait1(&bar[kBA2Full + bb], (jj >> 1) & 1, ok, a.status);
+            ok = pp_wait1(&bar[kBA2Full + bb], (jj >> 1) & 1, ok, a.status, wlim);
             tc::fence_after_sync();
             constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
             const uint32_t s_e3 = sbase + kPpA2 + bb * kPpA2Bytes, s_o3 = s_e3 + 4 * kFzE3Plane;
@@ -851,7 +856,7 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
         for (int j = 0; j < nb; ++j) {
             const int b = j & 1;
             float* part = reinterpret_cast<float*>(smem + kPpPart) + b * (kFzPairs * 5 * 32);
-            ok = pp_wait1(&bar[kBT3Full], j & 1, ok, a.status);
+            ok = pp_wait1(&bar[kBT3Full], j & 1, ok, a.status, wlim);
             __syncwarp();
             tc::fence_after_sync();
             uint32_t acc2[64];  // the two accumulators (K halves), 32 channels each
@@ -948,6 +953,8 @@ scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* pr
     a.status = n->status;
     a.d_pairs = d_pairs;
     a.out_index = out_index;
+    a.wait_ns = n->test_wait_ns;
+    a.withhold = n->test_withhold;
     const int64_t nbatch = (pairs + kFzPairs - 1) / kFzPairs;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
@@ -1478,6 +1485,8 @@ scn_status scn_cnn_create(int64_t max_batch, scn_cnn** out) {
     Net& n = c->net;
     std::memset(&n, 0, sizeof(n));
     n.max_batch = max_batch;
+    n.test_wait_ns = 0;    // the test hook off: default wait limit,
+    n.test_withhold = -1;  // nothing withheld
     const int64_t B = max_batch;
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
@@ -1593,6 +1602,14 @@ scn_status scn_cnn_activation(const scn_cnn* c, int32_t layer, const void** d_pt
         case 3: *d_ptr = c->net.a3; return SCN_OK;
         default: return SCN_ERANGE;
     }
+}
+
+scn_status scn_cnn_set_wait_test(scn_cnn* c, uint64_t wait_limit_ns, int32_t withhold_batch) {
+    if (!c) return SCN_EINVAL;
+    if (wait_limit_ns != 0 && (wait_limit_ns < 100000ull || wait_limit_ns > 10000000000ull)) return SCN_EINVAL;
+    c->net.test_wait_ns = wait_limit_ns;
+    c->net.test_withhold = withhold_batch < 0 ? -1 : withhold_batch;
+    return SCN_OK;
 }
 
 scn_status scn_cnn_sync_status(scn_cnn* c, void* stream) {

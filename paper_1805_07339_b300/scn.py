@@ -77,6 +77,7 @@ SIGNATURES = [
     ("scn_seq_destroy", c_i32, [c_vp]),
     ("scn_seq_sync_status", c_i32, [c_vp, c_vp]),
     ("scn_seq_set_wait_test", c_i32, [c_vp, c_u64, c_i32]),
+    ("scn_cnn_set_wait_test", c_i32, [c_vp, c_u64, c_i32]),
     ("scn_seq_set_tune", c_i32, [c_vp, _P(scn_tune)]),
     ("scn_seq_get_tune", c_i32, [c_vp, _P(scn_tune)]),
     ("scn_hist", c_i32, [c_vp, c_vp, c_vp]),
@@ -295,6 +296,12 @@ def scn_seq_set_wait_test(s: int, wait_limit_ns: int = 0, withhold_after: int = 
     """Test hook: bounded-wait limit of this sequence's hist launches (0: default)
     and, for withhold_after >= 0, chunks each producer hands out before withholding."""
     _check(_lib.scn_seq_set_wait_test(s, wait_limit_ns, withhold_after), "scn_seq_set_wait_test")
+
+
+def scn_cnn_set_wait_test(c: int, wait_limit_ns: int = 0, withhold_batch: int = -1) -> None:
+    """Test hook: bounded-wait limit of this network's inference launches (0: default)
+    and, for withhold_batch >= 0, the batch whose input-built signal is withheld."""
+    _check(_lib.scn_cnn_set_wait_test(c, wait_limit_ns, withhold_batch), "scn_cnn_set_wait_test")
 
 
 def scn_seq_set_tune(s: int, chunk_rows: int = 0, grid: int = 0, item_kpx: int = 0) -> None:

@@ -87,3 +87,36 @@ def test_short_limit_without_withholding_is_exact(scn, orc):
     finally:
         scn.scn_seq_destroy(seq)
         scn.scn_table_destroy(table)
+
+
+@pytest.mark.parametrize("pairs,withhold", [(600, 0), (600, 1), (7199, 3)])
+def test_forward_withheld_batch_times_out_and_the_next_call_is_exact(scn, pairs, withhold):
+    """The proposal network's inference kernel: its builder warps withhold the
+    "input built" signal of one batch (a test hook), the bounded waits on it run
+    out after 20 ms, the launch ends by itself and scn_cnn_sync_status reports
+    SCN_ETIMEOUT; the next launch (nothing withheld) gives the logits of a launch
+    made before, bit for bit."""
+    from paper_1805_07339_b300.proposal import he_uniform
+    g = torch.Generator(device="cpu").manual_seed(11 + withhold)
+    th = torch.randint(0, 256, (pairs + 1, 36, 64), dtype=torch.uint8, generator=g).cuda()
+    net = scn.scn_cnn_create(8)
+    try:
+        scn.scn_cnn_set_params(net, he_uniform(3))
+        ref = torch.full((pairs,), float("nan"), dtype=torch.float32, device="cuda")
+        scn.scn_cnn_forward(net, th, pairs, ref)
+        assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
+        with pytest.raises(scn.ScnError):  # limits outside [100 us, 10 s] are refused
+            scn.scn_cnn_set_wait_test(net, 1000, withhold)
+        scn.scn_cnn_set_wait_test(net, LIMIT_NS, withhold)
+        z = torch.full((pairs,), float("nan"), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            scn.scn_cnn_forward(net, th, pairs, z)
+            assert scn.scn_cnn_sync_status(net) == scn.SCN_ETIMEOUT
+        assert scn.scn_cnn_sync_status(net) == scn.SCN_OK  # the status word was cleared
+        scn.scn_cnn_set_wait_test(net, 0, -1)
+        z.fill_(float("nan"))
+        scn.scn_cnn_forward(net, th, pairs, z)
+        assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
+        assert torch.equal(z, ref)
+    finally:
+        scn.scn_cnn_destroy(net)
