@@ -177,9 +177,10 @@ scn_status scn_seq_sync_status(scn_seq* s, void* stream);
  * hanging the GPU).  Later scn_hist / scn_hist_scores launches of this sequence
  * wait at most wait_limit_ns at each bounded wait (0 restores the default 2 s;
  * otherwise it must lie in [1e5, 1e10] ns, else SCN_EINVAL), and with
- * withhold_after = k >= 0 each CTA's producer hands out k chunks of work and
- * then withholds the rest, so the consumers' waits run out: the launch ends by
- * itself with SCN_ETIMEOUT in the status word and undefined outputs.
+ * withhold_after = k >= 0 each counting region of each CTA hands its warps k
+ * chunks of work and then withholds the rest, so the waits on it run out: the
+ * launch ends by itself with SCN_ETIMEOUT in the status word and undefined
+ * outputs.
  * withhold_after < 0 restores normal operation.  Host-only setter. */
 scn_status scn_seq_set_wait_test(scn_seq* s, uint64_t wait_limit_ns, int32_t withhold_after);
 

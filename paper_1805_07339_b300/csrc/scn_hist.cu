@@ -116,6 +116,32 @@ static_assert(kStages * sizeof(ChunkMeta) + 128 * 4 + 2 * sizeof(PubMeta) + (2 *
                   kSmemMisc,
               "misc smem");
 
+struct SmemRg {
+    uint8_t* tab;
+    ChunkMeta* slot;    // [kRegions][2] the region's current and next chunk
+    uint32_t* acc;      // [kRegions][2][64]: flushed counts of an item, double-buffered for the publisher
+    PubMeta* pmeta;     // [kRegions][2]
+    uint64_t* cbar;     // [kRegions] barrier of one table region's consumer warps
+    uint64_t* accfull;  // [kRegions][2] acc holds an item's counts (the region's first thread arrives)
+    uint64_t* accfree;  // [kRegions][2] the publisher has taken acc (its 32 lanes arrive)
+    int* abort_flag;
+};
+
+__device__ __forceinline__ SmemRg carve_rg(uint8_t* smem) {
+    SmemRg s;
+    s.tab = smem;
+    s.acc = reinterpret_cast<uint32_t*>(smem + kTabBytes);
+    s.slot = reinterpret_cast<ChunkMeta*>(s.acc + kRegions * 2 * 64);
+    s.pmeta = reinterpret_cast<PubMeta*>(s.slot + kRegions * 2);
+    s.cbar = reinterpret_cast<uint64_t*>(s.pmeta + kRegions * 2);
+    s.accfull = s.cbar + kRegions;
+    s.accfree = s.accfull + kRegions * 2;
+    s.abort_flag = reinterpret_cast<int*>(s.accfree + kRegions * 2);
+    return s;
+}
+static_assert(kRegions * (2 * 64 * 4 + 2 * sizeof(ChunkMeta) + 2 * sizeof(PubMeta) + 5 * 8) + 16 <= kSmemMisc,
+              "misc smem (region streams)");
+
 __device__ __forceinline__ const Job& job_of(const Launch& L, int j) { return L.jobs ? L.jobs[j] : L.job0; }
 
 // how long a bounded wait of this launch waits before it gives up
@@ -128,12 +154,14 @@ __device__ __forceinline__ int64_t device_elems(const Launch& L) {
     return L.d_count ? static_cast<int64_t>(L.count_mul) * static_cast<int64_t>(*L.d_count) : L.job0.n;
 }
 
-__device__ __forceinline__ void fail(const Launch& L, const Smem& s) {
+template <class S>
+__device__ __forceinline__ void fail(const Launch& L, const S& s) {
     *reinterpret_cast<volatile int*>(s.abort_flag) = 1;
     atomicOr(L.status, kStatusTimeout);
 }
 
-__device__ __forceinline__ bool aborted(const Smem& s) {
+template <class S>
+__device__ __forceinline__ bool aborted(const S& s) {
     return *reinterpret_cast<volatile int*>(s.abort_flag) != 0;
 }
 
@@ -181,6 +209,118 @@ __device__ __forceinline__ bool stage_chunk(const Launch& L, const Smem& s, uint
 // out and the launch ends with the timeout bit in the status word.
 __device__ __forceinline__ bool withheld(const Launch& L, uint32_t it) {
     return L.withhold_after >= 0 && it >= static_cast<uint32_t>(L.withhold_after);
+}
+
+// ---------------------------------------------------------------------------
+// work of a table region: each region's first thread walks its share of the
+// CTA's work (popped items, or a contiguous range of row pairs) and hands its
+// four warps one chunk at a time, so that a frame is counted (and its table
+// flushed) by one region only
+// ---------------------------------------------------------------------------
+struct RegionSource {
+    bool queue;              // items popped from the launch's queue (else a contiguous range)
+    bool have_item, have_next, ended;
+    Item item;
+    uint64_t next;           // index of the next item, popped one item ahead
+    int r, r_end;            // luma rows of the current item still to hand out
+    int64_t g, g_end, k;     // contiguous mode: row pairs [g, g_end), current element k
+    int rp, seg;             //   row pair within element k, row pairs of the open segment
+    uint32_t handed;         // chunks handed out (test hook)
+};
+
+__device__ __forceinline__ int64_t queue_items(const Launch& L) {
+    return L.d_count ? device_elems(L) * L.job0.items_per_frame : L.n_items;
+}
+
+__device__ void src_init(RegionSource& q, const Launch& L, int region) {
+    q.handed = 0;
+    q.have_item = q.have_next = q.ended = false;
+    q.queue = L.rp_per_cta == 0;
+    if (q.queue) return;
+    // the CTA's contiguous range of job0's row pairs, split evenly over its regions;
+    // segments end at frame edges and every item_rp row pairs (16-bit bound)
+    const Job& J = L.job0;
+    const int hp = J.H / 2;
+    const int64_t total_rp = device_elems(L) * hp;
+    const int64_t rpc = L.rp_per_cta > 0 ? L.rp_per_cta : (total_rp + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = min(static_cast<int64_t>(blockIdx.x) * rpc, total_rp);
+    const int64_t c1 = min(c0 + rpc, total_rp);
+    const int64_t per = (c1 - c0 + kRegions - 1) / kRegions;
+    q.g = min(c0 + region * per, c1);
+    q.g_end = min(q.g + per, c1);
+    q.k = q.g / hp;
+    q.rp = static_cast<int>(q.g - q.k * hp);
+    q.seg = 0;
+}
+
+// pop one item index (the region that first finds the queue empty counts itself
+// done; the last of all regions resets the queue, so a launch leaves it zero)
+__device__ __forceinline__ uint64_t pop_item(RegionSource& q, const Launch& L) {
+    const uint64_t i = atomicAdd(reinterpret_cast<unsigned long long*>(L.queue), 1ull);
+    if (i >= static_cast<uint64_t>(queue_items(L)) && !q.ended) {
+        q.ended = true;
+        const uint32_t old = atomicAdd(&L.queue[2], 1u);
+        if (old == gridDim.x * kRegions - 1) {
+            atomicExch(reinterpret_cast<unsigned long long*>(L.queue), 0ull);
+            atomicExch(&L.queue[2], 0u);
+        }
+    }
+    return i;
+}
+
+// the region's next chunk (job < 0: no more)
+__device__ ChunkMeta src_next(RegionSource& q, const Launch& L) {
+    ChunkMeta m{};
+    m.job = -1;
+    if (!q.queue) {
+        if (q.g >= q.g_end) return m;
+        const Job& J = L.job0;
+        const int hp = J.H / 2, crp = J.chunk_rows / 2, srp = J.item_rp;
+        int mm = min(crp, hp - q.rp);
+        if (q.g_end - q.g < mm) mm = static_cast<int>(q.g_end - q.g);
+        mm = min(mm, srp - q.seg);
+        const int nseg = q.seg + mm;
+        const bool seg_end = (q.rp + mm == hp) || (q.g + mm == q.g_end) || (nseg == srp);
+        m.job = 0;
+        m.k = static_cast<int32_t>(q.k);
+        m.rows = 2 * mm;
+        m.seg_end = seg_end;
+        m.seg_rp = nseg;
+        m.r0 = 2 * q.rp;
+        q.g += mm;
+        q.rp += mm;
+        q.seg = seg_end ? 0 : nseg;
+        if (q.rp == hp) {
+            q.rp = 0;
+            ++q.k;
+        }
+        return m;
+    }
+    if (!q.have_item) {
+        if (q.ended && !q.have_next) return m;
+        const uint64_t i = q.have_next ? q.next : pop_item(q, L);
+        q.have_next = false;
+        if (i >= static_cast<uint64_t>(queue_items(L))) return m;
+        q.item = item_at(L, static_cast<int64_t>(i));
+        q.r = 2 * q.item.rp0;
+        q.r_end = 2 * (q.item.rp0 + q.item.nrp);
+        q.have_item = true;
+        if (!q.ended) {  // the next item's index, one item ahead (its latency hides behind this item)
+            q.next = pop_item(q, L);
+            q.have_next = true;
+        }
+    }
+    const Job& J = job_of(L, q.item.job);
+    const int rows = min(J.chunk_rows, q.r_end - q.r);
+    m.job = q.item.job;
+    m.k = q.item.k;
+    m.rows = rows;
+    m.seg_end = q.r + rows == q.r_end;
+    m.seg_rp = q.item.nrp;
+    m.r0 = q.r;
+    q.r += rows;
+    if (m.seg_end) q.have_item = false;
+    return m;
 }
 
 __device__ void produce(const Launch& L, const Smem& s) {
@@ -324,7 +464,6 @@ __device__ __forceinline__ void count_unit(uint32_t lanereg, uint32_t inc, uint3
 // the region): every row summed over its 64 words and both 16-bit halves,
 // extended bin folded into the final bin, added into acc[48]; the region's
 // rows are left zeroed.
-constexpr int kRegionThreads = kGroupWarps * 32;
 __device__ __forceinline__ void flush_region(uint8_t* tab, uint32_t* acc, int region, int rt) {
     const int lane = rt & 31;
     for (int row = region * kTabRowsPerRegion + rt; row < (region + 1) * kTabRowsPerRegion; row += kRegionThreads) {
@@ -605,6 +744,235 @@ __global__ void __launch_bounds__(kHistThreads, 1) hist_kernel(const __grid_cons
     consume(L, s, warp, lane);
 }
 
+// Barrier of one table region's consumer threads, bounded: every one of them
+// arrives (release) and waits (acquire) for the phase.  A consumer that gave up
+// earlier has left the loop, so the others would wait for it forever on a named
+// barrier; here they give up too, after the launch's wait limit.
+__device__ __forceinline__ bool consumer_sync_rg(const Launch& L, const SmemRg& s, int region, uint32_t& phase) {
+    ptx::mbar_arrive(&s.cbar[region]);
+    const bool ok = ptx::mbar_wait_bounded(&s.cbar[region], phase & 1u, wait_limit(L));
+    ++phase;
+    if (!ok) fail(L, s);
+    return ok;
+}
+
+// One table region (four warps): its first thread hands out the region's chunks
+// through slot[region][2] (chunk c + 1 written while chunk c is counted, made
+// visible by the region barrier that ends chunk c); all 128 threads count each
+// chunk's units; at the end of an item the region flushes its table into one of
+// its two accumulators and hands it to the publisher warp.
+__device__ void consume_rg(const Launch& L, const SmemRg& s, int warp, int lane) {
+    const int region = warp / kGroupWarps;
+    const int rt = (warp - region * kGroupWarps) * 32 + lane;  // thread within the region
+    const bool leader = rt == 0;
+    ChunkMeta* slot = s.slot + 2 * region;
+    uint32_t* racc = s.acc + region * 2 * 64;
+    const uint32_t lanereg = static_cast<uint32_t>(lane * 4 + (warp & 1) * 128);
+    const uint32_t inc = (warp & 2) ? 65536u : 1u;
+    // table row of x = (x >> 16): shared base / 256 + region rows + channel rows + extended bin
+    const uint32_t rowbase = ((ptx::smem_u32(s.tab) >> 8) + static_cast<uint32_t>(region * kTabRowsPerRegion)) << 16;
+    const uint32_t cR = static_cast<uint32_t>(kCR) + rowbase + (static_cast<uint32_t>(kBaseR) << 16);
+    const uint32_t cG = static_cast<uint32_t>(kCG) + rowbase + (static_cast<uint32_t>(kBaseG) << 16);
+    const uint32_t cB = static_cast<uint32_t>(kCB) + rowbase + (static_cast<uint32_t>(kBaseB) << 16);
+    RegionSource src;
+    bool stop = false;  // the leader withholds the rest (test hook)
+    if (leader) {
+        src_init(src, L, region);
+        if (withheld(L, 0)) {
+            slot[0].job = -2;  // the region's warps stop; no end marker, so the publisher gives up
+            stop = true;
+        } else {
+            slot[0] = src_next(src, L);
+            src.handed = 1;
+        }
+    }
+    uint32_t cphase = 0;  // completed phases of the region barrier
+    uint32_t seg = 0;     // items flushed so far (acc buffer seg & 1)
+    uint32_t par = 0;     // slot of the current chunk
+    int rot = 0;
+    // geometry of the current job, kept in registers: reloaded only when a chunk
+    // belongs to another job (global loads at every chunk start stall all warps)
+    int cur_job = -1, W = 0, H = 0, wv = 1, sc = 0;
+    uint32_t dY = 0, dU = 0;
+    float inv_wv = 1.f;
+    if (!consumer_sync_rg(L, s, region, cphase)) return;  // slot[0] written
+    for (;;) {
+        if (aborted(s)) break;
+        const ChunkMeta m = slot[par];
+        if (m.job < 0) break;
+        // the next chunk, while this one is counted (its slot was last read before the
+        // barrier that started this chunk)
+        if (leader) {
+            if (withheld(L, src.handed)) {
+                slot[par ^ 1u].job = -2;  // as above
+                stop = true;
+            } else {
+                slot[par ^ 1u] = src_next(src, L);
+                ++src.handed;
+            }
+        }
+        const Job& J = job_of(L, m.job);
+        if (m.job != cur_job) {
+            cur_job = m.job;
+            W = J.W;
+            wv = J.wv;
+            sc = J.sc_r;
+            H = J.H;
+            dY = J.dY_r;
+            dU = J.dU_r;
+            inv_wv = J.inv_wv;
+        }
+        const uint8_t* frame = J.nv12 + static_cast<int64_t>(J.slot[m.k]) * J.stride;
+        const int units = (m.rows / 2) * wv;
+        int u = rt - rot;
+        if (u < 0) u += kRegionThreads;
+        const int p0 = static_cast<int>((static_cast<float>(u) + 0.5f) * inv_wv);
+        int c = u - p0 * wv;
+        // unit u of the chunk: row pair p0 + (u / wv), 16-byte column c; luma rows
+        // r0 + 2p, r0 + 2p + 1 and chroma row r0/2 + p
+        const uint8_t* ya = frame + static_cast<int64_t>(m.r0 + 2 * p0) * W + c * 16;
+        const uint8_t* ua = frame + static_cast<int64_t>(W) * H + static_cast<int64_t>(m.r0 / 2 + p0) * W + c * 16;
+        uint4 y0{}, y1{}, uv{};
+        if (u < units) {
+            y0 = ldg128(ya);
+            y1 = ldg128(ya + W);
+            uv = ldg128(ua);
+        }
+        for (; u < units; u += kRegionThreads) {
+            // next unit: kRegionThreads units on; a column wrap adds one more row pair
+            // and removes a row of columns (luma +2W-W, chroma +W-W).  Its loads are
+            // issued before this unit is counted.
+            ya += dY;
+            ua += dU;
+            c += sc;
+            if (c >= wv) {
+                c -= wv;
+                ya += W;
+            }
+            uint4 ny0{}, ny1{}, nuv{};
+            if (u + kRegionThreads < units) {
+                ny0 = ldg128(ya);
+                ny1 = ldg128(ya + W);
+                nuv = ldg128(ua);
+            }
+            count_unit(lanereg, inc, cR, cG, cB, y0, y1, uv);
+            y0 = ny0;
+            y1 = ny1;
+            uv = nuv;
+        }
+        rot = (rot + units) % kRegionThreads;
+        if (m.seg_end) {
+            const uint32_t b = seg & 1u;
+            if (!consumer_sync_rg(L, s, region, cphase)) break;  // the region has counted the item
+            // acc[b] was last filled two items ago: the publisher has taken it
+            if (seg >= 2 && !ptx::mbar_wait_bounded(&s.accfree[2 * region + b], ((seg >> 1) - 1) & 1u,
+                                                    wait_limit(L))) {
+                fail(L, s);
+                break;
+            }
+            flush_region(s.tab, racc + 64 * b, region, rt);
+            // rows zeroed, acc[b] complete, the next chunk's slot written
+            if (!consumer_sync_rg(L, s, region, cphase)) break;
+            if (leader) {
+                s.pmeta[2 * region + b] = PubMeta{m.job, m.k, m.seg_rp, 0};
+                ptx::mbar_arrive(&s.accfull[2 * region + b]);  // release: the counts and their item
+            }
+            ++seg;
+        } else {
+            if (!consumer_sync_rg(L, s, region, cphase)) break;  // the next chunk's slot written
+        }
+        par ^= 1u;
+    }
+    // tell the publisher that the region is done (not after a failure or a withheld
+    // chunk: the publisher then gives up by itself)
+    if (leader && !stop && !aborted(s)) {
+        const uint32_t b = seg & 1u;
+        if (seg < 2 || ptx::mbar_wait_bounded(&s.accfree[2 * region + b], ((seg >> 1) - 1) & 1u, wait_limit(L))) {
+            s.pmeta[2 * region + b] = PubMeta{-1, 0, 0, 0};
+            ptx::mbar_arrive(&s.accfull[2 * region + b]);
+        } else {
+            fail(L, s);
+        }
+    }
+}
+
+// The publisher warp: takes each flushed item's counts off a region's accumulator
+// (freeing it for the region at once) and publishes them - global atomics, frame
+// completion, the score of each completed pair - so that the latency of those
+// global round trips is not on the consumers' path.  It polls the regions in turn
+// and gives up when none has handed over an item for the launch's wait limit.
+__device__ void publisher_rg(const Launch& L, const SmemRg& s, int lane) {
+    const int64_t n_dev = device_elems(L);
+    uint32_t pseg[kRegions];
+    uint32_t live = (1u << kRegions) - 1u;  // regions not yet done
+#pragma unroll
+    for (int r = 0; r < kRegions; ++r) pseg[r] = 0;
+    uint64_t t_last = ptx::globaltimer();
+    uint32_t polls = 0;
+    while (live) {
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < kRegions; ++r) {
+            if (!((live >> r) & 1u)) continue;
+            const uint32_t b = pseg[r] & 1u;
+            if (!ptx::mbar_try_wait(&s.accfull[2 * r + b], (pseg[r] >> 1) & 1u)) continue;
+            any = true;
+            const PubMeta pm = s.pmeta[2 * r + b];
+            if (pm.job < 0) {
+                live &= ~(1u << r);
+                continue;
+            }
+            uint32_t* acc = s.acc + (2 * r + b) * 64;
+            const uint32_t h0 = acc[lane];
+            const uint32_t h1 = lane < 16 ? acc[32 + lane] : 0u;
+            acc[lane] = 0;
+            if (lane < 16) acc[32 + lane] = 0;
+            ptx::mbar_arrive(&s.accfree[2 * r + b]);  // release: acc read and zeroed
+            const Job& J = job_of(L, pm.job);
+            publish(J, L.d_count ? n_dev : J.n, pm.k, pm.seg_rp, h0, h1, lane);
+            ++pseg[r];
+        }
+        if (any) {
+            t_last = ptx::globaltimer();
+        } else {
+            // nothing handed over: back off, the polls would take shared-memory cycles from
+            // the counting (items take microseconds; each region has two accumulators)
+            __nanosleep(256);
+            if ((++polls & 15u) == 0 && ptx::globaltimer() - t_last > wait_limit(L)) {
+                fail(L, s);
+                return;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kHistThreadsRg, 1) hist_kernel_rg(const __grid_constant__ Launch L) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const SmemRg s = carve_rg(smem);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < kTabBytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kRegions * 2 * 64; i += blockDim.x) s.acc[i] = 0;
+    if (tid == 0) {
+        for (int r = 0; r < kRegions; ++r) {
+            ptx::mbar_init(&s.cbar[r], kRegionThreads);
+            for (int i = 0; i < 2; ++i) {
+                ptx::mbar_init(&s.accfull[2 * r + i], 1);
+                ptx::mbar_init(&s.accfree[2 * r + i], 32);
+            }
+        }
+        *s.abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == kConsumerWarps) {
+        publisher_rg(L, s, lane);
+        return;
+    }
+    consume_rg(L, s, warp, lane);
+}
+
+
 // One warp per element: score[k] from hist[k-1], hist[k].
 __global__ void scores_kernel(const uint32_t* hist, int64_t n, int64_t pixel_count, uint32_t* score, uint8_t* flag) {
     const int lane = threadIdx.x & 31;
@@ -643,6 +1011,11 @@ void fill_job_consts(Job& j) {
     j.sc = kNT % j.wv;
     j.dY = static_cast<uint32_t>(j.sp * 2 * j.W + j.sc * 16);
     j.dU = static_cast<uint32_t>(j.sp * j.W + j.sc * 16);
+    // the same steps for one table region's threads (the region-stream kernel)
+    const int sp_r = kRegionThreads / j.wv;
+    j.sc_r = kRegionThreads % j.wv;
+    j.dY_r = static_cast<uint32_t>(sp_r * 2 * j.W + j.sc_r * 16);
+    j.dU_r = static_cast<uint32_t>(sp_r * j.W + j.sc_r * 16);
     j.inv_wv = 1.0f / static_cast<float>(j.wv);
 }
 
@@ -655,7 +1028,7 @@ void choose_items(Job& j, int64_t item_px, int grid) {
     } else {
         // whole frames when there are plenty of them; else split frames so the
         // queue holds about 8 items per CTA
-        const int64_t want = 8LL * grid;
+        const int64_t want = 8LL * grid * (region_frames(j.W, j.H) ? kRegions : 1);
         const int64_t n = std::max<int64_t>(j.n, 1);
         ipf = n >= want ? 1 : (want + n - 1) / n;
     }
@@ -671,6 +1044,7 @@ void choose_items(Job& j, int64_t item_px, int grid) {
 scn_status prepare_hist() {
     return once_per_device(g_attr_done, [] {
         SCN_CUDA_TRY(cudaFuncSetAttribute(hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        SCN_CUDA_TRY(cudaFuncSetAttribute(hist_kernel_rg, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
         return SCN_OK;
     });
 }
@@ -681,7 +1055,10 @@ scn_status launch_hist(const Launch& L, cudaStream_t st) {
     if (L.n_items <= 0 || L.grid <= 0) return SCN_OK;
     const scn_status sp = prepare_hist();
     if (sp != SCN_OK) return sp;
-    hist_kernel<<<L.grid, kHistThreads, smem, st>>>(L);
+    if (L.region_items)
+        hist_kernel_rg<<<L.grid, kHistThreadsRg, smem, st>>>(L);
+    else
+        hist_kernel<<<L.grid, kHistThreads, smem, st>>>(L);
     SCN_CUDA_TRY(cudaGetLastError());
     return SCN_OK;
 }
@@ -737,6 +1114,7 @@ Launch single_launch(const scn_table* t, int64_t n, const int32_t* slot, const H
     L.n_items = n * sh.items_per_frame;
     L.rp_per_cta = sh.rp_per_cta;
     L.grid = sh.grid;
+    L.region_items = (sh.rp_per_cta == 0 && region_frames(t->W, t->H)) ? 1 : 0;
     return L;
 }
 

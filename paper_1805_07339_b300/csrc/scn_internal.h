@@ -60,6 +60,7 @@ constexpr int kStatusTimeout = 1;
 // Histogram kernel geometry (fixed at compile time).
 constexpr int kConsumerWarps = 20;                        // warps that load, convert + count
 constexpr int kHistThreads = (kConsumerWarps + 2) * 32;  // + a producer warp (work descriptors) + a publisher warp
+constexpr int kHistThreadsRg = (kConsumerWarps + 1) * 32;  // region streams: + a publisher warp
 constexpr int kStages = 2;                                // chunk descriptors in flight
 constexpr int kGroupWarps = 4;                            // warps sharing one table region
 constexpr int kRegions = kConsumerWarps / kGroupWarps;
@@ -67,7 +68,7 @@ constexpr int kTabRowsPerRegion = 136;                    // 45 (R) + 39 (G) + 5
 constexpr int kTabBytes = kRegions * kTabRowsPerRegion * 256;
 constexpr int kReductionsPerPixel = 3;                    // one shared-memory count per channel
 constexpr int kSmemLimit = 232448;                        // 227 KB opt-in per CTA
-constexpr int kSmemMisc = 1024;                           // accumulators + barriers + flags
+constexpr int kSmemMisc = 4096;                           // accumulators, chunk descriptors, barriers, flags
 static_assert(kTabBytes + kSmemMisc <= kSmemLimit, "tables fit in shared memory");
 constexpr int kConsumerThreads = kConsumerWarps * 32;
 // Pixels of one work item at most: the table is flushed after every item, and
@@ -76,6 +77,17 @@ constexpr int kConsumerThreads = kConsumerWarps * 32;
 // pixels plus one unit of 32).
 constexpr int64_t kItemPixelsMax = int64_t(1) << 24;
 static_assert(kItemPixelsMax / kConsumerThreads + 2 * 32 < 65536, "16-bit lane counters");
+// Frames of at most this many pixels are counted by the region-stream kernel
+// (queue launches only): each 4-warp table region takes whole items of its own,
+// so an item's flush reads and zeroes one region's table instead of all five
+// (a fifth of the flush traffic per frame; at 640 x 360 the flush is otherwise
+// an eighth of the kernel's shared-memory traffic).  Larger frames stay with
+// the CTA-wide kernel, which streams one frame per SM.  One thread of the
+// counting region counts at most 1/kRegionThreads of an item plus two units.
+constexpr int kRegionThreads = kGroupWarps * 32;
+constexpr int64_t kRegionFramePxMax = int64_t(1) << 20;
+static_assert(kRegionFramePxMax / kRegionThreads + 2 * 32 < 65536, "16-bit lane counters (region streams)");
+inline bool region_frames(int W, int H) { return static_cast<int64_t>(W) * H <= kRegionFramePxMax; }
 
 }  // namespace scn
 
@@ -135,6 +147,8 @@ struct Job {
     int32_t items_per_frame;
     int32_t wv, sp, sc;    // 16-byte columns per row; consumer threads / wv; consumer threads % wv
     uint32_t dY, dU;       // luma / chroma byte step per consumer-thread stride of units
+    int32_t sc_r;          // the same for one table region's threads (region-stream kernel)
+    uint32_t dY_r, dU_r;
     float inv_wv;          // 1 / wv
 };
 
@@ -160,7 +174,10 @@ struct Launch {
     const int32_t* d_count = nullptr;
     int32_t count_mul = 0;
     uint64_t wait_limit_ns = 0;   // bounded waits give up after this long (0: 2 s)
-    int32_t withhold_after = -1;  // test hook, >= 0: each producer stops after this many chunks
+    int32_t withhold_after = -1;  // test hook, >= 0: each producer (each table region with region
+                                  // streams) stops after this many chunks
+    int32_t region_items = 0;     // 1: the region-stream kernel (queue launches of frames up to
+                                  // kRegionFramePxMax pixels), 0: the CTA-wide kernel
 };
 
 // Luma rows per work descriptor: the requested even count, or (0) the whole

@@ -45,7 +45,11 @@ scn_status build_items(scn_plan* p) {
     const int64_t item_px = p->tune.item_kpx > 0 ? static_cast<int64_t>(p->tune.item_kpx) * 1000 : kPlanItemPixelsAuto;
     p->jobs.assign(p->seqs.size(), Job{});
     int64_t total_frames = 0;
-    for (scn_seq* s : p->seqs) total_frames += s->n;
+    bool region = true;  // every frame small enough for the region-stream kernel
+    for (scn_seq* s : p->seqs) {
+        total_frames += s->n;
+        region = region && region_frames(s->table->W, s->table->H);
+    }
     // too few items for the CTAs: split frames further
     int64_t px_target = item_px;
     for (size_t j = 0; j < p->seqs.size(); ++j) {
@@ -73,7 +77,7 @@ scn_status build_items(scn_plan* p) {
             items += J.n * J.items_per_frame;
         }
         p->n_items = items;
-        if (items >= 8LL * grid_req || total_frames == 0 || px_target <= 65536) break;
+        if (items >= 8LL * grid_req * (region ? kRegions : 1) || total_frames == 0 || px_target <= 65536) break;
         px_target = std::max<int64_t>(65536, px_target / 2);
     }
     // items: largest frames first (their items are the longest), in element order per sequence
@@ -128,6 +132,9 @@ Launch plan_launch(const scn_plan* p) {
     L.queue = reinterpret_cast<uint32_t*>(static_cast<char*>(p->d_block) + 64);
     L.status = static_cast<int*>(p->d_block);
     L.grid = p->grid;
+    bool region = true;
+    for (const scn_seq* s : p->seqs) region = region && region_frames(s->table->W, s->table->H);
+    L.region_items = region ? 1 : 0;
     return L;
 }
 

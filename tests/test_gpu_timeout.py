@@ -34,11 +34,12 @@ def _run(scn, seq, n):
 
 
 @pytest.mark.parametrize("W,H,T,tune,withhold", [
-    (1920, 1080, 12, None, 0),               # row-pair ranges per CTA, nothing handed out
-    (1920, 1080, 12, None, 1),               # each CTA counts its range (frames split over CTAs), then waits
-    # work queue: 240 items of 15 row pairs in chunks of 4 row pairs (4 chunks an item)
+    (1920, 1080, 12, None, 0),               # row-pair ranges per table region, nothing handed out
+    (1920, 1080, 12, None, 1),               # each region counts its range (frames split over CTAs), then waits
+    # work queue: 240 items of 15 row pairs in chunks of 4 row pairs (4 chunks an item), at
+    # most one item per table region
     (320, 180, 40, dict(item_kpx=10, chunk_rows=8), 2),
-    (320, 180, 40, dict(item_kpx=10, chunk_rows=8), 5),
+    (320, 180, 40, dict(item_kpx=10, chunk_rows=8), 3),
 ])
 def test_withheld_work_times_out_and_the_next_call_is_exact(scn, orc, W, H, T, tune, withhold):
     frames = random_nv12(100 + withhold, T, W, H)
