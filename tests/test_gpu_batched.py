@@ -120,6 +120,29 @@ def test_plan_small_mixed_against_oracle(scn, orc):
         b.close()
 
 
+def test_plan_of_small_frames_against_oracle(scn, orc):
+    """A plan whose frames are all at most 1 Mpx runs the region-stream kernel
+    (each table region counts whole items of its own); every element of every
+    video against the oracle, twice (the plan's queue resets itself)."""
+    res = [(320, 180), (640, 360), (1280, 720)]
+    spec = batched_spec(nvideos=9, min_len=20, max_len=60, seed=23, resolutions=res)
+    b = Batch(scn, spec)
+    try:
+        p = b.plan()
+        for _ in range(2):
+            scn.scn_plan_run(p)
+            assert scn.scn_plan_sync_status(p) == scn.SCN_OK
+            got = b.results()
+            for v, g in zip(spec, got):
+                _properties(v, g)
+                n = len(v["frames"])
+                if n:
+                    _oracle_check(orc, v, g, list(range(n)))
+        scn.scn_plan_destroy(p)
+    finally:
+        b.close()
+
+
 def test_plan_matches_single_sequences_and_graph_replay(scn):
     spec = batched_spec(nvideos=16, min_len=40, max_len=160, seed=5)
     b = Batch(scn, spec)

@@ -175,6 +175,34 @@ def test_hist_launch_shapes_agree(scn, orc, tune):
         dev.close()
 
 
+@pytest.mark.parametrize("W,H,n,tune", [
+    (16, 2, 9, dict(item_kpx=1)),                       # 32-pixel frames, one item each
+    (48, 6, 5, dict(item_kpx=1, chunk_rows=2)),
+    (336, 200, 17, dict(item_kpx=20, chunk_rows=6)),    # frames split into items, items into chunks
+    (640, 360, 40, dict(item_kpx=230)),                 # whole frames, more items than one CTA's regions
+    (640, 360, 40, dict(item_kpx=50, grid=1)),          # one CTA: its five regions share the queue
+    (640, 360, 40, dict(item_kpx=50, grid=3, chunk_rows=10)),
+    (1280, 720, 7, dict(item_kpx=1000)),                # the largest frames counted by region streams
+    (1280, 720, 7, dict(item_kpx=100, grid=2)),
+])
+def test_region_stream_kernel_bit_exact(scn, orc, W, H, n, tune):
+    """Queue launches of frames up to 1 Mpx run the region-stream kernel (each
+    4-warp table region counts whole items of its own): bit-exact against the
+    oracle whatever the item, chunk and grid shapes, and again on a second call
+    (the queue and the cross-CTA counters reset themselves)."""
+    frames = random_nv12(W * 5 + H + n, n, W, H)
+    dev = Dev(scn, torch.from_numpy(frames.reshape(-1)).cuda(), W, H, n)
+    try:
+        seq = dev.seq(scn.SCN_RANGE, start=0, stop=n)
+        rh, rs, rf = _oracle_hs(orc, frames, W, H, np.arange(n))
+        for _ in range(2):
+            h, s, f = dev.hist_scores(seq, tune=tune)
+            assert np.array_equal(h, rh) and np.array_equal(s, rs) and np.array_equal(f, rf)
+        scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+
+
 def test_edge_cases(scn, orc):
     W, H, T = 64, 36, 6
     frames = random_nv12(5, T, W, H)
