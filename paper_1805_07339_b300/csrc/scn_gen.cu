@@ -56,6 +56,13 @@ struct FloorStep {
             --q;
         }
     }
+    // the same when |d| <= W: at most one wrap, no loop (selects only)
+    __device__ __forceinline__ void step1(int d, int W) {
+        r += d;
+        const bool up = r >= W, down = r < 0;
+        r += up ? -W : (down ? W : 0);
+        q += up ? 1 : (down ? -1 : 0);
+    }
 };
 
 __device__ __forceinline__ int floordiv_pos(int a, int b) {
@@ -102,12 +109,22 @@ __device__ __forceinline__ uint4 gen_vector(const GenArgs& a, int64_t f, const s
         FloorStep rx;
         rx.init(sh.gx[0] * (x0 - dt), a.W);
         const int gx = sh.gx[0];
+        if (abs(gx) <= a.W) {  // every frame of 32 columns or more (|gx| <= 32)
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int v = base + rx.q + noise_from_counter(c);
-            b[i] = static_cast<uint8_t>(min(max(v, 16), 235));
-            c += 2 * kGolden;
-            rx.step(gx, a.W);
+            for (int i = 0; i < 16; ++i) {
+                const int v = base + rx.q + noise_from_counter(c);
+                b[i] = static_cast<uint8_t>(min(max(v, 16), 235));
+                c += 2 * kGolden;
+                rx.step1(gx, a.W);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int v = base + rx.q + noise_from_counter(c);
+                b[i] = static_cast<uint8_t>(min(max(v, 16), 235));
+                c += 2 * kGolden;
+                rx.step(gx, a.W);
+            }
         }
     } else {
         const int cy = row - a.H;
@@ -124,14 +141,27 @@ __device__ __forceinline__ uint4 gen_vector(const GenArgs& a, int64_t f, const s
             base[pl - 1] = sh.base[pl] + floordiv_pos(sh.gy[pl] * (2 * cy), a.H);
             gx2[pl - 1] = 2 * sh.gx[pl];
         }
+        if (abs(gx2[0]) <= a.W && abs(gx2[1]) <= a.W) {  // every frame of 64 columns or more
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < 8; ++j) {
 #pragma unroll
-            for (int pl = 0; pl < 2; ++pl) {
-                const int v = base[pl] + rx[pl].q + noise_from_counter(c[pl]);
-                b[2 * j + pl] = static_cast<uint8_t>(min(max(v, 16), 240));
-                c[pl] += 2 * kGolden;
-                rx[pl].step(gx2[pl], a.W);
+                for (int pl = 0; pl < 2; ++pl) {
+                    const int v = base[pl] + rx[pl].q + noise_from_counter(c[pl]);
+                    b[2 * j + pl] = static_cast<uint8_t>(min(max(v, 16), 240));
+                    c[pl] += 2 * kGolden;
+                    rx[pl].step1(gx2[pl], a.W);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+#pragma unroll
+                for (int pl = 0; pl < 2; ++pl) {
+                    const int v = base[pl] + rx[pl].q + noise_from_counter(c[pl]);
+                    b[2 * j + pl] = static_cast<uint8_t>(min(max(v, 16), 240));
+                    c[pl] += 2 * kGolden;
+                    rx[pl].step(gx2[pl], a.W);
+                }
             }
         }
     }
