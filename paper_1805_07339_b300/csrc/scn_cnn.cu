@@ -550,6 +550,10 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kPpBar + kPpNBar * 8);
     uint8_t* X1 = smem + kPpX1;
     const uint32_t sbase = ptx::smem_u32(smem);
+    // launched behind the previous kernel of the stream (thumbnails, list): wait for it
+    // before the first global read; the next kernel may be scheduled from here on
+    ptx::pdl_wait();
+    ptx::pdl_release();
 
     // ---- once: weights, biases, zeroed activation buffers, barriers, TMEM
     for (int e = tid; e < 16 * 4; e += kPpThreads) {  // W1: 16 rows x 4 entries
@@ -959,8 +963,7 @@ scn_status launch_forward_fused(Net* n, const uint8_t* thumbs, const int32_t* pr
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
     const int grid = static_cast<int>(std::min<int64_t>(nbatch, static_cast<int64_t>(sms)));
-    cnn_forward_pipe<<<grid, kPpThreads, kPpSmem, st>>>(a);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(cnn_forward_pipe, dim3(grid), dim3(kPpThreads), kPpSmem, st, a));
     return SCN_OK;
 }
 

@@ -506,8 +506,10 @@ __device__ __forceinline__ void write_score(const Job& J, int64_t k, uint32_t h0
     if (lane < 16) d += (h1 > p1 ? h1 - p1 : p1 - h1);
     const uint32_t s = __reduce_add_sync(0xffffffffu, d);
     if (lane == 0) {
-        J.score[k] = s;
-        J.flag[k] = (2ull * s > static_cast<uint64_t>(J.W) * J.H) ? 1 : 0;
+        // a gated pass (score_at set) writes the score of its pair (2i, 2i+1) to element score_at[i]
+        const int64_t o = J.score_at ? J.score_at[k >> 1] : k;
+        J.score[o] = s;
+        J.flag[o] = (2ull * s > static_cast<uint64_t>(J.W) * J.H) ? 1 : 0;
     }
 }
 
@@ -539,12 +541,15 @@ __device__ void publish(const Job& J, int64_t n, int64_t k, int seg_rp, uint32_t
     if (!J.score) return;
     __threadfence();
     __syncwarp();
+    // a gated pass needs only the scores of its pairs (2i, 2i+1): the odd elements
+    const bool any_k = !J.score_at || (k & 1);
+    const bool any_k1 = !J.score_at || !(k & 1);
     if (k == 0) {
-        if (lane == 0) {
+        if (lane == 0 && !J.score_at) {
             J.score[0] = 0;
             J.flag[0] = 0;
         }
-    } else {
+    } else if (any_k) {
         uint32_t old = 0;
         if (lane == 0) old = atomicAdd(&J.pair[k], 1u);
         old = __shfl_sync(0xffffffffu, old, 0);
@@ -554,7 +559,7 @@ __device__ void publish(const Job& J, int64_t n, int64_t k, int seg_rp, uint32_t
             if (lane == 0) J.pair[k] = 0;
         }
     }
-    if (k + 1 < n) {
+    if (k + 1 < n && any_k1) {
         uint32_t old = 0;
         if (lane == 0) old = atomicAdd(&J.pair[k + 1], 1u);
         old = __shfl_sync(0xffffffffu, old, 0);
@@ -740,6 +745,10 @@ __global__ void __launch_bounds__(kHistThreads, 1) hist_kernel(const __grid_cons
         *s.abort_flag = 0;
         ptx::fence_mbar_init();
     }
+    // the table is zeroed and the barriers set up while the previous kernel in the
+    // stream may still be finishing; global memory only after it has completed
+    ptx::pdl_wait();
+    ptx::pdl_release();
     __syncthreads();
     if (warp == kConsumerWarps) {
         if (lane == 0) produce(L, s);
@@ -972,6 +981,8 @@ __global__ void __launch_bounds__(kHistThreadsRg, 1) hist_kernel_rg(const __grid
         *s.abort_flag = 0;
         ptx::fence_mbar_init();
     }
+    ptx::pdl_wait();
+    ptx::pdl_release();
     __syncthreads();
     if (warp == kConsumerWarps) {
         publisher_rg(L, s, lane);
@@ -1064,10 +1075,9 @@ scn_status launch_hist(const Launch& L, cudaStream_t st) {
     const scn_status sp = prepare_hist();
     if (sp != SCN_OK) return sp;
     if (L.region_items)
-        hist_kernel_rg<<<L.grid, kHistThreadsRg, smem, st>>>(L);
+        SCN_CUDA_TRY(launch_pdl(hist_kernel_rg, dim3(L.grid), dim3(kHistThreadsRg), smem, st, L));
     else
-        hist_kernel<<<L.grid, kHistThreads, smem, st>>>(L);
-    SCN_CUDA_TRY(cudaGetLastError());
+        SCN_CUDA_TRY(launch_pdl(hist_kernel, dim3(L.grid), dim3(kHistThreads), smem, st, L));
     return SCN_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <utility>
 #include <vector>
 
 #include "../../include/scn.h"
@@ -24,6 +25,26 @@ void set_cuda_error(cudaError_t e);
     } while (0)
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Launch with programmatic stream serialization: the grid may be scheduled
+// while the previous kernel in the stream is still finishing, so the launch
+// latency overlaps it.  Only kernels that call ptx::pdl_wait() before their
+// first global memory access are launched this way.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Runs set() once per device for the current device: `done` holds one bit per
 // device (at most 64).  Safe from several host threads on different devices;
@@ -140,6 +161,8 @@ struct Job {
     uint32_t* partial;     // [n][48] cross-CTA accumulators (left zero)
     uint32_t* done;        // [n] counted row pairs (left zero)
     uint32_t* pair;        // [n] score stencil arrivals (left zero)
+    const int32_t* score_at;  // null: score[k], flag[k] for every k; else only odd k, written to
+                              // score[score_at[k / 2]], flag[score_at[k / 2]] (the pairs of a gated pass)
     int64_t n;
     int32_t W, H;
     int32_t chunk_rows;    // luma rows per staged chunk (even)
@@ -214,6 +237,9 @@ int device_sm_count();
 scn_status cnn_forward_counted(scn_cnn* c, const uint8_t* d_thumbs, const int32_t* d_prev, const int32_t* d_cur,
                                int64_t max_pairs, const int* d_pairs, float* d_logits, cudaStream_t st,
                                const int32_t* d_out_index);
+// Luma (d_thumb) and/or coarse YUV (d_yuv) thumbnails of every element, as
+// scn_thumbs_yuv, and *zero = 0 when zero is given (scn_resize.cu).
+scn_status launch_thumbs(const scn_seq* s, uint8_t* d_thumb, uint8_t* d_yuv, int* zero, cudaStream_t st);
 // Luma thumbnails of both frames of listed pairs i < *count (sequence elements
 // prev[i], cur[i]) into out[element] (scn_resize.cu); max_pairs bounds *count.
 scn_status launch_thumbs_listed(const scn_seq* s, const int32_t* prev, const int32_t* cur, const int* count,

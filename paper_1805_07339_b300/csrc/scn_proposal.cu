@@ -6,7 +6,9 @@
 //
 // Steps: proposals, compacted into a list of proposed elements k (pair k-1, k)
 // with the storage slots of both frames of each -> one launch of the fused
-// kernel over that 2m-element sequence -> scatter of each pair's score.
+// kernel over that 2m-element sequence, which writes each pair's score and flag
+// to its element.  The kernels of a pass are launched as programmatic
+// dependents of one another, so each one's launch overlaps its predecessor's end.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -14,6 +16,7 @@
 #include <new>
 
 #include "scn_internal.h"
+#include "scn_ptx.cuh"
 
 namespace scn {
 namespace {
@@ -25,8 +28,6 @@ struct GateWs {
     int32_t* list = nullptr;  // [cap] proposed elements
     int32_t* slots2 = nullptr;  // [2 cap]
     uint32_t* hist2 = nullptr;  // [2 cap][48]
-    uint32_t* score2 = nullptr;
-    uint8_t* flag2 = nullptr;
     uint32_t* partial = nullptr;  // [2 cap][48] (left zero)
     uint32_t* done = nullptr;
     uint32_t* pair = nullptr;
@@ -46,6 +47,8 @@ struct GateWs {
 // gate and the exact pass.
 __global__ void propose_kernel(const float* gate, int64_t n, float tau, uint8_t* proposed, int32_t* list, int* count,
                                uint32_t* score, uint8_t* flag, const int32_t* slot, int32_t* slots2) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
          k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const bool p = k >= 1 && gate[k] > tau;
@@ -59,15 +62,6 @@ __global__ void propose_kernel(const float* gate, int64_t n, float tau, uint8_t*
             slots2[2 * i + 1] = slot[k];
         }
     }
-}
-
-__global__ void scatter_scores(const int32_t* list, const int* count, const uint32_t* score2, const uint8_t* flag2,
-                               uint32_t* score, uint8_t* flag) {
-    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= *count) return;
-    const int32_t k = list[i];
-    score[k] = score2[2 * i + 1];
-    flag[k] = flag2[2 * i + 1];
 }
 
 // Sum of |thumb[k] - thumb[k-1]| over the 2304 samples (0 for k = 0), by one
@@ -116,6 +110,8 @@ constexpr int kDiffWarps = 8;  // frames per 256-thread block, one warp each
 // the luma gate (thumbs given) or the luma + chroma gate (yuv given) of every element (0 for k = 0)
 __global__ void __launch_bounds__(32 * kDiffWarps) thumb_diff_kernel(const uint8_t* thumbs, const uint8_t* yuv,
                                                                      int64_t n, float* diff) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     const int64_t k = blockIdx.x * static_cast<int64_t>(kDiffWarps) + (threadIdx.x >> 5);
     if (k >= n) return;
     const int lane = threadIdx.x & 31;
@@ -130,7 +126,11 @@ __global__ void __launch_bounds__(32 * kDiffWarps) thumb_diff_kernel(const uint8
 __global__ void __launch_bounds__(32 * kDiffWarps) diff_prefilter_kernel(const uint8_t* yuv, int64_t n,
                                                                          float tau_diff, float* diff, float* gate,
                                                                          int32_t* prev, int32_t* cur, int32_t* elem,
-                                                                         int* count) {
+                                                                         int* count, int* zero) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
+    // the proposal list's counter, appended to by the gate after the network
+    if (blockIdx.x == 0 && threadIdx.x == 0) *zero = 0;
     const int64_t k = blockIdx.x * static_cast<int64_t>(kDiffWarps) + (threadIdx.x >> 5);
     if (k >= n) return;
     const float dk = yuv_gate(yuv, k, threadIdx.x & 31);
@@ -158,9 +158,8 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
     if (!ws) return SCN_ENOMEM;
     const int64_t c = std::max<int64_t>(s->n, 1);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t parts[] = {up(c * 4), up(2 * c * 4), up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c),
-                            up(2 * c * 48 * 4), up(2 * c * 4), up(2 * c * 4), 256, 256, 256,
-                            up(c * 4), up(c * 4), up(c * 4), 256};
+    const size_t parts[] = {up(c * 4), up(2 * c * 4), up(2 * c * 48 * 4), up(2 * c * 48 * 4), up(2 * c * 4),
+                            up(2 * c * 4), 256, 256, 256, up(c * 4), up(c * 4), up(c * 4), 256};
     size_t total = 0;
     for (size_t p : parts) total += p;
     cudaError_t e = obj_alloc(&ws->block, total);
@@ -175,8 +174,7 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
     }
     char* p = static_cast<char*>(ws->block);
     void** dst[] = {reinterpret_cast<void**>(&ws->list),    reinterpret_cast<void**>(&ws->slots2),
-                    reinterpret_cast<void**>(&ws->hist2),   reinterpret_cast<void**>(&ws->score2),
-                    reinterpret_cast<void**>(&ws->flag2),   reinterpret_cast<void**>(&ws->partial),
+                    reinterpret_cast<void**>(&ws->hist2),   reinterpret_cast<void**>(&ws->partial),
                     reinterpret_cast<void**>(&ws->done),    reinterpret_cast<void**>(&ws->pair),
                     reinterpret_cast<void**>(&ws->queue),   reinterpret_cast<void**>(&ws->status),
                     reinterpret_cast<void**>(&ws->count),   reinterpret_cast<void**>(&ws->pre_prev),
@@ -190,6 +188,62 @@ scn_status ensure_ws(scn_seq* s, GateWs*& ws) {
     ws->cap = c;
     ws->bytes = total;
     s->gate_ws = ws;
+    return SCN_OK;
+}
+
+// The gate, then the exact kernel on the proposed pairs.  count_zeroed: an
+// earlier kernel of the same pass has already zeroed the list's counter.
+scn_status gated_hist(scn_seq* s, const float* d_gate, float tau, uint8_t* d_proposed, uint32_t* d_score,
+                      uint8_t* d_flag, int64_t* h_nproposed, cudaStream_t cs, bool count_zeroed) {
+    if (!s || !d_gate || !d_proposed || !d_score || !d_flag) return SCN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_score) & 3u) return SCN_EINVAL;
+    if (h_nproposed) *h_nproposed = 0;
+    if (s->n == 0) return SCN_OK;
+    GateWs* ws = nullptr;
+    scn_status st = ensure_ws(s, ws);
+    if (st != SCN_OK) return st;
+    if (!count_zeroed) SCN_CUDA_TRY(cudaMemsetAsync(ws->count, 0, sizeof(int), cs));
+    const int64_t blocks = std::min<int64_t>((s->n + 255) / 256, 148 * 8);
+    SCN_CUDA_TRY(launch_pdl(propose_kernel, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, cs, d_gate, s->n, tau,
+                            d_proposed, ws->list, ws->count, d_score, d_flag,
+                            static_cast<const int32_t*>(s->d_slot), ws->slots2));
+    // m = *ws->count stays on the device: the exact launch is sized for the
+    // largest m (n - 1 pairs) and reads m itself
+    const int64_t cap = s->n;
+    // the exact kernel over the 2m frames of the proposed pairs: one contiguous
+    // range of row pairs per CTA, each CTA computing its range from m on the device;
+    // the score of pair i (elements 2i, 2i + 1) goes straight to element list[i]
+    scn_seq q;
+    q.table = s->table;
+    q.n = 2 * cap;
+    q.tune = s->tune;
+    HistShape sh = resolve_hist_shape(&q);
+    const int W = s->table->W, H = s->table->H;
+    int sms = device_sm_count();
+    if (sms <= 0) sms = 148;
+    sh.grid = s->tune.grid > 0 ? s->tune.grid : sms;
+    sh.rp_per_cta = -1;
+    sh.item_rp = static_cast<int>(std::min<int64_t>(H / 2, std::max<int64_t>(1, kItemPixelsMax / (2LL * W))));
+    Launch L = single_launch(s->table, q.n, ws->slots2, sh);
+    L.d_count = ws->count;
+    L.count_mul = 2;
+    L.job0.hist = ws->hist2;
+    L.job0.score = d_score;
+    L.job0.flag = d_flag;
+    L.job0.score_at = ws->list;
+    L.job0.partial = ws->partial;
+    L.job0.done = ws->done;
+    L.job0.pair = ws->pair;
+    L.queue = ws->queue;
+    L.status = s->d_status;
+    st = launch_hist(L, cs);
+    if (st != SCN_OK) return st;
+    if (h_nproposed) {  // the only host wait, at the end and only when asked for
+        int m = 0;
+        SCN_CUDA_TRY(cudaMemcpyAsync(&m, ws->count, sizeof(int), cudaMemcpyDeviceToHost, cs));
+        SCN_CUDA_TRY(cudaStreamSynchronize(cs));
+        *h_nproposed = m;
+    }
     return SCN_OK;
 }
 
@@ -221,9 +275,9 @@ scn_status scn_thumb_diff(const uint8_t* d_thumbs, int64_t n, float* d_diff, voi
     if (n == 0) return SCN_OK;
     if (!d_thumbs || !d_diff || (reinterpret_cast<uintptr_t>(d_thumbs) & 3u)) return SCN_EINVAL;
     if (n > 0x7fffffff) return SCN_ERANGE;
-    thumb_diff_kernel<<<static_cast<unsigned>((n + kDiffWarps - 1) / kDiffWarps), 32 * kDiffWarps, 0,
-                        static_cast<cudaStream_t>(stream)>>>(d_thumbs, nullptr, n, d_diff);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(thumb_diff_kernel, dim3(static_cast<unsigned>((n + kDiffWarps - 1) / kDiffWarps)),
+                            dim3(32 * kDiffWarps), 0, static_cast<cudaStream_t>(stream), static_cast<const uint8_t*>(d_thumbs),
+                            static_cast<const uint8_t*>(nullptr), n, d_diff));
     return SCN_OK;
 }
 
@@ -232,66 +286,16 @@ scn_status scn_thumb_diff_yuv(const uint8_t* d_yuv, int64_t n, float* d_diff, vo
     if (n == 0) return SCN_OK;
     if (!d_yuv || !d_diff || (reinterpret_cast<uintptr_t>(d_yuv) & 15u)) return SCN_EINVAL;
     if (n > 0x7fffffff) return SCN_ERANGE;
-    thumb_diff_kernel<<<static_cast<unsigned>((n + kDiffWarps - 1) / kDiffWarps), 32 * kDiffWarps, 0,
-                        static_cast<cudaStream_t>(stream)>>>(nullptr, d_yuv, n, d_diff);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(thumb_diff_kernel, dim3(static_cast<unsigned>((n + kDiffWarps - 1) / kDiffWarps)),
+                            dim3(32 * kDiffWarps), 0, static_cast<cudaStream_t>(stream), static_cast<const uint8_t*>(nullptr),
+                            static_cast<const uint8_t*>(d_yuv), n, d_diff));
     return SCN_OK;
 }
 
 scn_status scn_gated_hist_scores(scn_seq* s, const float* d_gate, float tau, uint8_t* d_proposed, uint32_t* d_score,
                                  uint8_t* d_flag, int64_t* h_nproposed, void* stream) {
-    if (!s || !d_gate || !d_proposed || !d_score || !d_flag) return SCN_EINVAL;
-    if (reinterpret_cast<uintptr_t>(d_score) & 3u) return SCN_EINVAL;
-    if (h_nproposed) *h_nproposed = 0;
-    if (s->n == 0) return SCN_OK;
-    GateWs* ws = nullptr;
-    scn_status st = ensure_ws(s, ws);
-    if (st != SCN_OK) return st;
-    cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    SCN_CUDA_TRY(cudaMemsetAsync(ws->count, 0, sizeof(int), cs));
-    const int64_t blocks = std::min<int64_t>((s->n + 255) / 256, 148 * 8);
-    propose_kernel<<<static_cast<unsigned>(blocks), 256, 0, cs>>>(d_gate, s->n, tau, d_proposed, ws->list, ws->count,
-                                                                  d_score, d_flag, s->d_slot, ws->slots2);
-    SCN_CUDA_TRY(cudaGetLastError());
-    // m = *ws->count stays on the device: every later launch is sized for the
-    // largest m (n - 1 pairs) and reads m itself
-    const int64_t cap = s->n;
-    const unsigned pblocks = static_cast<unsigned>((cap + 255) / 256);
-    // the exact kernel over the 2m frames of the proposed pairs: one contiguous
-    // range of row pairs per CTA, each CTA computing its range from m on the device
-    scn_seq q;
-    q.table = s->table;
-    q.n = 2 * cap;
-    q.tune = s->tune;
-    HistShape sh = resolve_hist_shape(&q);
-    const int W = s->table->W, H = s->table->H;
-    int sms = device_sm_count();
-    if (sms <= 0) sms = 148;
-    sh.grid = s->tune.grid > 0 ? s->tune.grid : sms;
-    sh.rp_per_cta = -1;
-    sh.item_rp = static_cast<int>(std::min<int64_t>(H / 2, std::max<int64_t>(1, kItemPixelsMax / (2LL * W))));
-    Launch L = single_launch(s->table, q.n, ws->slots2, sh);
-    L.d_count = ws->count;
-    L.count_mul = 2;
-    L.job0.hist = ws->hist2;
-    L.job0.score = ws->score2;
-    L.job0.flag = ws->flag2;
-    L.job0.partial = ws->partial;
-    L.job0.done = ws->done;
-    L.job0.pair = ws->pair;
-    L.queue = ws->queue;
-    L.status = s->d_status;
-    st = launch_hist(L, cs);
-    if (st != SCN_OK) return st;
-    scatter_scores<<<pblocks, 256, 0, cs>>>(ws->list, ws->count, ws->score2, ws->flag2, d_score, d_flag);
-    SCN_CUDA_TRY(cudaGetLastError());
-    if (h_nproposed) {  // the only host wait, at the end and only when asked for
-        int m = 0;
-        SCN_CUDA_TRY(cudaMemcpyAsync(&m, ws->count, sizeof(int), cudaMemcpyDeviceToHost, cs));
-        SCN_CUDA_TRY(cudaStreamSynchronize(cs));
-        *h_nproposed = m;
-    }
-    return SCN_OK;
+    return gated_hist(s, d_gate, tau, d_proposed, d_score, d_flag, h_nproposed, static_cast<cudaStream_t>(stream),
+                      false);
 }
 
 scn_status scn_proposal_hist_scores(scn_seq* s, scn_cnn* net, float tau, uint8_t* d_thumbs, float* d_logits,
@@ -300,14 +304,19 @@ scn_status scn_proposal_hist_scores(scn_seq* s, scn_cnn* net, float tau, uint8_t
     if (!s || !net || !d_thumbs || !d_logits) return SCN_EINVAL;
     if (h_nproposed) *h_nproposed = 0;
     if (s->n == 0) return SCN_OK;
-    scn_status st = scn_thumbs(s, d_thumbs, stream);
+    GateWs* ws = nullptr;
+    scn_status st = ensure_ws(s, ws);
+    if (st != SCN_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    // the thumbnail launch also zeroes the proposal list's counter
+    st = launch_thumbs(s, d_thumbs, nullptr, ws->count, cs);
     if (st != SCN_OK) return st;
     if (s->n > 1) {
         // pair (k-1, k) -> logit k
         st = scn_cnn_forward(net, d_thumbs, nullptr, nullptr, s->n - 1, d_logits + 1, stream);
         if (st != SCN_OK) return st;
     }
-    return scn_gated_hist_scores(s, d_logits, tau, d_proposed, d_score, d_flag, h_nproposed, stream);
+    return gated_hist(s, d_logits, tau, d_proposed, d_score, d_flag, h_nproposed, cs, true);
 }
 
 
@@ -325,13 +334,13 @@ scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, flo
     scn_status st = ensure_ws(s, ws);
     if (st != SCN_OK) return st;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    // coarse YUV thumbnails of every frame (the gate's input), not the luma thumbnails
-    st = scn_thumbs_yuv(s, nullptr, d_yuv, stream);
+    // coarse YUV thumbnails of every frame (the gate's input), not the luma thumbnails;
+    // the launch zeroes the prefilter's counter, the prefilter the proposal list's
+    st = launch_thumbs(s, nullptr, d_yuv, ws->pre_count, cs);
     if (st != SCN_OK) return st;
-    SCN_CUDA_TRY(cudaMemsetAsync(ws->pre_count, 0, sizeof(int), cs));
-    diff_prefilter_kernel<<<static_cast<unsigned>((s->n + kDiffWarps - 1) / kDiffWarps), 32 * kDiffWarps, 0, cs>>>(
-        d_yuv, s->n, tau_diff, d_diff, d_gate, ws->pre_prev, ws->pre_cur, ws->pre_elem, ws->pre_count);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(diff_prefilter_kernel, dim3(static_cast<unsigned>((s->n + kDiffWarps - 1) / kDiffWarps)),
+                            dim3(32 * kDiffWarps), 0, cs, static_cast<const uint8_t*>(d_yuv), s->n, tau_diff, d_diff,
+                            d_gate, ws->pre_prev, ws->pre_cur, ws->pre_elem, ws->pre_count, ws->count));
     if (s->n > 1) {
         // luma thumbnails only for the frames of the listed pairs: what the network reads
         st = launch_thumbs_listed(s, ws->pre_prev, ws->pre_cur, ws->pre_count, s->n - 1, d_thumbs, cs);
@@ -342,7 +351,7 @@ scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, flo
                                  ws->pre_elem);
         if (st != SCN_OK) return st;
     }
-    return scn_gated_hist_scores(s, d_gate, tau_net, d_proposed, d_score, d_flag, h_nproposed, stream);
+    return gated_hist(s, d_gate, tau_net, d_proposed, d_score, d_flag, h_nproposed, cs, true);
 }
 
 }  // extern "C"

@@ -1,5 +1,5 @@
 // Thin inline-PTX wrappers used by the kernels (mbarrier, byte dot products,
-// byte permute, bounded waits).
+// byte permute, bounded waits, dependent-launch control).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -92,6 +92,15 @@ __device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p) {
 __device__ __forceinline__ void named_bar_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
+
+// Programmatic dependent launch.  pdl_wait: block until the grids this launch
+// depends on have completed and their memory is visible (returns at once in a
+// launch made without the programmatic-serialization attribute); every thread
+// calls it before its first global memory access.  pdl_release: allow the next
+// launch in the stream to start its grid (it still waits in pdl_wait for this
+// one to complete).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 }  // namespace ptx
 }  // namespace scn

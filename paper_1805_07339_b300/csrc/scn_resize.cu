@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "scn_internal.h"
+#include "scn_ptx.cuh"
 
 namespace scn {
 namespace {
@@ -139,8 +140,14 @@ __device__ __forceinline__ void luma_thumb(const uint8_t* __restrict__ f, int W,
 // thumbnail).
 __global__ void __launch_bounds__(kThumbThreads) thumbs_kernel(const uint8_t* __restrict__ nv12, int64_t stride, int W,
                                                               int H, int s, const int32_t* __restrict__ slot,
-                                                              uint8_t* __restrict__ out, uint8_t* __restrict__ yuv) {
+                                                              uint8_t* __restrict__ out, uint8_t* __restrict__ yuv,
+                                                              int* zero) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     const int k = blockIdx.x;
+    // a counter the next kernels of a proposal pass append to, zeroed here instead of by a
+    // separate memset (every earlier reader of it has completed before pdl_wait returned)
+    if (zero && k == 0 && threadIdx.x == 0) *zero = 0;
     const uint8_t* f = nv12 + static_cast<int64_t>(slot[k]) * stride;
     if (out) luma_thumb(f, W, s, out + static_cast<int64_t>(k) * 2304);
     if (yuv) {
@@ -165,6 +172,8 @@ __global__ void __launch_bounds__(kThumbThreads) thumbs_listed_kernel(const uint
                                                                      const int32_t* __restrict__ cur,
                                                                      const int* __restrict__ count,
                                                                      uint8_t* __restrict__ out) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     const int64_t m2 = 2 * static_cast<int64_t>(*count);
     for (int64_t j = blockIdx.x; j < m2; j += gridDim.x) {
         const int32_t k = (j & 1) ? cur[j >> 1] : prev[j >> 1];
@@ -173,6 +182,18 @@ __global__ void __launch_bounds__(kThumbThreads) thumbs_listed_kernel(const uint
 }
 
 }  // namespace
+
+scn_status launch_thumbs(const scn_seq* s, uint8_t* d_thumb, uint8_t* d_yuv, int* zero, cudaStream_t st) {
+    if (!s || (!d_thumb && !d_yuv)) return SCN_EINVAL;
+    const int W = s->table->W, H = s->table->H;
+    if (W % 64 || H % 36 || W / 64 != H / 36) return SCN_EUNSUPPORTED;
+    if (s->n == 0) return SCN_OK;
+    if (s->n > 0x7fffffff) return SCN_ERANGE;
+    SCN_CUDA_TRY(launch_pdl(thumbs_kernel, dim3(static_cast<unsigned>(s->n)), dim3(kThumbThreads), 0, st,
+                            s->table->d_nv12, s->table->frame_stride, W, H, W / 64,
+                            static_cast<const int32_t*>(s->d_slot), d_thumb, d_yuv, zero));
+    return SCN_OK;
+}
 }  // namespace scn
 
 
@@ -220,9 +241,9 @@ scn_status launch_thumbs_listed(const scn_seq* s, const int32_t* prev, const int
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
     const unsigned grid = static_cast<unsigned>(std::min<int64_t>(2 * max_pairs, 4LL * sms));
-    thumbs_listed_kernel<<<grid, kThumbThreads, 0, st>>>(s->table->d_nv12, s->table->frame_stride, W, W / 64,
-                                                         s->d_slot, prev, cur, count, out);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(thumbs_listed_kernel, dim3(grid), dim3(kThumbThreads), 0, st, s->table->d_nv12,
+                            s->table->frame_stride, W, W / 64, static_cast<const int32_t*>(s->d_slot), prev, cur,
+                            count, out));
     return SCN_OK;
 }
 }  // namespace scn
@@ -248,15 +269,7 @@ scn_status scn_resize_norm_both(scn_seq* s, int32_t oh, int32_t ow, const float*
 }
 
 scn_status scn_thumbs_yuv(scn_seq* s, uint8_t* d_thumb, uint8_t* d_yuv, void* stream) {
-    if (!s || (!d_thumb && !d_yuv)) return SCN_EINVAL;
-    const int W = s->table->W, H = s->table->H;
-    if (W % 64 || H % 36 || W / 64 != H / 36) return SCN_EUNSUPPORTED;
-    if (s->n == 0) return SCN_OK;
-    if (s->n > 0x7fffffff) return SCN_ERANGE;
-    scn::thumbs_kernel<<<static_cast<unsigned>(s->n), scn::kThumbThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-        s->table->d_nv12, s->table->frame_stride, W, H, W / 64, s->d_slot, d_thumb, d_yuv);
-    SCN_CUDA_TRY(cudaGetLastError());
-    return SCN_OK;
+    return scn::launch_thumbs(s, d_thumb, d_yuv, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 scn_status scn_thumbs(scn_seq* s, uint8_t* d_thumb, void* stream) {
