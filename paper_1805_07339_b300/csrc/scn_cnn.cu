@@ -22,6 +22,9 @@
 //    MN-major from the forward's im2col chunks and the rows of dU, the bias
 //    gradient from a column of ones; accumulated in TMEM per CTA.
 //  * head forward/backward, Adam: CUDA cores.
+// Every kernel is launched as a programmatic dependent of the one before it
+// (launch_pdl) and starts with pdl_wait, ahead of any global memory access and
+// TMEM allocation, so a training step's 13 launches overlap one another's ends.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -163,6 +166,8 @@ __device__ __forceinline__ uint4 im2col_chunk(const ConvFwdArgs& a, int64_t b, i
 
 template <int L>
 __global__ void __launch_bounds__(128) conv_fwd_tc(const __grid_constant__ ConvFwdArgs a) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     using S = Shape<L>;
     using M = ConvSmem<L>;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -257,6 +262,8 @@ __global__ void __launch_bounds__(128) conv_fwd_tc(const __grid_constant__ ConvF
 __global__ void __launch_bounds__(256) head_fwd(const __nv_bfloat16* __restrict__ a3, const __nv_bfloat16* f1b,
                                                 const float* c1, const __nv_bfloat16* f2b, const float* c2, float* g_out,
                                                 float* v_out, float* z, int64_t pairs) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     const int lane = threadIdx.x & 31;
     const int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
     if (b >= pairs) return;
@@ -286,6 +293,8 @@ __global__ void __launch_bounds__(256) head_fwd(const __nv_bfloat16* __restrict_
 __global__ void prep_weights(const float* m, __nv_bfloat16* w1b, __nv_bfloat16* w2b, __nv_bfloat16* w3b,
                              __nv_bfloat16* w2t, __nv_bfloat16* w3t, __nv_bfloat16* f1b, __nv_bfloat16* f2b,
                              float* f1t) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     // conv weights W[co][ci][di][dj] -> [co][tap*CIN + ci]
     if (i < 16 * 32) {
@@ -324,8 +333,7 @@ scn_status launch_conv_fwd(const ConvFwdArgs& a, cudaStream_t st) {
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
     const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(sms) * 4));
-    conv_fwd_tc<L><<<grid, 128, ConvSmem<L>::BYTES, st>>>(a);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(conv_fwd_tc<L>, dim3(grid), dim3(128), ConvSmem<L>::BYTES, st, a));
     return SCN_OK;
 }
 
@@ -356,10 +364,9 @@ scn_status forward_chunk(Net* n, const uint8_t* thumbs, const int32_t* prev, con
     s = launch_conv_fwd<3>(a, st);
     if (s != SCN_OK) return s;
     const int64_t blocks = (pairs + 7) / 8;
-    head_fwd<<<static_cast<unsigned>(blocks), 256, 0, st>>>(n->a3, n->f1b, n->master + kC1, n->f2b, n->master + kC2,
-                                                            train ? n->g : nullptr, train ? n->v : nullptr, logits,
-                                                            pairs);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(head_fwd, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, st, n->a3, n->f1b,
+                            n->master + kC1, n->f2b, n->master + kC2, train ? n->g : nullptr,
+                            train ? n->v : nullptr, logits, pairs));
     return SCN_OK;
 }
 
@@ -975,6 +982,8 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ z, con
                                                 const __nv_bfloat16* __restrict__ a3, const __nv_bfloat16* f1b,
                                                 const __nv_bfloat16* f2b, float pos_weight, int64_t pairs,
                                                 float* grad, __nv_bfloat16* du3, float* loss) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     const int lane = threadIdx.x & 31;
     const int64_t w0 = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
@@ -1058,6 +1067,8 @@ struct BwdSmem {
 
 template <int L>
 __global__ void __launch_bounds__(128) conv_bwd_data_tc(const __grid_constant__ ConvBwdArgs a) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     using S = Shape<L>;
     using M = BwdSmem<L>;
     constexpr int NH = S::KP > 144 ? 2 : 1;   // N halves
@@ -1144,6 +1155,8 @@ __global__ void __launch_bounds__(128) conv_bwd_data_tc(const __grid_constant__ 
 template <int L>
 __global__ void col2im_mask(const float* __restrict__ dxcol, const __nv_bfloat16* __restrict__ act,
                             __nv_bfloat16* __restrict__ du_prev, int64_t pairs) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     using S = Shape<L>;
     const int64_t total = pairs * S::HIN * S::WIN * S::CIN;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
@@ -1228,6 +1241,8 @@ __device__ __forceinline__ uint64_t mn_desc(uint32_t saddr, uint32_t mn_stride, 
 
 template <int L>
 __global__ void __launch_bounds__(128) conv_bwd_weight_tc(const __grid_constant__ ConvWgtArgs a) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     using S = Shape<L>;
     using W = WgtTc<L>;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -1338,6 +1353,8 @@ __global__ void __launch_bounds__(128) conv_bwd_weight_tc(const __grid_constant_
 // Adam (bias-corrected), fp32 master weights
 __global__ void adam_update(float* p, float* m, float* v, const float* g, int n, float lr, float b1, float b2,
                             float eps, float c1, float c2) {
+    ptx::pdl_wait();
+    ptx::pdl_release();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -1362,8 +1379,7 @@ scn_status launch_bwd_data(const ConvBwdArgs& a, cudaStream_t st) {
     if (sms <= 0) sms = 148;
     // 256 TMEM columns per CTA: at most 2 CTAs per SM can hold them
     const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(sms) * 2));
-    conv_bwd_data_tc<L><<<grid, 128, BwdSmem<L>::BYTES, st>>>(a);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(conv_bwd_data_tc<L>, dim3(grid), dim3(128), BwdSmem<L>::BYTES, st, a));
     return SCN_OK;
 }
 
@@ -1382,8 +1398,7 @@ scn_status launch_bwd_weight(const ConvWgtArgs& a, cudaStream_t st) {
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
     const int grid = static_cast<int>(std::min<int64_t>(chunks, static_cast<int64_t>(sms)));
-    conv_bwd_weight_tc<L><<<grid, 128, WgtTc<L>::BYTES, st>>>(a);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(conv_bwd_weight_tc<L>, dim3(grid), dim3(128), WgtTc<L>::BYTES, st, a));
     return SCN_OK;
 }
 
@@ -1393,8 +1408,8 @@ scn_status launch_col2im(const float* dxcol, const __nv_bfloat16* act, __nv_bflo
     using S = Shape<L>;
     const int64_t total = pairs * S::HIN * S::WIN * S::CIN;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 8);
-    col2im_mask<L><<<static_cast<unsigned>(blocks), 256, 0, st>>>(dxcol, act, du_prev, pairs);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(
+        launch_pdl(col2im_mask<L>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, st, dxcol, act, du_prev, pairs));
     return SCN_OK;
 }
 
@@ -1406,9 +1421,8 @@ scn_status gradients(Net* n, const uint8_t* thumbs, const int32_t* prev, const i
     scn_status s = forward_chunk(n, thumbs, prev, cur, pairs, n->z, true, st);
     if (s != SCN_OK) return s;
     const int64_t hb = std::min<int64_t>((pairs + 7) / 8, 64);
-    head_bwd<<<static_cast<unsigned>(hb), 256, 0, st>>>(n->z, labels, n->g, n->v, n->a3, n->f1b, n->f2b, pos_weight,
-                                                        pairs, n->grad, n->du3, n->loss);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(head_bwd, dim3(static_cast<unsigned>(hb)), dim3(256), 0, st, n->z, labels, n->g, n->v,
+                            n->a3, n->f1b, n->f2b, pos_weight, pairs, n->grad, n->du3, n->loss));
     // layer 3
     ConvWgtArgs w{};
     w.thumbs = thumbs;
@@ -1449,9 +1463,8 @@ scn_status gradients(Net* n, const uint8_t* thumbs, const int32_t* prev, const i
 }
 
 scn_status prep(Net* n, cudaStream_t st) {
-    prep_weights<<<(32 * 288 + 255) / 256, 256, 0, st>>>(n->master, n->w1b, n->w2b, n->w3b, n->w2t, n->w3t, n->f1b,
-                                                         n->f2b, n->f1t);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(prep_weights, dim3((32 * 288 + 255) / 256), dim3(256), 0, st, n->master, n->w1b, n->w2b,
+                            n->w3b, n->w2t, n->w3t, n->f1b, n->f2b, n->f1t));
     return SCN_OK;
 }
 
@@ -1591,9 +1604,8 @@ scn_status scn_cnn_train_step(scn_cnn* c, const uint8_t* d_thumbs, const int32_t
     n.step += 1;
     const float c1 = 1.f - static_cast<float>(std::pow(0.9, static_cast<double>(n.step)));
     const float c2 = 1.f - static_cast<float>(std::pow(0.999, static_cast<double>(n.step)));
-    adam_update<<<(kNParams + 255) / 256, 256, 0, st>>>(n.master, n.adam_m, n.adam_v, n.grad, kNParams, lr, 0.9f,
-                                                        0.999f, 1e-8f, c1, c2);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(adam_update, dim3((kNParams + 255) / 256), dim3(256), 0, st, n.master, n.adam_m,
+                            n.adam_v, n.grad, kNParams, lr, 0.9f, 0.999f, 1e-8f, c1, c2));
     return prep(&n, st);
 }
 

@@ -66,6 +66,8 @@ __device__ __forceinline__ float small_to_float(int v) { return __int_as_float(v
 constexpr int kRzTile = 32;
 
 __global__ void __launch_bounds__(256) resize_kernel(ResizeArgs a) {
+    ptx::pdl_wait();  // launched as a programmatic dependent: global memory only after the wait
+    ptx::pdl_release();
     __shared__ int2 tap[2 * kRzTile];  // columns, then rows: (first index, weight numerator)
     const int k = blockIdx.z, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ox0 = blockIdx.x * kRzTile, oy0 = blockIdx.y * kRzTile;
@@ -223,8 +225,7 @@ scn_status launch_resize(scn_seq* s, int32_t oh, int32_t ow, const float* h_mean
     a.out32 = out32;
     a.out16 = out16;
     dim3 grid((ow + kRzTile - 1) / kRzTile, (oh + kRzTile - 1) / kRzTile, static_cast<unsigned>(s->n));
-    resize_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(a);
-    SCN_CUDA_TRY(cudaGetLastError());
+    SCN_CUDA_TRY(launch_pdl(resize_kernel, grid, dim3(256), 0, static_cast<cudaStream_t>(stream), a));
     return SCN_OK;
 }
 }  // namespace
