@@ -114,6 +114,9 @@ struct ConvFwdArgs {
     __nv_bfloat16* y;         // NHWC output [pairs][P][COUT]
     int64_t pairs;
     int* status;
+    float* zero;              // non-null: zero[0, nzero) and *zero_one set to 0 by the launch (a training
+    int32_t nzero;            // step's gradient and loss accumulators, ahead of every kernel that adds to them)
+    float* zero_one;
 };
 
 template <int L>
@@ -168,6 +171,10 @@ template <int L>
 __global__ void __launch_bounds__(128) conv_fwd_tc(const __grid_constant__ ConvFwdArgs a) {
     ptx::pdl_wait();
     ptx::pdl_release();
+    if (a.zero) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nzero; i += gridDim.x * blockDim.x) a.zero[i] = 0.f;
+        if (blockIdx.x == 0 && threadIdx.x == 0) *a.zero_one = 0.f;
+    }
     using S = Shape<L>;
     using M = ConvSmem<L>;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -341,6 +348,11 @@ scn_status launch_conv_fwd(const ConvFwdArgs& a, cudaStream_t st) {
 scn_status forward_chunk(Net* n, const uint8_t* thumbs, const int32_t* prev, const int32_t* cur, int64_t pairs,
                          float* logits, bool train, cudaStream_t st) {
     ConvFwdArgs a{};
+    if (train) {  // the gradient and loss accumulators, zeroed by the first launch of the step
+        a.zero = n->grad;
+        a.nzero = kNParams;
+        a.zero_one = n->loss;
+    }
     a.thumbs = thumbs;
     a.prev = prev;
     a.cur = cur;
@@ -351,6 +363,7 @@ scn_status forward_chunk(Net* n, const uint8_t* thumbs, const int32_t* prev, con
     a.y = n->a1;
     scn_status s = launch_conv_fwd<1>(a, st);
     if (s != SCN_OK) return s;
+    a.zero = nullptr;
     a.x = n->a1;
     a.w = n->w2b;
     a.bias = n->master + kB2;
@@ -1416,9 +1429,7 @@ scn_status launch_col2im(const float* dxcol, const __nv_bfloat16* act, __nv_bflo
 // Gradients of the mean loss over one batch into n->grad (oracle layout) and n->loss.
 scn_status gradients(Net* n, const uint8_t* thumbs, const int32_t* prev, const int32_t* cur, const float* labels,
                      int64_t pairs, float pos_weight, cudaStream_t st) {
-    SCN_CUDA_TRY(cudaMemsetAsync(n->grad, 0, kNParams * 4, st));
-    SCN_CUDA_TRY(cudaMemsetAsync(n->loss, 0, 4, st));
-    scn_status s = forward_chunk(n, thumbs, prev, cur, pairs, n->z, true, st);
+    scn_status s = forward_chunk(n, thumbs, prev, cur, pairs, n->z, true, st);  // zeroes grad and loss
     if (s != SCN_OK) return s;
     const int64_t hb = std::min<int64_t>((pairs + 7) / 8, 64);
     SCN_CUDA_TRY(launch_pdl(head_bwd, dim3(static_cast<unsigned>(hb)), dim3(256), 0, st, n->z, labels, n->g, n->v,
