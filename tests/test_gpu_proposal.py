@@ -87,6 +87,63 @@ def test_gate_async_calls_in_a_row(scn, tiny):
         assert int(p.sum()) == int((g_host[1:] > tau).sum())
 
 
+def test_proposal_passes_in_a_row(scn, tiny):
+    """Cascade, learned and gated passes queued back to back on one stream with no host wait
+    (each pass's kernels are dependent launches; the list counters are zeroed inside the
+    thumbnail and prefilter launches): every pass's outputs equal those of the same call made
+    alone, with the device idle before and after it."""
+    from paper_1805_07339_b300.proposal import he_uniform
+    T = tiny["T"]
+    net = scn.scn_cnn_create(64)
+    try:
+        scn.scn_cnn_set_params(net, he_uniform(5))
+        th = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
+        yuv = torch.empty((T, 3, 6, 32), dtype=torch.uint8, device="cuda")
+        d = torch.empty(T, dtype=torch.float32, device="cuda")
+        zz = torch.empty(T - 1, dtype=torch.float32, device="cuda")
+        scn.scn_thumbs_yuv(tiny["seq"], th, yuv)
+        scn.scn_thumb_diff_yuv(yuv, T, d)
+        scn.scn_cnn_forward(net, th, T - 1, zz)
+        dh, zh = d.cpu().numpy(), zz.cpu().numpy()
+        g = torch.from_numpy(np.random.default_rng(9).random(T).astype(np.float32)).cuda()
+        passes = [("cascade", float(np.quantile(dh[1:], 0.3)), float(np.quantile(zh, 0.4))),
+                  ("learned", float(np.quantile(zh, 0.8)), None),
+                  ("gated", 0.6, None),
+                  ("cascade", float(np.quantile(dh[1:], 0.8)), float(np.quantile(zh, 0.1))),
+                  ("learned", float(np.quantile(zh, 0.2)), None)]
+
+        def run(kind, a, b, count):
+            th_, yuv_, d_, gate = (torch.zeros_like(th), torch.zeros_like(yuv), torch.zeros_like(d),
+                                   torch.full((T,), -1e30, dtype=torch.float32, device="cuda"))
+            prop, sc, fl = _outs(T)
+            if kind == "cascade":
+                scn.scn_cascade_hist_scores(tiny["seq"], net, a, b, th_, yuv_, d_, gate, prop, sc, fl, count=count)
+            elif kind == "learned":
+                scn.scn_proposal_hist_scores(tiny["seq"], net, a, th_, gate, prop, sc, fl, count=count)
+            else:
+                scn.scn_gated_hist_scores(tiny["seq"], g, a, prop, sc, fl, count=count)
+            return prop, sc, fl, gate
+
+        alone = []
+        for kind, a, b in passes:
+            torch.cuda.synchronize()
+            out = run(kind, a, b, True)
+            torch.cuda.synchronize()
+            _check(*out[:3], tiny["exact"])
+            alone.append([x.cpu() for x in out])
+        torch.cuda.synchronize()
+        queued = [run(kind, a, b, False) for kind, a, b in passes]
+        torch.cuda.synchronize()
+        for (kind, _, _), q, ref in zip(passes, queued, alone):
+            for x, y in zip(q, ref):
+                assert torch.equal(x.cpu(), y), kind
+        assert any(int(r[0].sum()) > 0 for r in alone)
+        assert scn.scn_seq_sync_status(tiny["seq"]) == scn.SCN_OK
+        assert scn.scn_cnn_sync_status(net) == scn.SCN_OK
+    finally:
+        scn.scn_cnn_destroy(net)
+
+
 def test_thumb_diff(scn, orc, tiny):
     T = tiny["T"]
     th = torch.empty((T, 36, 64), dtype=torch.uint8, device="cuda")
