@@ -575,51 +575,44 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
     ptx::pdl_wait();
     ptx::pdl_release();
 
-    // ---- once: weights, biases, zeroed activation buffers, barriers, TMEM
-    for (int e = tid; e < 16 * 4; e += kPpThreads) {  // W1: 16 rows x 4 entries
-        const int n = e >> 2, j = e & 3;
-        uint32_t w[4];
-        // conv1's bias in the K slots 6 and 7 of the first filter row, as two BF16
-        // parts whose sum is the fp32 bias to 16 significant bits; X1 carries 1.0 there
-        const float b1 = a.master[kB1 + n];
-        const __nv_bfloat16 bhi = __float2bfloat16_rn(b1);
-        const __nv_bfloat16 blo = __float2bfloat16_rn(b1 - __bfloat162float(bhi));
+    // ---- once: weights, biases, zeroed activation buffers, barriers, TMEM.  Every global
+    //      load is issued first (one round trip to L2 for all of them), the buffers are zeroed
+    //      while they are in flight, then the values are stored in their layouts.
+    static_assert(32 * 64 == 4 * kPpThreads, "F1: four entries per thread");
+    uint4 w2r[2], w3r[3];
+    float f1r[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint16_t h[2];
+    for (int i = 0; i < 2; ++i) {  // W2: tap x 32 rows x 2 entries
+        const int e = tid + i * kPpThreads, t = e / 64, n = (e >> 1) & 31, j = e & 1;
+        if (e < 9 * 32 * 2) w2r[i] = __ldg(reinterpret_cast<const uint4*>(a.w2b + n * 144 + t * 16 + 8 * j));
+    }
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int k = 8 * j + 2 * q + s, dy = k >> 3, rem = k & 7, dx = rem >> 1, c = rem & 1;
-                h[s] = (dy < 3 && rem < 6) ? __bfloat16_as_ushort(a.w1b[n * 32 + (dy * 3 + dx) * 2 + c])
-                       : k == 6           ? __bfloat16_as_ushort(bhi)
-                       : k == 7           ? __bfloat16_as_ushort(blo)
-                                          : 0;
-            }
-            w[q] = static_cast<uint32_t>(h[0]) | (static_cast<uint32_t>(h[1]) << 16);
+    for (int i = 0; i < 3; ++i) {  // W3: tap x 32 rows x 4 entries
+        const int e = tid + i * kPpThreads, t = e / 128, n = (e >> 2) & 31, j = e & 3;
+        if (e < 9 * 32 * 4) w3r[i] = __ldg(reinterpret_cast<const uint4*>(a.w3b + n * 288 + t * 32 + 8 * j));
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f1r[i] = a.f1t[tid + i * kPpThreads];
+    // biases: b1 @0, b2 @16, b3 @48, c1 @80, f2 @144, c2 @208 (thread tid loads entry tid of each)
+    const float rb1 = tid < 16 ? a.master[kB1 + tid] : 0.f;
+    const float rb2 = tid < 32 ? a.master[kB2 + tid] : 0.f, rb3 = tid < 32 ? a.master[kB3 + tid] : 0.f;
+    const float rc1 = tid < 64 ? a.master[kC1 + tid] : 0.f;
+    const float rf2 = tid < 64 ? __bfloat162float(a.f2b[tid]) : 0.f;
+    const float rc2 = tid == 0 ? a.master[kC2] : 0.f;
+    // W1: 16 rows x 4 entries of 8 K slots, thread e < 64 builds entry e; conv1's bias sits in
+    // the K slots 6 and 7 of the first filter row, as two BF16 parts whose sum is the fp32
+    // bias to 16 significant bits (X1 carries 1.0 there)
+    uint16_t w1h[8];
+    float w1b1 = 0.f;
+    if (tid < 16 * 4) {
+        const int n = tid >> 2, j = tid & 3;
+        w1b1 = a.master[kB1 + n];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = 8 * j + i, dy = k >> 3, rem = k & 7, dx = rem >> 1, c = rem & 1;
+            w1h[i] = (dy < 3 && rem < 6) ? __bfloat16_as_ushort(a.w1b[n * 32 + (dy * 3 + dx) * 2 + c]) : 0;
         }
-        *reinterpret_cast<uint4*>(smem + kPpW1 + tc::core_offset(n, 8 * j, 32)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    for (int e = tid; e < 9 * 32 * 2; e += kPpThreads) {  // W2: tap x 32 rows x 2 entries
-        const int t = e / 64, n = (e >> 1) & 31, j = e & 1;
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w2b + n * 144 + t * 16 + 8 * j));
-        *reinterpret_cast<uint4*>(smem + kPpW2 + t * 1024 + tc::core_offset(n, 8 * j, 16)) = v;
-    }
-    for (int e = tid; e < 9 * 32 * 4; e += kPpThreads) {  // W3: tap x 32 rows x 4 entries
-        const int t = e / 128, n = (e >> 2) & 31, j = e & 3;
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w3b + n * 288 + t * 32 + 8 * j));
-        *reinterpret_cast<uint4*>(smem + kPpW3 + t * 2048 + tc::core_offset(n, 8 * j, 32)) = v;
-    }
-    if (tid < 16) bias[tid] = a.master[kB1 + tid];
-    if (tid < 32) {
-        bias[16 + tid] = a.master[kB2 + tid];
-        bias[48 + tid] = a.master[kB3 + tid];
-    }
-    if (tid < 64) {
-        bias[80 + tid] = a.master[kC1 + tid];
-        bias[144 + tid] = __bfloat162float(a.f2b[tid]);
-    }
-    if (tid == 0) bias[208] = a.master[kC2];
-    for (int e = tid; e < 32 * 64; e += kPpThreads) reinterpret_cast<float*>(smem + kPpF1)[e] = a.f1t[e];
     // X1: every entry 0 with 1.0 in the two bias slots (the padding rows keep it: the
     // build writes the image rows only); both A1 and both A2 buffers zero (the
     // epilogues write the live entries only)
@@ -627,6 +620,41 @@ __global__ void __launch_bounds__(kPpThreads, 1) cnn_forward_pipe(const __grid_c
         reinterpret_cast<uint4*>(X1)[e] = make_uint4(0, 0, 0, kPpOnes);
     for (int e = tid; e < (kPpPart - kPpA1) / 16; e += kPpThreads)
         reinterpret_cast<uint4*>(smem + kPpA1)[e] = make_uint4(0, 0, 0, 0);
+    if (tid < 16 * 4) {
+        const int n = tid >> 2, j = tid & 3;
+        const __nv_bfloat16 bhi = __float2bfloat16_rn(w1b1);
+        const __nv_bfloat16 blo = __float2bfloat16_rn(w1b1 - __bfloat162float(bhi));
+        if (j == 0) {  // K slots 6, 7 of the first entry
+            w1h[6] = __bfloat16_as_ushort(bhi);
+            w1h[7] = __bfloat16_as_ushort(blo);
+        }
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = static_cast<uint32_t>(w1h[2 * q]) | (static_cast<uint32_t>(w1h[2 * q + 1]) << 16);
+        *reinterpret_cast<uint4*>(smem + kPpW1 + tc::core_offset(n, 8 * j, 32)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int e = tid + i * kPpThreads, t = e / 64, n = (e >> 1) & 31, j = e & 1;
+        if (e < 9 * 32 * 2) *reinterpret_cast<uint4*>(smem + kPpW2 + t * 1024 + tc::core_offset(n, 8 * j, 16)) = w2r[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int e = tid + i * kPpThreads, t = e / 128, n = (e >> 2) & 31, j = e & 3;
+        if (e < 9 * 32 * 4) *reinterpret_cast<uint4*>(smem + kPpW3 + t * 2048 + tc::core_offset(n, 8 * j, 32)) = w3r[i];
+    }
+    if (tid < 16) bias[tid] = rb1;
+    if (tid < 32) {
+        bias[16 + tid] = rb2;
+        bias[48 + tid] = rb3;
+    }
+    if (tid < 64) {
+        bias[80 + tid] = rc1;
+        bias[144 + tid] = rf2;
+    }
+    if (tid == 0) bias[208] = rc2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) reinterpret_cast<float*>(smem + kPpF1)[tid + i * kPpThreads] = f1r[i];
     if (tid == 0) {
         for (int i = 0; i < kPpNBar; ++i) {
             uint32_t cnt = 1;  // tcgen05.commit of one issuer
