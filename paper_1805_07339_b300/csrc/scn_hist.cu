@@ -496,12 +496,9 @@ __device__ __forceinline__ void flush_region(uint8_t* tab, uint32_t* acc, int re
     }
 }
 
-// Score of element k from its histogram (h0: bins lane, h1: bins 32+lane) and
-// a neighbour's, read from global memory.
-__device__ __forceinline__ void write_score(const Job& J, int64_t k, uint32_t h0, uint32_t h1, const uint32_t* other,
+// Score of element k from two histograms (h0, p0: bins lane; h1, p1: bins 32 + lane).
+__device__ __forceinline__ void write_score(const Job& J, int64_t k, uint32_t h0, uint32_t h1, uint32_t p0, uint32_t p1,
                                             int lane) {
-    const uint32_t p0 = ptx::ld_cg_u32(other + lane);
-    const uint32_t p1 = lane < 16 ? ptx::ld_cg_u32(other + 32 + lane) : 0u;
     uint32_t d = (h0 > p0 ? h0 - p0 : p0 - h0);
     if (lane < 16) d += (h1 > p1 ? h1 - p1 : p1 - h1);
     const uint32_t s = __reduce_add_sync(0xffffffffu, d);
@@ -542,32 +539,38 @@ __device__ void publish(const Job& J, int64_t n, int64_t k, int seg_rp, uint32_t
     __threadfence();
     __syncwarp();
     // a gated pass needs only the scores of its pairs (2i, 2i+1): the odd elements
-    const bool any_k = !J.score_at || (k & 1);
-    const bool any_k1 = !J.score_at || !(k & 1);
-    if (k == 0) {
-        if (lane == 0 && !J.score_at) {
-            J.score[0] = 0;
-            J.flag[0] = 0;
-        }
-    } else if (any_k) {
-        uint32_t old = 0;
-        if (lane == 0) old = atomicAdd(&J.pair[k], 1u);
-        old = __shfl_sync(0xffffffffu, old, 0);
-        if (old == 1) {
-            __threadfence();
-            write_score(J, k, h0, h1, J.hist + (k - 1) * 48, lane);
-            if (lane == 0) J.pair[k] = 0;
-        }
+    const bool want0 = k > 0 && (!J.score_at || (k & 1));
+    const bool want1 = k + 1 < n && (!J.score_at || !(k & 1));
+    if (k == 0 && lane == 0 && !J.score_at) {
+        J.score[0] = 0;
+        J.flag[0] = 0;
     }
-    if (k + 1 < n && any_k1) {
-        uint32_t old = 0;
-        if (lane == 0) old = atomicAdd(&J.pair[k + 1], 1u);
-        old = __shfl_sync(0xffffffffu, old, 0);
-        if (old == 1) {
-            __threadfence();
-            write_score(J, k + 1, h0, h1, J.hist + (k + 1) * 48, lane);
-            if (lane == 0) J.pair[k + 1] = 0;
-        }
+    // both stencil pairs of element k at once, (k - 1, k) counted by lane 0 and (k, k + 1) by
+    // lane 1: the second arrival of a pair computes its score
+    uint32_t old = 0;
+    if (lane == 0 && want0) old = atomicAdd(&J.pair[k], 1u);
+    if (lane == 1 && want1) old = atomicAdd(&J.pair[k + 1], 1u);
+    const bool s0 = __shfl_sync(0xffffffffu, old, 0) == 1u;
+    const bool s1 = __shfl_sync(0xffffffffu, old, 1) == 1u;
+    if (!s0 && !s1) return;
+    __threadfence();
+    // the neighbours' histograms, every load in flight together
+    uint32_t a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    if (s0) {
+        a0 = ptx::ld_cg_u32(J.hist + (k - 1) * 48 + lane);
+        if (lane < 16) a1 = ptx::ld_cg_u32(J.hist + (k - 1) * 48 + 32 + lane);
+    }
+    if (s1) {
+        b0 = ptx::ld_cg_u32(J.hist + (k + 1) * 48 + lane);
+        if (lane < 16) b1 = ptx::ld_cg_u32(J.hist + (k + 1) * 48 + 32 + lane);
+    }
+    if (s0) {
+        write_score(J, k, h0, h1, a0, a1, lane);
+        if (lane == 0) J.pair[k] = 0;
+    }
+    if (s1) {
+        write_score(J, k + 1, h0, h1, b0, b1, lane);
+        if (lane == 0) J.pair[k + 1] = 0;
     }
 }
 
