@@ -178,6 +178,13 @@ __device__ __forceinline__ Item item_at(const Launch& L, int64_t i) {
     const Job& J = L.job0;
     Item it;
     it.job = 0;
+    if (J.tail_parts > 0 && i >= J.tail_from) {
+        const int64_t j = i - J.tail_from;
+        it.k = static_cast<int32_t>(J.tail_from + j / J.tail_parts);
+        it.rp0 = static_cast<int32_t>(j - (it.k - J.tail_from) * static_cast<int64_t>(J.tail_parts)) * J.tail_rp;
+        it.nrp = min(J.tail_rp, J.H / 2 - it.rp0);
+        return it;
+    }
     it.k = static_cast<int32_t>(i / J.items_per_frame);
     const int part = static_cast<int>(i - static_cast<int64_t>(it.k) * J.items_per_frame);
     it.rp0 = part * J.item_rp;
@@ -1136,6 +1143,22 @@ Launch single_launch(const scn_table* t, int64_t n, const int32_t* slot, const H
     L.rp_per_cta = sh.rp_per_cta;
     L.grid = sh.grid;
     L.region_items = (sh.rp_per_cta == 0 && region_frames(t->W, t->H)) ? 1 : 0;
+    // A queue of whole frames ends with every CTA on its last frame, finishing up to a frame's
+    // time apart: the last `grid` frames are queued in kTailParts parts each instead, so the
+    // launch ends on parts of frames.
+    if (sh.rp_per_cta == 0 && !L.region_items && sh.items_per_frame == 1 && n >= 2LL * sh.grid &&
+        n <= 0x7fffffff) {
+        const int hp = t->H / 2;
+        const int rp = (hp + kTailParts - 1) / kTailParts;
+        j.tail_parts = (hp + rp - 1) / rp;
+        if (j.tail_parts > 1) {
+            j.tail_rp = rp;
+            j.tail_from = static_cast<int32_t>(n - sh.grid);
+            L.n_items = j.tail_from + static_cast<int64_t>(sh.grid) * j.tail_parts;
+        } else {
+            j.tail_parts = 0;
+        }
+    }
     return L;
 }
 

@@ -109,6 +109,7 @@ constexpr int kRegionThreads = kGroupWarps * 32;
 constexpr int64_t kRegionFramePxMax = int64_t(1) << 20;
 static_assert(kRegionFramePxMax / kRegionThreads + 2 * 32 < 65536, "16-bit lane counters (region streams)");
 inline bool region_frames(int W, int H) { return static_cast<int64_t>(W) * H <= kRegionFramePxMax; }
+constexpr int kTailParts = 4;  // parts of each of the last `grid` frames of a whole-frame queue
 
 }  // namespace scn
 
@@ -168,6 +169,9 @@ struct Job {
     int32_t chunk_rows;    // luma rows per staged chunk (even)
     int32_t item_rp;       // row pairs per work item
     int32_t items_per_frame;
+    int32_t tail_from;     // tail_parts > 0 (whole-frame queues): frames from tail_from on are
+    int32_t tail_parts;    // queued as tail_parts items of tail_rp row pairs each, so that the
+    int32_t tail_rp;       // launch ends on parts of frames
     int32_t wv, sp, sc;    // 16-byte columns per row; consumer threads / wv; consumer threads % wv
     uint32_t dY, dU;       // luma / chroma byte step per consumer-thread stride of units
     int32_t sc_r;          // the same for one table region's threads (region-stream kernel)

@@ -356,8 +356,10 @@ def test_flat_frames_all_work_assignments(scn, orc, W, H):
     dev = Dev(scn, buf, W, H, n)
     try:
         # default: contiguous row-pair ranges per CTA; then the work queue with items
-        # of about a quarter frame and of whole frames, and a one-CTA launch
-        for tune in (None, dict(item_kpx=W * H // 4000), dict(item_kpx=W * H // 1000 + 1), dict(grid=1)):
+        # of about a quarter frame and of whole frames (with two CTAs, the last two frames
+        # are queued in quarters), and a one-CTA launch
+        for tune in (None, dict(item_kpx=W * H // 4000), dict(item_kpx=W * H // 1000 + 1),
+                     dict(item_kpx=W * H // 1000 + 1, grid=2), dict(grid=1)):
             seq = dev.seq(scn.SCN_GATHER, indices=order)
             h, s, f = dev.hist_scores(seq, tune=tune)
             assert np.array_equal(h, rh[order]), tune
