@@ -493,6 +493,89 @@ def test_thumbs_parity(scn, orc, W, H):
         dev.close()
 
 
+def test_mixed_calls_queued_back_to_back(scn):
+    """Hist (contiguous ranges, region streams, whole-frame queue with its split tail), resize,
+    thumbnails and a batched plan queued on one stream with no host wait between them (the
+    kernels are launched as programmatic dependents of one another): every output equals the
+    same call's made alone, with the device idle before and after it."""
+    W, H = TINY["width"], TINY["height"]
+    vt = _video(scn, TINY)
+    bt = _generate(scn, vt, W, H, TINY["num_frames"])
+    vh = _video(scn, HD)
+    bh = _generate(scn, vh, HD["width"], HD["height"], 12)
+    dt = Dev(scn, bt, W, H, TINY["num_frames"])
+    dh = Dev(scn, bh, HD["width"], HD["height"], 12)
+    qt = dt.seq(scn.SCN_STRIDE, start=0, stop=TINY["num_frames"], step=1)
+    qt2 = dt.seq(scn.SCN_STRIDE, start=3, stop=TINY["num_frames"], step=2)
+    scn.scn_seq_set_tune(qt2, item_kpx=20)  # queue of small items: region streams
+    qh = dh.seq(scn.SCN_GATHER, indices=[0, 5, 5, 11, 2, 7, 1])
+    qh2 = dh.seq(scn.SCN_STRIDE, start=0, stop=12, step=1)
+    scn.scn_seq_set_tune(qh2, item_kpx=2100, grid=3)  # whole-frame queue, last 3 frames in quarters
+    n = {q: scn.scn_seq_length(q) for q in (qt, qt2, qh, qh2)}
+    plan_outs = [(torch.empty((n[q], 48), dtype=torch.int32, device="cuda"),
+                  torch.empty(n[q], dtype=torch.int32, device="cuda"),
+                  torch.empty(n[q], dtype=torch.uint8, device="cuda")) for q in (qt2, qh)]
+    plan = scn.scn_plan_create([qt2, qh], [o[0] for o in plan_outs], [o[1] for o in plan_outs],
+                               [o[2] for o in plan_outs])
+
+    def hist(q):
+        out = (torch.empty((n[q], 48), dtype=torch.int32, device="cuda"), torch.empty(n[q], dtype=torch.int32, device="cuda"),
+               torch.empty(n[q], dtype=torch.uint8, device="cuda"))
+        scn.scn_hist_scores(q, *out)
+        return out
+
+    def resize(q):
+        f32 = torch.empty((n[q], 3, 224, 224), dtype=torch.float32, device="cuda")
+        b16 = torch.empty((n[q], 3, 224, 224), dtype=torch.bfloat16, device="cuda")
+        scn.scn_resize_norm_both(q, 224, 224, MEAN, STD, f32, b16)
+        return f32, b16
+
+    def thumbs(q):
+        th = torch.empty((n[q], 36, 64), dtype=torch.uint8, device="cuda")
+        yuv = torch.empty((n[q], 3, 6, 32), dtype=torch.uint8, device="cuda")
+        scn.scn_thumbs_yuv(q, th, yuv)
+        return th, yuv
+
+    def run_plan():
+        for o in plan_outs:
+            for x in o:
+                x.fill_(-1)
+        scn.scn_plan_run(plan)
+        return tuple(x.clone() for o in plan_outs for x in o)
+
+    ops = [lambda: hist(qt), lambda: resize(qh), lambda: hist(qh2), lambda: thumbs(qt), lambda: hist(qh),
+           run_plan, lambda: hist(qt2), lambda: resize(qt), lambda: hist(qh2), lambda: thumbs(qh)]
+    try:
+        alone = []
+        for op in ops:
+            torch.cuda.synchronize()
+            alone.append([x.cpu() for x in op()])
+            torch.cuda.synchronize()
+        queued = [op() for op in ops]
+        torch.cuda.synchronize()
+        for i, (q, a) in enumerate(zip(queued, alone)):
+            for x, y in zip(q, a):
+                assert torch.equal(x.cpu(), y), i
+        for q in (qt, qt2, qh, qh2):
+            assert scn.scn_seq_sync_status(q) == scn.SCN_OK
+        assert scn.scn_plan_sync_status(plan) == scn.SCN_OK
+        # the whole-frame queue with a split tail and the plan agree with the plain launches
+        h0, s0, f0 = alone[2]
+        plain = dh.seq(scn.SCN_STRIDE, start=0, stop=12, step=1)
+        h1, s1, f1 = dh.hist_scores(plain)
+        scn.scn_seq_destroy(plain)
+        assert np.array_equal(h0.numpy().view(np.uint32).reshape(-1, 3, 16), h1)
+        assert np.array_equal(s0.numpy().view(np.uint32), s1) and np.array_equal(f0.numpy(), f1)
+    finally:
+        scn.scn_plan_destroy(plan)
+        for q in (qt, qt2, qh, qh2):
+            scn.scn_seq_destroy(q)
+        dt.close()
+        dh.close()
+        scn.scn_video_destroy(vt)
+        scn.scn_video_destroy(vh)
+
+
 def test_argument_errors_before_launch(scn):
     W, H, n = 64, 36, 2
     buf = torch.zeros(n * W * H * 3 // 2, dtype=torch.uint8, device="cuda")
