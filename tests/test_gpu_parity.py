@@ -155,6 +155,27 @@ def test_hist_random_bytes_bit_exact(scn, orc, W, H, n):
         dev.close()
 
 
+@pytest.mark.parametrize("W,H,n,grid", [(8192, 130, 6, 2), (1920, 1080, 5, 2), (2048, 1024, 9, 3), (1936, 1090, 4, 1),
+                                        (4096, 2052, 3, 1)])
+def test_split_tail_queue_bit_exact(scn, orc, W, H, n, grid):
+    """Whole-frame queue items (frames above 1 Mpx) with the last `grid` frames queued in quarters
+    (fewer when a frame has under four row pairs per part), on random bytes, with a gather order
+    that repeats and jumps back: equal to the oracle; chunks of a few rows cut the tail items too."""
+    frames = random_nv12(W + 3 * H, n, W, H)
+    buf = torch.from_numpy(frames.reshape(-1)).cuda()
+    dev = Dev(scn, buf, W, H, n)
+    try:
+        order = list(range(n)) + [0, n - 1, n - 1]
+        rh, rs, rf = _oracle_hs(orc, frames, W, H, np.array(order))
+        for chunk_rows in (0, 6):
+            seq = dev.seq(scn.SCN_GATHER, indices=order)
+            h, s, f = dev.hist_scores(seq, tune=dict(item_kpx=W * H // 1000 + 1, grid=grid, chunk_rows=chunk_rows))
+            assert np.array_equal(h, rh) and np.array_equal(s, rs) and np.array_equal(f, rf), chunk_rows
+            scn.scn_seq_destroy(seq)
+    finally:
+        dev.close()
+
+
 @pytest.mark.parametrize("tune", [dict(grid=1), dict(grid=2), dict(grid=3, chunk_rows=6), dict(grid=7),
                                   dict(chunk_rows=2, grid=16), dict(grid=1000), dict(chunk_rows=4, grid=2),
                                   dict(chunk_rows=10)])
