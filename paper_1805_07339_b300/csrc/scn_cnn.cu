@@ -1023,9 +1023,16 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ z, con
                                                 const __nv_bfloat16* __restrict__ a3, const __nv_bfloat16* f1b,
                                                 const __nv_bfloat16* f2b, float pos_weight, int64_t pairs,
                                                 float* grad, __nv_bfloat16* du3, float* loss) {
+    // F1 staged in shared memory; the block's gradient sums of F1 ([c][j] so that a warp's 32
+    // lanes hit 32 banks), c1 and F2, added by its warps and then once per element to `grad`
+    __shared__ __nv_bfloat16 sf1[64 * 32];
+    __shared__ float sacc[64 * 32 + 64 + 64];
     ptx::pdl_wait();
     ptx::pdl_release();
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < 64 * 32; i += blockDim.x) sf1[i] = f1b[i];
+    for (int i = tid; i < 64 * 32 + 128; i += blockDim.x) sacc[i] = 0.f;
+    __syncthreads();
     const int64_t w0 = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
     float dF1a[32], dF1b[32];  // rows j = lane and lane + 32
@@ -1033,24 +1040,30 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ z, con
     for (int c = 0; c < 32; ++c) dF1a[c] = dF1b[c] = 0.f;
     float dc1a = 0.f, dc1b = 0.f, dF2a = 0.f, dF2b = 0.f, dc2 = 0.f, lsum = 0.f;
     const float inv_b = 1.f / static_cast<float>(pairs);
+    const float f2a = __bfloat162float(f2b[lane]), f2c = __bfloat162float(f2b[lane + 32]);
     for (int64_t b = w0; b < pairs; b += nw) {
+        // the pair's a3 (for the ReLU mask of du3) requested first, with its other inputs
+        uint16_t am[40];
+        const uint16_t* ap = reinterpret_cast<const uint16_t*>(a3 + b * 40 * 32 + lane);
+#pragma unroll
+        for (int pos = 0; pos < 40; ++pos) am[pos] = ap[pos * 32];
         const float zz = z[b], yy = y[b];
+        const float va = v[b * 64 + lane], vb = v[b * 64 + 32 + lane];
+        const float gl = g[b * 32 + lane];
         const float sig = 1.f / (1.f + __expf(-zz));
         const float dz = (pos_weight * yy * (sig - 1.f) + (1.f - yy) * sig) * inv_b;
         // softplus(-z), softplus(z) for the loss
         const float spn = fmaxf(-zz, 0.f) + log1pf(__expf(-fabsf(zz)));
         const float spp = fmaxf(zz, 0.f) + log1pf(__expf(-fabsf(zz)));
         lsum += (pos_weight * yy * spn + (1.f - yy) * spp) * inv_b;
-        const float va = v[b * 64 + lane], vb = v[b * 64 + 32 + lane];
         const float ha = fmaxf(va, 0.f), hb = fmaxf(vb, 0.f);
         dF2a += dz * ha;
         dF2b += dz * hb;
         dc2 += dz;
-        const float dva = va > 0.f ? dz * __bfloat162float(f2b[lane]) : 0.f;
-        const float dvb = vb > 0.f ? dz * __bfloat162float(f2b[lane + 32]) : 0.f;
+        const float dva = va > 0.f ? dz * f2a : 0.f;
+        const float dvb = vb > 0.f ? dz * f2c : 0.f;
         dc1a += dva;
         dc1b += dvb;
-        const float gl = g[b * 32 + lane];
         float dg = 0.f;  // for channel c = lane
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
@@ -1061,29 +1074,40 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ z, con
 #pragma unroll 8
         for (int j = 0; j < 32; ++j) {
             const float dvj_a = __shfl_sync(0xffffffffu, dva, j), dvj_b = __shfl_sync(0xffffffffu, dvb, j);
-            dg = fmaf(__bfloat162float(f1b[j * 32 + lane]), dvj_a, dg);
-            dg = fmaf(__bfloat162float(f1b[(j + 32) * 32 + lane]), dvj_b, dg);
+            dg = fmaf(__bfloat162float(sf1[j * 32 + lane]), dvj_a, dg);
+            dg = fmaf(__bfloat162float(sf1[(j + 32) * 32 + lane]), dvj_b, dg);
         }
-        const float da3 = dg * (1.f / 40.f);
-        const __nv_bfloat16* ap = a3 + b * 40 * 32 + lane;
+        const __nv_bfloat16 da3 = __float2bfloat16_rn(dg * (1.f / 40.f));
+        const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
         __nv_bfloat16* dp = du3 + b * 40 * 32 + lane;
-        for (int pos = 0; pos < 40; ++pos)
-            dp[pos * 32] = __float2bfloat16_rn(__bfloat162float(ap[pos * 32]) > 0.f ? da3 : 0.f);
-    }
-    if (w0 >= pairs) return;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        atomicAdd(grad + kF1 + lane * 32 + c, dF1a[c]);
-        atomicAdd(grad + kF1 + (lane + 32) * 32 + c, dF1b[c]);
+        for (int pos = 0; pos < 40; ++pos)  // a3 > 0: bit patterns 0x0001 (least positive) .. 0x7F80 (+inf)
+            dp[pos * 32] = (static_cast<uint32_t>(am[pos]) - 1u < 0x7F80u) ? da3 : zero;
     }
-    atomicAdd(grad + kC1 + lane, dc1a);
-    atomicAdd(grad + kC1 + lane + 32, dc1b);
-    atomicAdd(grad + kF2 + lane, dF2a);
-    atomicAdd(grad + kF2 + lane + 32, dF2b);
-    // dc2 and the loss are the same in every lane (they depend on z only)
-    if (lane == 0) {
-        atomicAdd(grad + kC2, dc2);
-        atomicAdd(loss, lsum);
+    if (w0 < pairs) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            atomicAdd(&sacc[c * 64 + lane], dF1a[c]);
+            atomicAdd(&sacc[c * 64 + 32 + lane], dF1b[c]);
+        }
+        atomicAdd(&sacc[2048 + lane], dc1a);
+        atomicAdd(&sacc[2048 + 32 + lane], dc1b);
+        atomicAdd(&sacc[2112 + lane], dF2a);
+        atomicAdd(&sacc[2112 + 32 + lane], dF2b);
+        // dc2 and the loss are the same in every lane (they depend on z only)
+        if (lane == 0) {
+            atomicAdd(grad + kC2, dc2);
+            atomicAdd(loss, lsum);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < 64 * 32; i += blockDim.x) {
+        const int c = i >> 6, j = i & 63;
+        atomicAdd(grad + kF1 + j * 32 + c, sacc[i]);
+    }
+    if (tid < 64) {
+        atomicAdd(grad + kC1 + tid, sacc[2048 + tid]);
+        atomicAdd(grad + kF2 + tid, sacc[2112 + tid]);
     }
 }
 
@@ -1280,8 +1304,12 @@ __device__ __forceinline__ uint64_t mn_desc(uint32_t saddr, uint32_t mn_stride, 
     return tc::smem_desc(saddr, k_stride, mn_stride);
 }
 
+// Threads of the weight-gradient kernel: kWgtParts threads gather each of a chunk's 128 rows,
+// every one of its im2col loads in flight before its first store.
+constexpr int kWgtThreads = 512, kWgtParts = kWgtThreads / 128;
+
 template <int L>
-__global__ void __launch_bounds__(128) conv_bwd_weight_tc(const __grid_constant__ ConvWgtArgs a) {
+__global__ void __launch_bounds__(kWgtThreads) conv_bwd_weight_tc(const __grid_constant__ ConvWgtArgs a) {
     ptx::pdl_wait();
     ptx::pdl_release();
     using S = Shape<L>;
@@ -1292,8 +1320,10 @@ __global__ void __launch_bounds__(128) conv_bwd_weight_tc(const __grid_constant_
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + W::A_BYTES + W::B_BYTES);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & 127, part = tid >> 7;  // the chunk row this thread gathers, and which of its k chunks
     // k columns beyond the written chunks stay zero for the whole launch
-    for (int i = tid; i < (W::A_BYTES + W::B_BYTES) / 16; i += 128) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < (W::A_BYTES + W::B_BYTES) / 16; i += kWgtThreads)
+        reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         ptx::mbar_init(mbar, 1);
         ptx::fence_mbar_init();
@@ -1316,27 +1346,47 @@ __global__ void __launch_bounds__(128) conv_bwd_weight_tc(const __grid_constant_
     const int64_t chunks = (rows + 127) / 128;
     uint32_t phase = 0;
     bool ok = true, first = true;
+    constexpr int NJ = (S::KP / 8 + kWgtParts - 1) / kWgtParts;  // k chunks per thread
+    constexpr int NG = (S::COUT / 8 + kWgtParts - 1) / kWgtParts;  // dU chunks per thread
     for (int64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
-        const int64_t r = c * 128 + tid;
+        const int64_t r = c * 128 + row;
         const bool live = r < rows;
         const int64_t b = live ? r / S::P : 0;
         const int pos = live ? static_cast<int>(r - b * S::P) : 0;
-        uint8_t* arow = As + (tid >> 3) * (W::MP / 8) * 128 + (tid & 7) * 16;
-#pragma unroll 4
-        for (int j = 0; j < S::KP / 8; ++j) {
-            uint4 v = live ? im2col_chunk<L>(f, b, pos, j) : make_uint4(0, 0, 0, 0);
-            if (j == S::K / 8 && live) set_bf16_one<S::K % 8>(v);  // the ones column k = K shares this chunk
-            *reinterpret_cast<uint4*>(arow + j * 128) = v;
+        uint8_t* arow = As + (row >> 3) * (W::MP / 8) * 128 + (row & 7) * 16;
+        uint8_t* brow = Bs + (row >> 3) * (S::COUT / 8) * 128 + (row & 7) * 16;
+        // k chunks part, part + kWgtParts, ... of the row and its dU chunks: loads first
+        uint4 v[NJ], u[NG];
+#pragma unroll
+        for (int q = 0; q < NJ; ++q) {
+            const int j = part + q * kWgtParts;
+            v[q] = (live && j < S::KP / 8) ? im2col_chunk<L>(f, b, pos, j) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < NG; ++q) {
+            const int g = part + q * kWgtParts;
+            u[q] = (live && g < S::COUT / 8) ? __ldg(reinterpret_cast<const uint4*>(a.du + r * S::COUT + 8 * g))
+                                             : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < NJ; ++q) {
+            const int j = part + q * kWgtParts;
+            if (j < S::KP / 8) {
+                if (j == S::K / 8 && live) set_bf16_one<S::K % 8>(v[q]);  // the ones column k = K shares this chunk
+                *reinterpret_cast<uint4*>(arow + j * 128) = v[q];
+            }
         }
         if constexpr (S::K % 8 == 0) {
             // the ones column starts its own chunk
-            *reinterpret_cast<uint4*>(arow + (S::K / 8) * 128) = live ? make_uint4(0x3F80u, 0, 0, 0) : make_uint4(0, 0, 0, 0);
+            if (part == (S::K / 8) % kWgtParts)
+                *reinterpret_cast<uint4*>(arow + (S::K / 8) * 128) =
+                    live ? make_uint4(0x3F80u, 0, 0, 0) : make_uint4(0, 0, 0, 0);
         }
-        uint8_t* brow = Bs + (tid >> 3) * (S::COUT / 8) * 128 + (tid & 7) * 16;
 #pragma unroll
-        for (int g = 0; g < S::COUT / 8; ++g)
-            *reinterpret_cast<uint4*>(brow + g * 128) =
-                live ? __ldg(reinterpret_cast<const uint4*>(a.du + r * S::COUT + 8 * g)) : make_uint4(0, 0, 0, 0);
+        for (int q = 0; q < NG; ++q) {
+            const int g = part + q * kWgtParts;
+            if (g < S::COUT / 8) *reinterpret_cast<uint4*>(brow + g * 128) = u[q];
+        }
         tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
@@ -1361,9 +1411,9 @@ __global__ void __launch_bounds__(128) conv_bwd_weight_tc(const __grid_constant_
         phase ^= 1u;
         tc::fence_after_sync();
     }
-    // epilogue: TMEM lane = k within the tile, column = co (every CTA has at
+    // epilogue by warps 0-3 (TMEM lane = k within the tile, column = co; every CTA has at
     // least one chunk; the loads are warp-wide, the adds only after a complete wait)
-    if (!first) {
+    if (!first && warp < 4) {
 #pragma unroll
         for (int t = 0; t < W::MT; ++t) {
             const int k = t * 128 + tid;
@@ -1432,14 +1482,18 @@ scn_status launch_bwd_weight(const ConvWgtArgs& a, cudaStream_t st) {
     const scn_status sa = once_per_device(attr_done, [] {
         SCN_CUDA_TRY(cudaFuncSetAttribute(conv_bwd_weight_tc<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           WgtTc<L>::BYTES));
+        SCN_CUDA_TRY(cudaFuncSetAttribute(conv_bwd_weight_tc<L>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
         return SCN_OK;
     });
     if (sa != SCN_OK) return sa;
     const int64_t chunks = (a.pairs * S::P + 127) / 128;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
-    const int grid = static_cast<int>(std::min<int64_t>(chunks, static_cast<int64_t>(sms)));
-    SCN_CUDA_TRY(launch_pdl(conv_bwd_weight_tc<L>, dim3(grid), dim3(128), WgtTc<L>::BYTES, st, a));
+    // as many CTAs per SM as shared memory and threads allow (at most 4: TMEM columns fit)
+    const int per_sm = std::max(1, std::min<int>(2048 / kWgtThreads, (227 * 1024) / (WgtTc<L>::BYTES + 1024)));
+    const int grid = static_cast<int>(std::min<int64_t>(chunks, static_cast<int64_t>(sms) * per_sm));
+    SCN_CUDA_TRY(launch_pdl(conv_bwd_weight_tc<L>, dim3(grid), dim3(kWgtThreads), WgtTc<L>::BYTES, st, a));
     return SCN_OK;
 }
 
