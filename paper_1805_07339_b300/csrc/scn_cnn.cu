@@ -167,8 +167,12 @@ __device__ __forceinline__ uint4 im2col_chunk(const ConvFwdArgs& a, int64_t b, i
     }
 }
 
+// Threads of the training convolutions: kConvParts threads gather each of a tile's 128 rows,
+// every one of its im2col loads in flight before its first store.
+constexpr int kConvThreads = 512, kConvParts = kConvThreads / 128;
+
 template <int L>
-__global__ void __launch_bounds__(128) conv_fwd_tc(const __grid_constant__ ConvFwdArgs a) {
+__global__ void __launch_bounds__(kConvThreads) conv_fwd_tc(const __grid_constant__ ConvFwdArgs a) {
     ptx::pdl_wait();
     ptx::pdl_release();
     if (a.zero) {
@@ -183,8 +187,9 @@ __global__ void __launch_bounds__(128) conv_fwd_tc(const __grid_constant__ ConvF
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + M::A_BYTES + M::B_BYTES);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & 127, part = tid >> 7;  // the tile row this thread gathers, and which of its k chunks
     // weights -> B tile (core layout), once
-    for (int e = tid; e < S::COUT * (S::KP / 8); e += 128) {
+    for (int e = tid; e < S::COUT * (S::KP / 8); e += kConvThreads) {
         const int n = e / (S::KP / 8), j = e % (S::KP / 8);
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w + n * S::KP + 8 * j));
         *reinterpret_cast<uint4*>(Bs + tc::core_offset(n, 8 * j, S::KP)) = v;
@@ -205,16 +210,23 @@ __global__ void __launch_bounds__(128) conv_fwd_tc(const __grid_constant__ ConvF
     const int64_t tiles = (rows + 127) / 128;
     uint32_t phase = 0;
     bool ok = true;
+    constexpr int NJ = (S::KP / 8 + kConvParts - 1) / kConvParts;  // k chunks per thread
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        // A tile: row tid of this tile
-        const int64_t r = t * 128 + tid;
+        // A tile: k chunks part, part + kConvParts, ... of row `row`, loads first
+        const int64_t r = t * 128 + row;
         const bool live = r < rows;
         const int64_t b = live ? r / S::P : 0;
         const int pos = live ? static_cast<int>(r - b * S::P) : 0;
-#pragma unroll 4
-        for (int j = 0; j < S::KP / 8; ++j) {
-            const uint4 v = live ? im2col_chunk<L>(a, b, pos, j) : make_uint4(0, 0, 0, 0);
-            *reinterpret_cast<uint4*>(As + tc::core_offset(tid, 8 * j, S::KP)) = v;
+        uint4 v[NJ];
+#pragma unroll
+        for (int q = 0; q < NJ; ++q) {
+            const int j = part + q * kConvParts;
+            v[q] = (live && j < S::KP / 8) ? im2col_chunk<L>(a, b, pos, j) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < NJ; ++q) {
+            const int j = part + q * kConvParts;
+            if (j < S::KP / 8) *reinterpret_cast<uint4*>(As + tc::core_offset(row, 8 * j, S::KP)) = v[q];
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
@@ -234,27 +246,29 @@ __global__ void __launch_bounds__(128) conv_fwd_tc(const __grid_constant__ ConvF
         }
         phase ^= 1u;
         tc::fence_after_sync();
-        // epilogue: thread = row, COUT columns
-        uint32_t acc[S::COUT];
+        // epilogue by warps 0-3: thread = row, COUT columns
+        if (warp < 4) {
+            uint32_t acc[S::COUT];
 #pragma unroll
-        for (int c0 = 0; c0 < S::COUT; c0 += 16) {
-            uint32_t q[16];
-            tc::ld16(tmem + ((32u * warp) << 16) + c0, q);
+            for (int c0 = 0; c0 < S::COUT; c0 += 16) {
+                uint32_t q[16];
+                tc::ld16(tmem + ((32u * warp) << 16) + c0, q);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[c0 + i] = q[i];
-        }
-        tc::wait_ld();
-        if (live && ok) {
-            uint32_t out[S::COUT / 2];
-#pragma unroll
-            for (int c = 0; c < S::COUT; c += 2) {
-                const float v0 = fmaxf(__uint_as_float(acc[c]) + __ldg(a.bias + c), 0.f);
-                const float v1 = fmaxf(__uint_as_float(acc[c + 1]) + __ldg(a.bias + c + 1), 0.f);
-                out[c / 2] = pack_bf16(v0, v1);
+                for (int i = 0; i < 16; ++i) acc[c0 + i] = q[i];
             }
-            uint4* dst = reinterpret_cast<uint4*>(a.y + r * S::COUT);
+            tc::wait_ld();
+            if (live && ok) {
+                uint32_t out[S::COUT / 2];
 #pragma unroll
-            for (int q = 0; q < S::COUT / 8; ++q) dst[q] = make_uint4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+                for (int c = 0; c < S::COUT; c += 2) {
+                    const float v0 = fmaxf(__uint_as_float(acc[c]) + __ldg(a.bias + c), 0.f);
+                    const float v1 = fmaxf(__uint_as_float(acc[c + 1]) + __ldg(a.bias + c + 1), 0.f);
+                    out[c / 2] = pack_bf16(v0, v1);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(a.y + r * S::COUT);
+#pragma unroll
+                for (int q = 0; q < S::COUT / 8; ++q) dst[q] = make_uint4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+            }
         }
         tc::fence_before_sync();
         __syncthreads();
@@ -333,6 +347,8 @@ scn_status launch_conv_fwd(const ConvFwdArgs& a, cudaStream_t st) {
     const scn_status sa = once_per_device(attr_done, [] {
         SCN_CUDA_TRY(cudaFuncSetAttribute(conv_fwd_tc<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           ConvSmem<L>::BYTES));
+        SCN_CUDA_TRY(cudaFuncSetAttribute(conv_fwd_tc<L>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxShared));
         return SCN_OK;
     });
     if (sa != SCN_OK) return sa;
@@ -340,7 +356,7 @@ scn_status launch_conv_fwd(const ConvFwdArgs& a, cudaStream_t st) {
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
     const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(sms) * 4));
-    SCN_CUDA_TRY(launch_pdl(conv_fwd_tc<L>, dim3(grid), dim3(128), ConvSmem<L>::BYTES, st, a));
+    SCN_CUDA_TRY(launch_pdl(conv_fwd_tc<L>, dim3(grid), dim3(kConvThreads), ConvSmem<L>::BYTES, st, a));
     return SCN_OK;
 }
 
@@ -1138,7 +1154,7 @@ __global__ void __launch_bounds__(128) conv_bwd_data_tc(const __grid_constant__ 
     using M = BwdSmem<L>;
     constexpr int NH = S::KP > 144 ? 2 : 1;   // N halves
     constexpr int NN = S::KP / NH;            // 144 for both layers
-    static_assert(NN % 16 == 0 && NN <= 256, "N");
+    static_assert(NN % 48 == 0 && NN <= 256, "N: three 16-column TMEM loads at a time");
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* As = smem;
     uint8_t* Bs = smem + M::A_BYTES;
@@ -1166,7 +1182,10 @@ __global__ void __launch_bounds__(128) conv_bwd_data_tc(const __grid_constant__ 
     const int64_t tiles = (rows + 127) / 128;
     uint32_t phase = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    // work item w: row tile w / NH, column half w % NH (the halves of a tile run on separate CTAs)
+    for (int64_t w = blockIdx.x; w < tiles * NH; w += gridDim.x) {
+        const int64_t t = w / NH;
+        const int h = static_cast<int>(w - t * NH);
         const int64_t r = t * 128 + tid;
         const bool live = r < rows;
 #pragma unroll
@@ -1175,36 +1194,38 @@ __global__ void __launch_bounds__(128) conv_bwd_data_tc(const __grid_constant__ 
             *reinterpret_cast<uint4*>(As + tc::core_offset(tid, 8 * j, S::COUT)) = v;
         }
         tc::fence_proxy_async();
-        for (int h = 0; h < NH; ++h) {
-            tc::fence_before_sync();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after_sync();
-                const uint32_t bh = b_addr + (h * NN / 8) * kSbo;
-#pragma unroll
-                for (int kk = 0; kk < S::COUT / 16; ++kk)
-                    tc::mma(tmem, tc::smem_desc(a_addr + kk * 256, 128, kSbo), tc::smem_desc(bh + kk * 256, 128, kSbo),
-                            idesc, kk > 0 ? 1u : 0u);
-                tc::commit(mbar);
-            }
-            if (ok && !ptx::mbar_wait_bounded(mbar, phase, kWaitNs)) {
-                ok = false;
-                atomicOr(a.status, kStatusTimeout);
-            }
-            phase ^= 1u;
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
             tc::fence_after_sync();
-            float* dst = a.dxcol + r * S::KP + h * NN;
-#pragma unroll 1
-            for (int c0 = 0; c0 < NN; c0 += 16) {
-                uint32_t q[16];
-                tc::ld16(tmem + ((32u * warp) << 16) + c0, q);
-                tc::wait_ld();
-                if (live && ok) {
-                    float4* d4 = reinterpret_cast<float4*>(dst + c0);
+            const uint32_t bh = b_addr + (h * NN / 8) * kSbo;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        d4[i] = make_float4(__uint_as_float(q[4 * i]), __uint_as_float(q[4 * i + 1]),
-                                            __uint_as_float(q[4 * i + 2]), __uint_as_float(q[4 * i + 3]));
+            for (int kk = 0; kk < S::COUT / 16; ++kk)
+                tc::mma(tmem, tc::smem_desc(a_addr + kk * 256, 128, kSbo), tc::smem_desc(bh + kk * 256, 128, kSbo),
+                        idesc, kk > 0 ? 1u : 0u);
+            tc::commit(mbar);
+        }
+        if (ok && !ptx::mbar_wait_bounded(mbar, phase, kWaitNs)) {
+            ok = false;
+            atomicOr(a.status, kStatusTimeout);
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+        float* dst = a.dxcol + r * S::KP + h * NN;
+        // three 16-column TMEM loads in flight per wait
+#pragma unroll 1
+        for (int c0 = 0; c0 < NN; c0 += 48) {
+            uint32_t q[3][16];
+#pragma unroll
+            for (int g = 0; g < 3; ++g) tc::ld16(tmem + ((32u * warp) << 16) + c0 + 16 * g, q[g]);
+            tc::wait_ld();
+            if (live && ok) {
+                float4* d4 = reinterpret_cast<float4*>(dst + c0);
+#pragma unroll
+                for (int i = 0; i < 12; ++i) {
+                    const uint32_t* qi = q[i >> 2] + 4 * (i & 3);
+                    d4[i] = make_float4(__uint_as_float(qi[0]), __uint_as_float(qi[1]), __uint_as_float(qi[2]),
+                                        __uint_as_float(qi[3]));
                 }
             }
         }
@@ -1468,8 +1489,9 @@ scn_status launch_bwd_data(const ConvBwdArgs& a, cudaStream_t st) {
     const int64_t tiles = (a.pairs * Shape<L>::P + 127) / 128;
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
-    // 256 TMEM columns per CTA: at most 2 CTAs per SM can hold them
-    const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(sms) * 2));
+    // one work item per row tile and column half; 256 TMEM columns per CTA: at most 2 CTAs per SM
+    constexpr int NH = Shape<L>::KP > 144 ? 2 : 1;
+    const int grid = static_cast<int>(std::min<int64_t>(tiles * NH, static_cast<int64_t>(sms) * 2));
     SCN_CUDA_TRY(launch_pdl(conv_bwd_data_tc<L>, dim3(grid), dim3(128), BwdSmem<L>::BYTES, st, a));
     return SCN_OK;
 }
@@ -1502,7 +1524,8 @@ scn_status launch_col2im(const float* dxcol, const __nv_bfloat16* act, __nv_bflo
                          cudaStream_t st) {
     using S = Shape<L>;
     const int64_t total = pairs * S::HIN * S::WIN * S::CIN;
-    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 8);
+    // one element per thread: every thread's few loads in flight at once
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 0x7fffffff);
     SCN_CUDA_TRY(
         launch_pdl(col2im_mask<L>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, st, dxcol, act, du_prev, pairs));
     return SCN_OK;
