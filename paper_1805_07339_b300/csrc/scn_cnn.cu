@@ -167,12 +167,15 @@ __device__ __forceinline__ uint4 im2col_chunk(const ConvFwdArgs& a, int64_t b, i
     }
 }
 
-// Threads of the training convolutions: kConvParts threads gather each of a tile's 128 rows,
-// every one of its im2col loads in flight before its first store.
-constexpr int kConvThreads = 512, kConvParts = kConvThreads / 128;
+// Threads that gather each 128-row tile of the training convolutions: every one of a
+// thread's im2col loads is in flight before its first store; layers with many k chunks per
+// row (2 and 3) split each row over four threads, layer 1 (four chunks) keeps one.
+template <int L>
+constexpr int gather_parts() { return Shape<L>::KP / 8 >= 16 ? 4 : 1; }
 
 template <int L>
-__global__ void __launch_bounds__(kConvThreads) conv_fwd_tc(const __grid_constant__ ConvFwdArgs a) {
+__global__ void __launch_bounds__(128 * gather_parts<L>()) conv_fwd_tc(const __grid_constant__ ConvFwdArgs a) {
+    constexpr int kConvParts = gather_parts<L>(), kConvThreads = 128 * kConvParts;
     ptx::pdl_wait();
     ptx::pdl_release();
     if (a.zero) {
@@ -356,7 +359,7 @@ scn_status launch_conv_fwd(const ConvFwdArgs& a, cudaStream_t st) {
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
     const int grid = static_cast<int>(std::min<int64_t>(tiles, static_cast<int64_t>(sms) * 4));
-    SCN_CUDA_TRY(launch_pdl(conv_fwd_tc<L>, dim3(grid), dim3(kConvThreads), ConvSmem<L>::BYTES, st, a));
+    SCN_CUDA_TRY(launch_pdl(conv_fwd_tc<L>, dim3(grid), dim3(128 * gather_parts<L>()), ConvSmem<L>::BYTES, st, a));
     return SCN_OK;
 }
 
@@ -1325,12 +1328,10 @@ __device__ __forceinline__ uint64_t mn_desc(uint32_t saddr, uint32_t mn_stride, 
     return tc::smem_desc(saddr, k_stride, mn_stride);
 }
 
-// Threads of the weight-gradient kernel: kWgtParts threads gather each of a chunk's 128 rows,
-// every one of its im2col loads in flight before its first store.
-constexpr int kWgtThreads = 512, kWgtParts = kWgtThreads / 128;
-
+// The weight-gradient kernel gathers its 128-row chunks the same way (gather_parts threads a row).
 template <int L>
-__global__ void __launch_bounds__(kWgtThreads) conv_bwd_weight_tc(const __grid_constant__ ConvWgtArgs a) {
+__global__ void __launch_bounds__(128 * gather_parts<L>()) conv_bwd_weight_tc(const __grid_constant__ ConvWgtArgs a) {
+    constexpr int kWgtParts = gather_parts<L>(), kWgtThreads = 128 * kWgtParts;
     ptx::pdl_wait();
     ptx::pdl_release();
     using S = Shape<L>;
@@ -1513,9 +1514,10 @@ scn_status launch_bwd_weight(const ConvWgtArgs& a, cudaStream_t st) {
     int sms = device_sm_count();
     if (sms <= 0) sms = 148;
     // as many CTAs per SM as shared memory and threads allow (at most 4: TMEM columns fit)
-    const int per_sm = std::max(1, std::min<int>(2048 / kWgtThreads, (227 * 1024) / (WgtTc<L>::BYTES + 1024)));
+    constexpr int threads = 128 * gather_parts<L>();
+    const int per_sm = std::max(1, std::min<int>(std::min(4, 2048 / threads), (227 * 1024) / (WgtTc<L>::BYTES + 1024)));
     const int grid = static_cast<int>(std::min<int64_t>(chunks, static_cast<int64_t>(sms) * per_sm));
-    SCN_CUDA_TRY(launch_pdl(conv_bwd_weight_tc<L>, dim3(grid), dim3(kWgtThreads), WgtTc<L>::BYTES, st, a));
+    SCN_CUDA_TRY(launch_pdl(conv_bwd_weight_tc<L>, dim3(grid), dim3(threads), WgtTc<L>::BYTES, st, a));
     return SCN_OK;
 }
 
