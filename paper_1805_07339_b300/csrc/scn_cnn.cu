@@ -70,6 +70,7 @@ constexpr int kW1 = 0, kB1 = kW1 + 16 * 2 * 9, kW2 = kB1 + 16, kB2 = kW2 + 32 * 
               kB3 = kW3 + 32 * 32 * 9, kF1 = kB3 + 32, kC1 = kF1 + 64 * 32, kF2 = kC1 + 64, kC2 = kF2 + 64,
               kNParams = kC2 + 1;
 static_assert(kNParams == 16369, "parameter count");
+static_assert(kW1 % 4 == 0 && kW2 % 4 == 0 && kW3 % 4 == 0, "conv weights start on 16-byte boundaries");
 
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -1433,8 +1434,13 @@ __global__ void __launch_bounds__(128 * gather_parts<L>()) conv_bwd_weight_tc(co
         phase ^= 1u;
         tc::fence_after_sync();
     }
-    // epilogue by warps 0-3 (TMEM lane = k within the tile, column = co; every CTA has at
-    // least one chunk; the loads are warp-wide, the adds only after a complete wait)
+    // epilogue: warps 0-3 read the accumulators (TMEM lane = k within the tile, column = co; the
+    // loads are warp-wide) and place the CTA's partial gradient in the operand buffer, free once
+    // the last MMAs have completed, in the gradient's own layout [co][ci][tap]; then every thread
+    // adds it to global memory with 16-byte vector atomics over contiguous words (the per-k
+    // addresses are 36 bytes apart: one atomic per element would cost one transaction each)
+    static_assert(S::COUT * S::K * 4 <= W::A_BYTES && (S::COUT * S::K) % 4 == 0, "partial gradient in the A buffer");
+    float* pgrad = reinterpret_cast<float*>(As);
     if (!first && warp < 4) {
 #pragma unroll
         for (int t = 0; t < W::MT; ++t) {
@@ -1444,18 +1450,23 @@ __global__ void __launch_bounds__(128 * gather_parts<L>()) conv_bwd_weight_tc(co
                 uint32_t q[16];
                 tc::ld16(tmem + ((32u * warp) << 16) + t * S::COUT + c0, q);
                 tc::wait_ld();
-                if (!ok) continue;
                 if (k < S::K) {
                     const int tap = k / S::CIN, ci = k % S::CIN;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        atomicAdd(a.gw + ((c0 + i) * S::CIN + ci) * 9 + tap, __uint_as_float(q[i]));
-                } else if (k == S::K) {
+                    for (int i = 0; i < 16; ++i) pgrad[(c0 + i) * S::K + ci * 9 + tap] = __uint_as_float(q[i]);
+                } else if (k == S::K && ok) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) atomicAdd(a.gb + c0 + i, __uint_as_float(q[i]));
                 }
             }
         }
+    }
+    __syncthreads();
+    if (!first && ok) {
+        // the gradient block is 16-byte aligned: the parameter offsets of W1, W2, W3 are multiples of 4
+        const float4* p4 = reinterpret_cast<const float4*>(pgrad);
+        float4* g4 = reinterpret_cast<float4*>(a.gw);
+        for (int i = tid; i < S::COUT * S::K / 4; i += blockDim.x) atomicAdd(g4 + i, p4[i]);
     }
     tc::fence_before_sync();
     __syncthreads();
