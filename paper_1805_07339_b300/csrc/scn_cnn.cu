@@ -70,7 +70,8 @@ constexpr int kW1 = 0, kB1 = kW1 + 16 * 2 * 9, kW2 = kB1 + 16, kB2 = kW2 + 32 * 
               kB3 = kW3 + 32 * 32 * 9, kF1 = kB3 + 32, kC1 = kF1 + 64 * 32, kF2 = kC1 + 64, kC2 = kF2 + 64,
               kNParams = kC2 + 1;
 static_assert(kNParams == 16369, "parameter count");
-static_assert(kW1 % 4 == 0 && kW2 % 4 == 0 && kW3 % 4 == 0, "conv weights start on 16-byte boundaries");
+static_assert(kW1 % 4 == 0 && kW2 % 4 == 0 && kW3 % 4 == 0 && kF1 % 4 == 0 && kC1 % 4 == 0 && kF2 % 4 == 0,
+              "parameter blocks added with vector atomics start on 16-byte boundaries");
 
 constexpr uint64_t kWaitNs = 2000000000ull;
 
@@ -1043,15 +1044,17 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ z, con
                                                 const __nv_bfloat16* __restrict__ a3, const __nv_bfloat16* f1b,
                                                 const __nv_bfloat16* f2b, float pos_weight, int64_t pairs,
                                                 float* grad, __nv_bfloat16* du3, float* loss) {
-    // F1 staged in shared memory; the block's gradient sums of F1 ([c][j] so that a warp's 32
-    // lanes hit 32 banks), c1 and F2, added by its warps and then once per element to `grad`
+    // F1 staged in shared memory; the block's gradient sums of F1 (row c of 65 words holds
+    // column c of F1, so that both a warp's 32 rows j and 32 consecutive columns c hit 32
+    // banks), c1 and F2, added by its warps and then to `grad` with 16-byte vector atomics
+    constexpr int kF1s = 32 * 65;
     __shared__ __nv_bfloat16 sf1[64 * 32];
-    __shared__ float sacc[64 * 32 + 64 + 64];
+    __shared__ float sacc[kF1s + 64 + 64];
     ptx::pdl_wait();
     ptx::pdl_release();
     const int tid = threadIdx.x, lane = tid & 31;
     for (int i = tid; i < 64 * 32; i += blockDim.x) sf1[i] = f1b[i];
-    for (int i = tid; i < 64 * 32 + 128; i += blockDim.x) sacc[i] = 0.f;
+    for (int i = tid; i < kF1s + 128; i += blockDim.x) sacc[i] = 0.f;
     __syncthreads();
     const int64_t w0 = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
@@ -1107,13 +1110,13 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ z, con
     if (w0 < pairs) {
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
-            atomicAdd(&sacc[c * 64 + lane], dF1a[c]);
-            atomicAdd(&sacc[c * 64 + 32 + lane], dF1b[c]);
+            atomicAdd(&sacc[c * 65 + lane], dF1a[c]);
+            atomicAdd(&sacc[c * 65 + 32 + lane], dF1b[c]);
         }
-        atomicAdd(&sacc[2048 + lane], dc1a);
-        atomicAdd(&sacc[2048 + 32 + lane], dc1b);
-        atomicAdd(&sacc[2112 + lane], dF2a);
-        atomicAdd(&sacc[2112 + 32 + lane], dF2b);
+        atomicAdd(&sacc[kF1s + lane], dc1a);
+        atomicAdd(&sacc[kF1s + 32 + lane], dc1b);
+        atomicAdd(&sacc[kF1s + 64 + lane], dF2a);
+        atomicAdd(&sacc[kF1s + 64 + 32 + lane], dF2b);
         // dc2 and the loss are the same in every lane (they depend on z only)
         if (lane == 0) {
             atomicAdd(grad + kC2, dc2);
@@ -1121,13 +1124,22 @@ __global__ void __launch_bounds__(256) head_bwd(const float* __restrict__ z, con
         }
     }
     __syncthreads();
-    for (int i = tid; i < 64 * 32; i += blockDim.x) {
-        const int c = i >> 6, j = i & 63;
-        atomicAdd(grad + kF1 + j * 32 + c, sacc[i]);
+    // F1's gradient is [j][c] in `grad`: four consecutive columns c of row j per vector atomic
+    for (int i = tid; i < 64 * 32 / 4; i += blockDim.x) {
+        const int j = i >> 3, c = (i & 7) * 4;
+        const float4 v = make_float4(sacc[c * 65 + j], sacc[(c + 1) * 65 + j], sacc[(c + 2) * 65 + j],
+                                     sacc[(c + 3) * 65 + j]);
+        atomicAdd(reinterpret_cast<float4*>(grad + kF1) + i, v);
     }
-    if (tid < 64) {
-        atomicAdd(grad + kC1 + tid, sacc[2048 + tid]);
-        atomicAdd(grad + kF2 + tid, sacc[2112 + tid]);
+    if (tid < 16) {  // c1 and F2: 64 each
+        atomicAdd(reinterpret_cast<float4*>(grad + kC1) + tid,
+                  make_float4(sacc[kF1s + 4 * tid], sacc[kF1s + 4 * tid + 1], sacc[kF1s + 4 * tid + 2],
+                              sacc[kF1s + 4 * tid + 3]));
+    } else if (tid < 32) {
+        const int u = tid - 16;
+        atomicAdd(reinterpret_cast<float4*>(grad + kF2) + u,
+                  make_float4(sacc[kF1s + 64 + 4 * u], sacc[kF1s + 64 + 4 * u + 1], sacc[kF1s + 64 + 4 * u + 2],
+                              sacc[kF1s + 64 + 4 * u + 3]));
     }
 }
 
