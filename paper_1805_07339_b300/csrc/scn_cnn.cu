@@ -1260,33 +1260,42 @@ __global__ void col2im_mask(const float* __restrict__ dxcol, const __nv_bfloat16
     ptx::pdl_wait();
     ptx::pdl_release();
     using S = Shape<L>;
-    const int64_t total = pairs * S::HIN * S::WIN * S::CIN;
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int ci = static_cast<int>(i % S::CIN);
-        const int64_t q = i / S::CIN;
-        const int ix = static_cast<int>(q % S::WIN);
-        const int iy = static_cast<int>((q / S::WIN) % S::HIN);
-        const int64_t b = q / (S::WIN * S::HIN);
-        float s = 0.f;
-        // output (oy, ox) with tap (di, dj): iy = 2 oy - 1 + di, ix = 2 ox - 1 + dj
+    static_assert(S::CIN % 4 == 0 && S::KP % 4 == 0, "four channels per thread, 16-byte dX loads");
+    constexpr int Q = S::CIN / 4;  // channel quads per input position
+    // one thread per input position and channel quad (32-bit indices: the launch checks the count)
+    const int total = static_cast<int>(pairs) * S::HIN * S::WIN * Q;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int c4 = i % Q, q = i / Q;
+    const int ix = q % S::WIN, iy = (q / S::WIN) % S::HIN, b = q / (S::WIN * S::HIN);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    // output (oy, ox) with tap (di, dj): iy = 2 oy - 1 + di, ix = 2 ox - 1 + dj
 #pragma unroll
-        for (int di = 0; di < 3; ++di) {
-            const int ty = iy + 1 - di;
-            if (ty < 0 || (ty & 1)) continue;
-            const int oy = ty >> 1;
-            if (oy >= S::HO) continue;
+    for (int di = 0; di < 3; ++di) {
+        const int ty = iy + 1 - di;
+        if (ty < 0 || (ty & 1)) continue;
+        const int oy = ty >> 1;
+        if (oy >= S::HO) continue;
 #pragma unroll
-            for (int dj = 0; dj < 3; ++dj) {
-                const int tx = ix + 1 - dj;
-                if (tx < 0 || (tx & 1)) continue;
-                const int ox = tx >> 1;
-                if (ox >= S::WO) continue;
-                s += dxcol[((b * S::P) + oy * S::WO + ox) * S::KP + (di * 3 + dj) * S::CIN + ci];
-            }
+        for (int dj = 0; dj < 3; ++dj) {
+            const int tx = ix + 1 - dj;
+            if (tx < 0 || (tx & 1)) continue;
+            const int ox = tx >> 1;
+            if (ox >= S::WO) continue;
+            const float4 v = __ldg(reinterpret_cast<const float4*>(
+                dxcol + (static_cast<int64_t>(b) * S::P + oy * S::WO + ox) * S::KP + (di * 3 + dj) * S::CIN + 4 * c4));
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
         }
-        du_prev[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.f ? s : 0.f);
     }
+    // ReLU mask of the layer below: its activation > 0 (bf16 bit patterns 0x0001 .. 0x7F80)
+    const uint2 a = __ldg(reinterpret_cast<const uint2*>(act) + i);
+    auto pos = [](uint32_t h) { return (h & 0xFFFFu) - 1u < 0x7F80u; };
+    const float r0 = pos(a.x) ? acc.x : 0.f, r1 = pos(a.x >> 16) ? acc.y : 0.f;
+    const float r2 = pos(a.y) ? acc.z : 0.f, r3 = pos(a.y >> 16) ? acc.w : 0.f;
+    reinterpret_cast<uint2*>(du_prev)[i] = make_uint2(pack_bf16(r0, r1), pack_bf16(r2, r3));
 }
 
 // Arguments of the backward-weights kernel.
@@ -1548,9 +1557,10 @@ template <int L>
 scn_status launch_col2im(const float* dxcol, const __nv_bfloat16* act, __nv_bfloat16* du_prev, int64_t pairs,
                          cudaStream_t st) {
     using S = Shape<L>;
-    const int64_t total = pairs * S::HIN * S::WIN * S::CIN;
-    // one element per thread: every thread's few loads in flight at once
-    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 0x7fffffff);
+    // one thread per input position and four channels: every thread's loads in flight at once
+    const int64_t total = pairs * S::HIN * S::WIN * (S::CIN / 4);
+    if (total > 0x7fffffff) return SCN_ERANGE;
+    const int64_t blocks = (total + 255) / 256;
     SCN_CUDA_TRY(
         launch_pdl(col2im_mask<L>, dim3(static_cast<unsigned>(blocks)), dim3(256), 0, st, dxcol, act, du_prev, pairs));
     return SCN_OK;
