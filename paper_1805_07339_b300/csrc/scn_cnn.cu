@@ -1159,7 +1159,8 @@ template <int L>
 struct BwdSmem {
     using S = Shape<L>;
     static constexpr int A_BYTES = 128 * S::COUT * 2, B_BYTES = S::KP * S::COUT * 2;
-    static constexpr int BYTES = A_BYTES + B_BYTES + 64;
+    static constexpr int S_OFF = A_BYTES + B_BYTES + 64;  // the epilogue's 128 x 48 staging block
+    static constexpr int BYTES = S_OFF + 128 * 52 * 4;
 };
 
 template <int L>
@@ -1227,23 +1228,35 @@ __global__ void __launch_bounds__(128) conv_bwd_data_tc(const __grid_constant__ 
         }
         phase ^= 1u;
         tc::fence_after_sync();
-        float* dst = a.dxcol + r * S::KP + h * NN;
-        // three 16-column TMEM loads in flight per wait
+        // three 16-column TMEM loads in flight per wait; the 128 x 48 block goes through shared
+        // memory (row pitch 52 floats: a quarter warp's 16-byte stores hit 8 distinct bank groups)
+        // so that consecutive threads store consecutive 16-byte pieces of a row
+        float* stg = reinterpret_cast<float*>(smem + M::S_OFF);
 #pragma unroll 1
         for (int c0 = 0; c0 < NN; c0 += 48) {
             uint32_t q[3][16];
 #pragma unroll
             for (int g = 0; g < 3; ++g) tc::ld16(tmem + ((32u * warp) << 16) + c0 + 16 * g, q[g]);
             tc::wait_ld();
-            if (live && ok) {
-                float4* d4 = reinterpret_cast<float4*>(dst + c0);
+            float4* srow = reinterpret_cast<float4*>(stg + tid * 52);
 #pragma unroll
-                for (int i = 0; i < 12; ++i) {
-                    const uint32_t* qi = q[i >> 2] + 4 * (i & 3);
-                    d4[i] = make_float4(__uint_as_float(qi[0]), __uint_as_float(qi[1]), __uint_as_float(qi[2]),
-                                        __uint_as_float(qi[3]));
+            for (int i = 0; i < 12; ++i) {
+                const uint32_t* qi = q[i >> 2] + 4 * (i & 3);
+                srow[i] = make_float4(__uint_as_float(qi[0]), __uint_as_float(qi[1]), __uint_as_float(qi[2]),
+                                      __uint_as_float(qi[3]));
+            }
+            __syncthreads();
+            if (ok) {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    const int f = tid + 128 * k, rr = f / 12, c4 = f - rr * 12;
+                    const int64_t row = t * 128 + rr;
+                    if (row < rows)
+                        reinterpret_cast<float4*>(a.dxcol + row * S::KP + h * NN + c0)[c4] =
+                            reinterpret_cast<const float4*>(stg + rr * 52)[c4];
                 }
             }
+            __syncthreads();
         }
         tc::fence_before_sync();
         __syncthreads();
