@@ -103,18 +103,18 @@ def train(torch, net: int, thumbs, prev, cur, labels, steps: int = 2500, batch: 
     draws = torch.from_numpy(rng.integers(0, labels.numel(), (steps, batch)).astype(np.int64)).cuda()
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     curve = []
-    bp = torch.empty(batch, dtype=torch.int32, device="cuda")
-    bc = torch.empty(batch, dtype=torch.int32, device="cuda")
-    by = torch.empty(batch, dtype=torch.float32, device="cuda")
     t0 = time.perf_counter()
+    # every step's batch gathered up front, so that a step is the library's launches alone: one
+    # chain of dependent launches, with no gather kernel and no loss copy except on logging steps
+    bp_all = torch.index_select(prev, 0, draws.reshape(-1)).reshape(steps, batch)
+    bc_all = torch.index_select(cur, 0, draws.reshape(-1)).reshape(steps, batch)
+    by_all = torch.index_select(labels, 0, draws.reshape(-1)).reshape(steps, batch)
     for s in range(steps):
-        ix = draws[s]
-        torch.index_select(prev, 0, ix, out=bp)
-        torch.index_select(cur, 0, ix, out=bc)
-        torch.index_select(labels, 0, ix, out=by)
         lr_s = lr * 0.5 * (1.0 + np.cos(np.pi * s / steps)) if cosine else lr
-        scn.scn_cnn_train_step(net, thumbs, by, batch, pos_weight, max(lr_s, 1e-6), loss=loss, prev=bp, cur=bc)
-        if log_every and (s % log_every == 0 or s == steps - 1):
+        log = bool(log_every) and (s % log_every == 0 or s == steps - 1)
+        scn.scn_cnn_train_step(net, thumbs, by_all[s], batch, pos_weight, max(lr_s, 1e-6), loss=loss if log else None,
+                               prev=bp_all[s], cur=bc_all[s])
+        if log:
             curve.append((s, float(loss.item())))
     torch.cuda.synchronize()
     return {"pos_weight": pos_weight, "steps": steps, "batch": batch, "lr": lr, "curve": curve,
