@@ -288,20 +288,29 @@ __global__ void __launch_bounds__(128 * gather_parts<L>()) conv_fwd_tc(const __g
 __global__ void __launch_bounds__(256) head_fwd(const __nv_bfloat16* __restrict__ a3, const __nv_bfloat16* f1b,
                                                 const float* c1, const __nv_bfloat16* f2b, const float* c2, float* g_out,
                                                 float* v_out, float* z, int64_t pairs) {
+    // F1 as fp32 in shared memory, row pitch 33 (a warp reading column c of 32 rows hits 32 banks)
+    __shared__ float sf1[64 * 33];
     ptx::pdl_wait();
     ptx::pdl_release();
+    for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) sf1[(i >> 5) * 33 + (i & 31)] = __bfloat162float(f1b[i]);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t b = blockIdx.x * static_cast<int64_t>(blockDim.x / 32) + threadIdx.x / 32;
     if (b >= pairs) return;
     float s = 0.f;
     const __nv_bfloat16* p = a3 + b * 40 * 32 + lane;
-    for (int pos = 0; pos < 40; ++pos) s += __bfloat162float(p[pos * 32]);
+    __nv_bfloat16 av[40];  // every load in flight before the (ordered) sum
+#pragma unroll
+    for (int pos = 0; pos < 40; ++pos) av[pos] = p[pos * 32];
+#pragma unroll
+    for (int pos = 0; pos < 40; ++pos) s += __bfloat162float(av[pos]);
     const float g = s * (1.f / 40.f);
     float v0 = c1[lane], v1 = c1[lane + 32];
+#pragma unroll
     for (int c = 0; c < 32; ++c) {
         const float gc = __shfl_sync(0xffffffffu, g, c);
-        v0 = fmaf(__bfloat162float(f1b[lane * 32 + c]), gc, v0);
-        v1 = fmaf(__bfloat162float(f1b[(lane + 32) * 32 + c]), gc, v1);
+        v0 = fmaf(sf1[lane * 33 + c], gc, v0);
+        v1 = fmaf(sf1[(lane + 32) * 33 + c], gc, v1);
     }
     float zz = __bfloat162float(f2b[lane]) * fmaxf(v0, 0.f) + __bfloat162float(f2b[lane + 32]) * fmaxf(v1, 0.f);
     for (int o = 16; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
