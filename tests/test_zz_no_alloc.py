@@ -74,6 +74,28 @@ def test_noalloc_matches_regular_entry_point_twice(scn):
         assert torch.equal(x, y)
 
 
+def test_noalloc_whole_frame_queue_with_split_tail(scn):
+    """Enough 1080p frames for a whole-frame queue (at least eight per CTA), whose last frames are
+    queued in quarters through the partial accumulators of the library's fixed scratch: the same
+    histograms, scores and flags as the regular entry point."""
+    W, H, T = 1920, 1080, 1200
+    v = scn.scn_video_create(MASTER_SEED, 3, W, H, T, 10)
+    buf = torch.empty(T * W * H * 3 // 2, dtype=torch.uint8, device="cuda")
+    try:
+        scn.scn_generate(v, buf, 0, T, W * H * 3 // 2)
+        idx = list(range(T))
+        idx[600:610] = idx[600:610][::-1]  # a stretch out of order: its scores cross shots both ways
+        a = _noalloc(scn, buf, W, H, idx)
+        b = _regular(scn, buf, W, H, T, idx)
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+        assert int(a[0].sum()) == 3 * W * H * T
+    finally:
+        scn.scn_video_destroy(v)
+        del buf
+        torch.cuda.empty_cache()
+
+
 def test_noalloc_limits(scn):
     buf = torch.zeros(64 * 36 * 3 // 2, dtype=torch.uint8, device="cuda")
     out = torch.zeros(16, dtype=torch.int32, device="cuda")
