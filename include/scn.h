@@ -473,8 +473,8 @@ scn_status scn_thumb_diff_yuv(const uint8_t* d_yuv, int64_t n, float* d_diff, vo
  * scn_gated_hist_scores with tau_net, so a pair is proposed only when both
  * thresholds pass and the exact kernel keeps the final say.  The network runs
  * on the listed pairs only (their count stays on the device: no host round
- * trip).  Workspace as scn_gated_hist_scores.  d_diff, d_gate 4-byte aligned
- * (SCN_EINVAL); more than 2^31 - 1 elements: SCN_ERANGE. */
+ * trip).  Workspace as scn_gated_hist_scores.  d_diff, d_gate, d_score 4-byte
+ * aligned (SCN_EINVAL); more than 2^31 - 1 elements: SCN_ERANGE. */
 scn_status scn_cascade_hist_scores(scn_seq* s, scn_cnn* net, float tau_diff, float tau_net, uint8_t* d_thumbs,
                                    uint8_t* d_uv, float* d_diff, float* d_gate, uint8_t* d_proposed,
                                    uint32_t* d_score, uint8_t* d_flag, int64_t* h_nproposed, void* stream);
